@@ -1,0 +1,198 @@
+/*
+ * rbc.h -- C ABI of librbc: GB300 (sm_103a) seismic modeling and reverse time
+ * migration with random boundary conditions (Barbosa & Coutinho,
+ * arXiv:2204.03380).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid.  The velocity model has an interior of nx x ny x nz nodes (ny = 1 for
+ * 2-D) padded with nb random-boundary cells on every side (Section 4.3), so
+ * the PADDED grid has NX = nx + 2 nb, NY = ny + 2 nb (1 in 2-D), NZ = nz + 2 nb
+ * nodes.  Dense arrays are x fastest: element (x, y, z) sits at
+ * ((z * NY) + y) * NX + x; interior arrays use (nz, ny, nx) the same way.
+ * Node indices passed to the ABI (source, receivers) are in the padded frame;
+ * for 2-D grids the y index must be 0.  Beyond the padded grid the pressure is
+ * zero (Eq. 1: p = 0 on the domain boundary).
+ *
+ * Scheme.  Eq. 1 discretised 8th order in space, 2nd order in time (Section
+ * 4): p^{n+1} = 2 p^n - p^{n-1} + a L8 p^n - a_s f[n] h^(2-d) delta_s, where
+ * a = (v dt / h)^2 and L8 is h^2 times the 8th-order Laplacian.  f[n] drives
+ * the step from level n to n+1; records hold levels 0..nt (N_t + 1 samples).
+ * Arithmetic is fp32.
+ *
+ * Memory.  Every pointer named *_dev is device memory on the current CUDA
+ * device, owned by the caller, 16-byte aligned (any pointer from cudaMalloc or
+ * a PyTorch CUDA tensor).  Pointers named *_host are host memory.  No call
+ * allocates memory visible to the caller; an rbc_ctx owns its internal
+ * wavefields.  Calls that take a `stream` (a cudaStream_t; NULL = legacy
+ * default stream) are asynchronous on it unless stated.
+ *
+ * Errors.  Every call returns RBC_OK (0) or a positive error code, never
+ * throws, and leaves a thread-local message for rbc_last_error().  On an
+ * error no work has been queued, except for RBC_ECUDA, which reports a CUDA
+ * failure from a launch or a copy.
+ */
+#ifndef RBC_H_
+#define RBC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RBC_OK = 0,
+  RBC_EINVAL = 1,   /* bad shape, index outside the grid, NULL pointer      */
+  RBC_ECFL = 2,     /* a = (v dt/h)^2 violates the scheme's stability limit  */
+  RBC_ENOMEM = 3,   /* device allocation failed                              */
+  RBC_ECUDA = 4,    /* CUDA launch / copy failure                            */
+  RBC_ETIMEOUT = 5, /* a bounded device wait gave up                         */
+  RBC_ENOTSUP = 6   /* option not supported by this build                    */
+};
+
+/* Flags of rbc_rtm_shot. */
+#define RBC_REINJECT_SOURCE 1 /* reconstruction re-subtracts the source term  */
+#define RBC_ZERO_FIRST 2      /* overwrite num/den instead of accumulating    */
+
+typedef struct {
+  int ndim;         /* 2 or 3                                                 */
+  int nx, ny, nz;   /* interior nodes; ny is ignored (taken as 1) for 2-D     */
+  int nb;           /* random-boundary cells on each side, >= 2              */
+  int free_surface; /* must be 0: random boundary on every side              */
+  double h;         /* grid spacing dx = dy = dz (m)                          */
+  double dt;        /* time step (s)                                          */
+  int nt;           /* number of time steps N_t (>= 1)                        */
+} rbc_grid;
+
+typedef struct rbc_ctx rbc_ctx;
+
+/*
+ * rbc_build_velocity -- pad an interior velocity with a random boundary and
+ * form the leapfrog coefficient (Section 4.3, Eqs. 4-5; Algorithm 3 "create
+ * a RBC").
+ *   v_int_dev: interior velocity (m/s), dense (nz, ny, nx) fp32.
+ *   For a pad cell with max-norm distance i (1..nb) into the pad and padded
+ *   linear index L, two splitmix64 counter draws U1 = draw(2L+1),
+ *   U2 = draw(2L+2) of stream `seed` (each the top 53 bits / 2^53) give
+ *     c = lo_i + (hi_i - lo_i) U1,  lo_i/hi_i = min/max(h(i), g(i)) of Eqs. 5/4,
+ *     v_rand = v_lo + (v_hi - v_lo) U2,
+ *     mode 0 ("blend"):   v = c v_edge + (1 - c) v_rand  (v_edge = nearest
+ *                         interior value),
+ *     mode 1 ("literal"): v = max(c v_rand, v_lo);
+ *   then v = min(v, v_max).  Interior cells keep v_int.  All arithmetic in
+ *   fp64, a = (v dt / h)^2 rounded once to fp32.
+ *   v_pad_dev (may be NULL): padded velocity, dense (NZ, NY, NX) fp32.
+ *   a_dev: padded coefficient, dense (NZ, NY, NX) fp32.
+ * Errors: RBC_EINVAL for a bad grid, NULL v_int_dev / a_dev, v_lo > v_hi, or
+ * mode not 0/1.
+ */
+int rbc_build_velocity(const rbc_grid *g, const float *v_int_dev, float v_lo,
+                       float v_hi, float v_max, uint64_t seed, int mode,
+                       float *v_pad_dev, float *a_dev, void *stream);
+
+/*
+ * rbc_create -- make a context for one padded model (Algorithm 4/6 "move data
+ * to GPU"): validates the grid, checks stability, allocates the internal
+ * wavefields (two panels per wavefield, Algorithm 3) and copies a_dev into
+ * the context's aligned, zero-haloed layout.  a_dev (dense (NZ, NY, NX)
+ * fp32) is only read during this call.  Synchronous.
+ * Stability (the paper requires it of the random velocities, Section 4.3):
+ *   max(a) * ndim * 6.5015873 < 4   (6.50... = |symbol of L8| at Nyquist),
+ *   else RBC_ECFL.
+ * Errors: RBC_EINVAL (bad grid, NULL), RBC_ECFL, RBC_ENOMEM, RBC_ECUDA.
+ */
+int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out);
+
+/* rbc_destroy -- free a context (synchronises its device work first).
+ * NULL is accepted and ignored. */
+int rbc_destroy(rbc_ctx *ctx);
+
+/*
+ * rbc_model -- Algorithm 1 (seismic modeling) for one shot.
+ *   src_host: (x, y, z) padded node of the point source.
+ *   wavelet_dev: f[0..nt-1] fp32 (f[n] drives step n -> n+1).
+ *   rec_host: nrec x (x, y, z) int32 padded receiver nodes (nrec >= 0).
+ *   seis_dev: output (nrec, nt + 1) fp32, seis[r][n] = p^n(rec_r).
+ * After the call the context holds p^{nt-1} and p^{nt} (the two panels that
+ * rbc_rtm_shot would keep), readable with rbc_get_panels.
+ * Errors: RBC_EINVAL (NULL, node outside the padded grid), RBC_ENOMEM (the
+ * receiver tables could not grow), RBC_ECUDA.
+ */
+int rbc_model(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
+              int nrec, const int *rec_host, float *seis_dev, void *stream);
+
+/*
+ * rbc_rtm_shot -- Algorithm 3 (RTM with wavefield reconstruction) for one
+ * shot, with the imaging condition of Eq. 3 accumulated as two integrals.
+ *   Forward: Algorithm 1 without recording; keeps p^{nt-1}, p^{nt}.
+ *   Reverse, n = nt .. 0:  num += p^R_n pbar_n,  den += (p^R_n)^2 on the
+ *   interior; p^R_{n-1} from Eq. 6 (source re-subtracted when flags has
+ *   RBC_REINJECT_SOURCE: the exact inverse of the forward step); pbar_{n-1}
+ *   from Eq. 2 with the record injected as + a_r s[r][n] h^(2-d).
+ *   seis_dev: (nrec, nt + 1) fp32 record (e.g. from rbc_model).
+ *   num_dev, den_dev: interior (nz, ny, nx) fp32, ACCUMULATED (+=), or
+ *   overwritten with this shot's integrals when flags has RBC_ZERO_FIRST.
+ * Errors: as rbc_model; flags outside RBC_REINJECT_SOURCE | RBC_ZERO_FIRST
+ * -> RBC_EINVAL.
+ */
+int rbc_rtm_shot(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
+                 int nrec, const int *rec_host, const float *seis_dev,
+                 int flags, float *num_dev, float *den_dev, void *stream);
+
+/*
+ * rbc_image_stack -- Eq. 3 ratio and Algorithm 3 stacking:
+ *   I = num / (den + eps_rel * max(den)) over the shot interior (nz, ny, nx),
+ *   image[z][y + off_y][x + off_x] += I[z][y][x]   (survey grid interior),
+ * where shot->nz must equal survey->nz and the window must fit.  2-D grids
+ * need off_y = 0.  Uses a few bytes of stream-ordered scratch.
+ * Errors: RBC_EINVAL (shape, window, NULL), RBC_ECUDA.
+ */
+int rbc_image_stack(const rbc_grid *shot, const float *num_dev,
+                    const float *den_dev, float eps_rel, int off_x, int off_y,
+                    const rbc_grid *survey, float *image_dev, void *stream);
+
+/*
+ * rbc_set_snapshots -- ask the next rbc_model / rbc_rtm_shot on this context
+ * to copy wavefields at chosen time levels (Figure 1's propagation and
+ * reconstruction panels).  levels_host[k] in [0, nt]; pf_dev / pr_dev / pb_dev
+ * (each may be NULL) receive nsnap dense padded (NZ, NY, NX) fp32 fields:
+ * pf = forward p^n (both calls), pr = reconstructed p^R_n and pb = receiver
+ * pbar_n (rbc_rtm_shot only).  nsnap = 0 clears the request.  The request
+ * stays until cleared.  Errors: RBC_EINVAL.
+ */
+int rbc_set_snapshots(rbc_ctx *ctx, int nsnap, const int *levels_host,
+                      float *pf_dev, float *pr_dev, float *pb_dev);
+
+/*
+ * rbc_get_panels -- copy the two forward panels kept after the last
+ * rbc_model / forward phase (p^{nt-1} -> prev_dev, p^{nt} -> last_dev; dense
+ * padded (NZ, NY, NX) fp32; either may be NULL).  Lets a caller checkpoint the
+ * reconstruction's initial state (Algorithm 3 "store p_{N-1}, p_N").
+ */
+int rbc_get_panels(rbc_ctx *ctx, float *prev_dev, float *last_dev,
+                   void *stream);
+
+/*
+ * rbc_phase_timing -- per-phase device timing with CUDA events recorded on
+ * the caller's stream.  enable = 1 clears the record and starts timing the
+ * forward and reverse phases of every following rbc_rtm_shot on this
+ * context; enable = 0 stops, synchronises and writes out[0] = forward ms,
+ * out[1] = reverse ms, out[2] = forward stencil launches, out[3] = reverse
+ * stencil launches, out[4] = shots timed (out may be NULL).  The phase times
+ * include the few memsets that clear the fields.  Errors: RBC_EINVAL,
+ * RBC_ECUDA.
+ */
+int rbc_phase_timing(rbc_ctx *ctx, int enable, double *out);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char *rbc_last_error(void);
+
+/* Kernel launches queued by this thread's calls since the counter was last
+ * reset (diagnostics for launch accounting); reset=1 zeroes it. */
+long long rbc_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBC_H_ */

@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) seismic modeling and reverse time migration with
+random boundary conditions (Barbosa & Coutinho, arXiv:2204.03380).
+
+The compute path is the C-ABI library ``librbc`` (include/rbc.h), hand-written
+CUDA kernels for sm_103a; this package only binds it.  PyTorch provides device
+memory and streams.
+"""
+from ._native import (  # noqa: F401
+    RBC_REINJECT_SOURCE, RBC_ZERO_FIRST, RBCError, make_grid, rbc_build_velocity, rbc_create, rbc_destroy,
+    rbc_get_panels, rbc_grid, rbc_image_stack, rbc_last_error, rbc_launch_count, rbc_model,
+    rbc_phase_timing, rbc_rtm_shot, rbc_set_snapshots, LIB_PATH, EXPORTED,
+)

@@ -1,0 +1,181 @@
+"""ctypes binding of librbc (include/rbc.h): argument marshalling only.
+
+Every call checks tensor device/dtype/shape, passes raw pointers, the current
+CUDA stream and host index arrays to the C ABI, and raises ``RBCError`` with
+the library's message on a non-zero status.  There is no CPU fallback: if the
+shared library has not been built, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librbc.so")
+
+RBC_OK, RBC_EINVAL, RBC_ECFL, RBC_ENOMEM, RBC_ECUDA, RBC_ETIMEOUT, RBC_ENOTSUP = range(7)
+RBC_REINJECT_SOURCE = 1
+RBC_ZERO_FIRST = 2
+_NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOTSUP"}
+
+
+class RBCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"RBC_{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rbc_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("nb", C.c_int), ("free_surface", C.c_int), ("h", C.c_double),
+                ("dt", C.c_double), ("nt", C.c_int)]
+
+    @property
+    def padded(self):
+        n = 2 * self.nb
+        if self.ndim == 2:
+            return (self.nz + n, self.nx + n)
+        return (self.nz + n, self.ny + n, self.nx + n)
+
+    @property
+    def interior(self):
+        return (self.nz, self.nx) if self.ndim == 2 else (self.nz, self.ny, self.nx)
+
+
+def make_grid(ndim, nx, ny, nz, nb, h, dt, nt, free_surface=0) -> rbc_grid:
+    return rbc_grid(int(ndim), int(nx), int(ny if ndim == 3 else 1), int(nz), int(nb),
+                    int(free_surface), float(h), float(dt), int(nt))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librbc is not built ({LIB_PATH} missing): run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    P, I, F = C.c_void_p, C.c_int, C.c_float
+    G = C.POINTER(rbc_grid)
+    lib.rbc_build_velocity.argtypes = [G, P, F, F, F, C.c_uint64, I, P, P, P]
+    lib.rbc_create.argtypes = [G, P, C.POINTER(C.c_void_p)]
+    lib.rbc_destroy.argtypes = [P]
+    lib.rbc_model.argtypes = [P, P, P, I, P, P, P]
+    lib.rbc_rtm_shot.argtypes = [P, P, P, I, P, P, I, P, P, P]
+    lib.rbc_image_stack.argtypes = [G, P, P, F, I, I, G, P, P]
+    lib.rbc_set_snapshots.argtypes = [P, I, P, P, P, P]
+    lib.rbc_get_panels.argtypes = [P, P, P, P]
+    lib.rbc_phase_timing.argtypes = [P, I, P]
+    lib.rbc_last_error.restype = C.c_char_p
+    lib.rbc_launch_count.argtypes = [I]
+    lib.rbc_launch_count.restype = C.c_longlong
+    for name in ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc_rtm_shot",
+                 "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing"):
+        getattr(lib, name).restype = I
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc_rtm_shot",
+            "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing",
+            "rbc_last_error", "rbc_launch_count")
+
+
+def _check(code):
+    if code != RBC_OK:
+        raise RBCError(code, _lib.rbc_last_error().decode())
+
+
+def _dev(t, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _nodes(a, n=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1, 3))
+    if n is not None and arr.shape[0] != n:
+        raise ValueError("bad node list")
+    return arr
+
+
+def rbc_build_velocity(grid, v_int, v_lo, v_hi, v_max, seed, mode, v_pad, a, stream=None):
+    _check(_lib.rbc_build_velocity(C.byref(grid), _dev(v_int, grid.interior, "v_int"), float(v_lo),
+                                   float(v_hi), float(v_max), C.c_uint64(int(seed)), int(mode),
+                                   _dev(v_pad, grid.padded, "v_pad"), _dev(a, grid.padded, "a"),
+                                   _stream(stream)))
+
+
+def rbc_create(grid, a):
+    """Returns an opaque context handle (int); free it with rbc_destroy."""
+    out = C.c_void_p()
+    torch.cuda.synchronize()
+    _check(_lib.rbc_create(C.byref(grid), _dev(a, grid.padded, "a"), C.byref(out)))
+    return out.value
+
+
+def rbc_destroy(ctx):
+    _check(_lib.rbc_destroy(C.c_void_p(ctx)))
+
+
+def rbc_model(ctx, src, wavelet, rec, seis, stream=None):
+    s = _nodes(src, 1)
+    r = _nodes(rec)
+    _check(_lib.rbc_model(C.c_void_p(ctx), s.ctypes.data_as(C.c_void_p), _dev(wavelet, None, "wavelet"),
+                          r.shape[0], r.ctypes.data_as(C.c_void_p) if r.size else None,
+                          _dev(seis, None, "seis") if r.shape[0] else None, _stream(stream)))
+
+
+def rbc_rtm_shot(ctx, src, wavelet, rec, seis, flags, num, den, stream=None):
+    s = _nodes(src, 1)
+    r = _nodes(rec)
+    _check(_lib.rbc_rtm_shot(C.c_void_p(ctx), s.ctypes.data_as(C.c_void_p), _dev(wavelet, None, "wavelet"),
+                             r.shape[0], r.ctypes.data_as(C.c_void_p) if r.size else None,
+                             _dev(seis, None, "seis") if r.shape[0] else None, int(flags),
+                             _dev(num, None, "num"), _dev(den, None, "den"), _stream(stream)))
+
+
+def rbc_image_stack(shot_grid, num, den, eps_rel, off_x, off_y, survey_grid, image, stream=None):
+    _check(_lib.rbc_image_stack(C.byref(shot_grid), _dev(num, shot_grid.interior, "num"),
+                                _dev(den, shot_grid.interior, "den"), float(eps_rel), int(off_x), int(off_y),
+                                C.byref(survey_grid), _dev(image, survey_grid.interior, "image"),
+                                _stream(stream)))
+
+
+def rbc_set_snapshots(ctx, levels, pf=None, pr=None, pb=None):
+    lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32).ravel())
+    _check(_lib.rbc_set_snapshots(C.c_void_p(ctx), lv.size, lv.ctypes.data_as(C.c_void_p) if lv.size else None,
+                                  _dev(pf, None, "pf"), _dev(pr, None, "pr"), _dev(pb, None, "pb")))
+
+
+def rbc_get_panels(ctx, prev=None, last=None, stream=None):
+    _check(_lib.rbc_get_panels(C.c_void_p(ctx), _dev(prev, None, "prev"), _dev(last, None, "last"),
+                               _stream(stream)))
+
+
+def rbc_phase_timing(ctx, enable):
+    """enable=True starts phase timing; enable=False stops and returns
+    dict(fwd_ms, rev_ms, fwd_launches, rev_launches, shots)."""
+    out = (C.c_double * 5)()
+    _check(_lib.rbc_phase_timing(C.c_void_p(ctx), 1 if enable else 0, out))
+    if enable:
+        return None
+    return dict(fwd_ms=out[0], rev_ms=out[1], fwd_launches=int(out[2]), rev_launches=int(out[3]),
+                shots=int(out[4]))
+
+
+def rbc_last_error() -> str:
+    return _lib.rbc_last_error().decode()
+
+
+def rbc_launch_count(reset: bool = False) -> int:
+    return int(_lib.rbc_launch_count(1 if reset else 0))

@@ -1,0 +1,121 @@
+// rbc_internal.cuh -- shared device/host definitions of librbc (sm_103a).
+//
+// Internal wavefield layout ("pitched, zero-haloed"): a field of the padded
+// grid NX x NY x NZ lives in a buffer where node (x, y, z) sits at
+//   origin + z * plane + y * pitch + x
+// with 32 zero floats before x = 0 (so rows start 128-byte aligned), at least
+// 32 after the last computed column, 4 zero rows before/after in y (3-D) and
+// 4 zero planes before/after in z.  The zeros are never written: they are the
+// p = 0 boundary of Eq. 1 seen by the 8th-order stencil (radius 4).  Columns
+// in [NX, NX4) (NX4 = NX rounded up to 4) carry a = 0 and stay exactly zero.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rbc {
+
+// 8th-order central second-derivative weights c1..c4 (Section 4).  The
+// kernels evaluate h^2 lap p as sum_k c_k [(p_{-k} - p) + (p_{+k} - p)] per
+// axis, which equals c0 p + sum_k c_k (p_{-k} + p_{+k}) because
+// c0 = -2 (c1 + c2 + c3 + c4); differences from the centre keep the fp32
+// rounding relative to the (small) second differences instead of |p|.
+constexpr float kC1 = 1.6f;
+constexpr float kC2 = -0.2f;
+constexpr float kC3 = 0.025396825396825397f;   // 8/315
+constexpr float kC4 = -0.0017857142857142857f; // -1/560
+// |symbol of L8| at the Nyquist wavenumber: stability needs a * ndim * it < 4.
+constexpr double kSymbolMax = 6.501587301587302;
+
+constexpr int kTileX = 128;  // x extent of a block tile: 32 lanes x float4
+constexpr int kHaloX = 32;   // zero floats before x = 0
+constexpr int kHaloR = 4;    // stencil radius
+
+struct Lay {
+  int ndim;
+  int NX, NY, NZ;  // padded grid
+  int NX4;         // NX rounded up to 4
+  int pitch;       // floats per row (multiple of 32)
+  int rows;        // rows per z-plane (1 in 2-D)
+  int plane;       // floats per z-plane
+  int origin;      // offset of node (0, 0, 0)
+  long long total; // floats per buffer
+};
+
+__host__ __device__ inline int lay_off(const Lay &L, int x, int y, int z) {
+  return L.origin + z * L.plane + y * L.pitch + x;
+}
+
+// Per-shot values read by the kernels from device memory, so that a captured
+// CUDA graph stays valid from shot to shot.
+struct ShotInfo {
+  int src_off;     // source node offset in the pitched layout
+  int nrec;        // receivers of this shot
+  float src_fwd;   // h^(2-d): forward injection scale
+  float src_rev;   // h^(2-d) or 0: reconstruction re-subtraction scale
+  float rec_scale; // +h^(2-d): receiver injection scale (Eq. 2)
+  int pad[3];
+};
+
+struct StepArgs {
+  Lay L;
+  const float *__restrict__ a;
+  const float *__restrict__ cur;  // p^n
+  float *__restrict__ nxt;        // in: p^{n-1}; out: p^{n+1}
+  const ShotInfo *info;
+  const float *wav;               // f[0..nt-1]
+  const int *rec_off;             // receiver offsets (pitched layout)
+  float *seis_t;                  // [nt+1][nrec] time-major record
+  int n;                          // time level held in `cur`
+  int sample;                     // record cur at the receivers
+  int zc;                         // z planes per block (3-D)
+};
+
+struct RevArgs {
+  Lay L;
+  const float *__restrict__ a;
+  const float *__restrict__ rc;   // p^R_n
+  float *__restrict__ rn;         // in: p^R_{n+1}; out: p^R_{n-1}
+  const float *__restrict__ bc;   // pbar_n
+  float *__restrict__ bn;         // in: pbar_{n+1}; out: pbar_{n-1}
+  float *__restrict__ num;        // pitched image accumulators
+  float *__restrict__ den;
+  const ShotInfo *info;
+  const float *wav;
+  const int *rec_off;
+  const int *tile_ptr;            // receivers of each block tile (CSR)
+  const int *tile_rec;
+  const float *seis_t;            // [nt+1][nrec]
+  int n;
+  int do_r, do_b;                 // update p^R / pbar at this level
+  int ix0, ix1, iy0, iy1, iz0, iz1; // interior box [lo, hi) in padded nodes
+  int zc;
+};
+
+// ---- launch geometry shared by the host (CSR) and the kernels ----
+constexpr int k2dWarps = 8;   // warps per block, stacked in z (2-D)
+constexpr int k2dRowsF = 4;   // rows per warp, forward kernel
+constexpr int k2dRowsR = 2;   // rows per warp, reverse kernel
+constexpr int k3dBY = 16;     // warps per block = y rows (3-D)
+constexpr int k3dZC = 64;     // z planes per block (3-D)
+
+} // namespace rbc
+
+// kernel launchers (rbc_kernels.cu)
+namespace rbc {
+void launch_fwd(const StepArgs &A, cudaStream_t s);
+void launch_rev(const RevArgs &A, cudaStream_t s);
+void rev_tiling(const Lay &L, int *gx, int *gy, int *gz, int *tz_or_by);
+void launch_copy_in(const Lay &L, const float *dense, float *pitched, cudaStream_t s);
+void launch_copy_out(const Lay &L, const float *pitched, float *dense, cudaStream_t s);
+void launch_transpose(const float *in, float *out, int rows, int cols, cudaStream_t s);
+void launch_accum_interior(const Lay &L, const float *pitched, float *dense, int nb, int nx,
+                           int ny, int nz, int overwrite, cudaStream_t s);
+void launch_max(const float *x, long long n, unsigned int *out_bits, cudaStream_t s);
+void launch_image_stack(const float *num, const float *den, const unsigned int *maxbits,
+                        float eps_rel, int nx, int ny, int nz, int off_x, int off_y, int sx,
+                        int sy, float *image, cudaStream_t s);
+void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_int, double v_lo,
+                      double v_hi, double v_max, uint64_t seed, int mode, double dt, double h,
+                      float *v_pad, float *a, cudaStream_t s);
+} // namespace rbc

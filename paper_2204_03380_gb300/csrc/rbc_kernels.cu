@@ -1,0 +1,615 @@
+// rbc_kernels.cu -- sm_103a kernels of librbc.
+//
+// Hot path (Algorithm 3 of arXiv:2204.03380, per time step):
+//   k_fwd2d / k_fwd3d : leapfrog step of Eq. 1 + fused point-source injection
+//                       + fused receiver sampling (Algorithm 1).
+//   k_rev2d / k_rev3d : one pass over the grid that advances the
+//                       reconstruction p^R (Eq. 6, source re-subtracted) and the
+//                       receiver wavefield pbar (Eq. 2, record injected) by one
+//                       level back in time and accumulates the two integrals of
+//                       the imaging condition (Eq. 3) -- a is read once for
+//                       both updates.
+// All are HBM/L2 streaming kernels (about 2 flop/byte): no tensor cores.
+// Every lane owns a float4 (4 consecutive x) so a warp covers a 128-float,
+// 512-byte row segment with fully coalesced 16-byte accesses; x neighbours
+// come from the adjacent lanes by warp shuffles (lanes 0/31 fetch the
+// 4-float halo), z neighbours from a register queue marching down z, and in
+// 3-D the y neighbours from a shared-memory plane tile.
+#include "rbc_internal.cuh"
+
+namespace rbc {
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float cmp(const float4 &v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float4 shfl_up4(float4 v) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+  v.z = __shfl_up_sync(0xffffffffu, v.z, 1);
+  v.w = __shfl_up_sync(0xffffffffu, v.w, 1);
+  return v;
+}
+__device__ __forceinline__ float4 shfl_dn4(float4 v) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+  v.z = __shfl_down_sync(0xffffffffu, v.z, 1);
+  v.w = __shfl_down_sync(0xffffffffu, v.w, 1);
+  return v;
+}
+
+// Leapfrog update of 4 consecutive nodes:
+//   out = (2 p - p_old) + a * sum_axes sum_k c_k [(p_{-k} - p) + (p_{+k} - p)]
+// lf/c/rt: x window (x0-4 .. x0+7); zq[0..8]: z window centred on zq[4] == c;
+// yq[0..8]: y window (3-D only).
+template <bool kThreeD>
+__device__ __forceinline__ float4 leap4(const float4 lf, const float4 c, const float4 rt,
+                                        const float4 *zq, const float4 *yq, const float4 po,
+                                        const float4 av) {
+  const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w, rt.x, rt.y, rt.z, rt.w};
+  float out[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float p = w[4 + i];
+    float s[5];
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+      float t = (w[4 + i - k] - p) + (w[4 + i + k] - p);
+      t += (cmp(zq[4 - k], i) - p) + (cmp(zq[4 + k], i) - p);
+      if (kThreeD) t += (cmp(yq[4 - k], i) - p) + (cmp(yq[4 + k], i) - p);
+      s[k] = t;
+    }
+    float lap = kC4 * s[4];
+    lap = fmaf(kC3, s[3], lap);
+    lap = fmaf(kC2, s[2], lap);
+    lap = fmaf(kC1, s[1], lap);
+    out[i] = fmaf(cmp(av, i), lap, 2.0f * p - cmp(po, i));
+  }
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// Subtract a point term from component (src - o) of v when the source node
+// falls in the float4 starting at offset o.
+__device__ __forceinline__ void point_sub(float4 &v, int d, float term) {
+  if (d == 0) v.x -= term;
+  else if (d == 1) v.y -= term;
+  else if (d == 2) v.z -= term;
+  else if (d == 3) v.w -= term;
+}
+
+__device__ __forceinline__ float4 masked_prod(const float4 u, const float4 v, int x0, int lo, int hi) {
+  float4 r;
+  r.x = (x0 + 0 >= lo && x0 + 0 < hi) ? u.x * v.x : 0.f;
+  r.y = (x0 + 1 >= lo && x0 + 1 < hi) ? u.y * v.y : 0.f;
+  r.z = (x0 + 2 >= lo && x0 + 2 < hi) ? u.z * v.z : 0.f;
+  r.w = (x0 + 3 >= lo && x0 + 3 < hi) ? u.w * v.w : 0.f;
+  return r;
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Record the current level at every receiver (Algorithm 1 "record
+// seismogram"): grid-strided so any block may sample any receiver.
+__device__ __forceinline__ void sample_receivers(const StepArgs &A, int nblocks, int bid) {
+  const int nrec = A.info->nrec;
+  const int nthr = blockDim.x * blockDim.y;
+  const int tid = bid * nthr + threadIdx.y * blockDim.x + threadIdx.x;
+  for (int r = tid; r < nrec; r += nblocks * nthr)
+    A.seis_t[(long long)A.n * nrec + r] = A.cur[A.rec_off[r]];
+}
+
+// Add the record at this block's receivers to the freshly written pbar_{n-1}
+// (Eq. 2 source term).  Runs after the block's stores; the fence + barrier
+// make those stores visible to the atomics of other threads of the block.
+__device__ __forceinline__ void inject_receivers(const RevArgs &A, int bid) {
+  const int beg = A.tile_ptr[bid], end = A.tile_ptr[bid + 1];
+  if (end > beg) __threadfence();
+  __syncthreads();
+  if (end <= beg) return;
+  const int nrec = A.info->nrec;
+  const float sc = A.info->rec_scale;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int k = beg + threadIdx.y * blockDim.x + threadIdx.x; k < end; k += nthr) {
+    const int r = A.tile_rec[k];
+    const int o = A.rec_off[r];
+    atomicAdd(A.bn + o, sc * A.a[o] * A.seis_t[(long long)A.n * nrec + r]);
+  }
+}
+
+// ------------------------------------------------------------------ 2-D ----
+// Block: 32 x k2dWarps threads; tile 128 (x) x k2dWarps*RZ (z); each warp
+// marches RZ rows with a (RZ + 8)-deep register queue.
+template <int RZ>
+__global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d(const StepArgs A) {
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int x0 = blockIdx.x * kTileX + lane * 4;
+  const int zb = (blockIdx.y * k2dWarps + w) * RZ;
+  const bool xok = x0 < L.NX4;
+  const int col = L.origin + x0;
+  if (A.sample) sample_receivers(A, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+  if (zb >= L.NZ) return;  // warp-uniform; no block barrier in this kernel
+  float4 q[RZ + 8];
+#pragma unroll
+  for (int j = 0; j < RZ + 8; ++j) {
+    const int z = zb - kHaloR + j;
+    q[j] = (xok && z < L.NZ + kHaloR) ? ldg4(A.cur + col + z * L.pitch) : zero4();
+  }
+  const int src = A.info->src_off;
+  const float fsrc = A.wav[A.n] * A.info->src_fwd;
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int z = zb + j;
+    if (z >= L.NZ) break;
+    const int o = col + z * L.pitch;
+    const float4 c = q[j + 4];
+    float4 lf = shfl_up4(c), rt = shfl_dn4(c);
+    if (lane == 0) lf = ldg4(A.cur + o - 4);
+    if (lane == 31) rt = ldg4(A.cur + o + 4);
+    if (xok) {
+      const float4 av = ldg4(A.a + o);
+      const float4 po = ld4(A.nxt + o);
+      float4 r = leap4<false>(lf, c, rt, &q[j], nullptr, po, av);
+      const int d = src - o;
+      if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
+      st4(A.nxt + o, r);
+    }
+  }
+}
+
+// One field of the reverse pass: advance (cur, nxt) and return the centre
+// values of `cur` for the imaging condition.
+template <int RZ>
+__device__ __forceinline__ void rev_field2d(const Lay &L, const float *__restrict__ a,
+                                            const float *__restrict__ cur, float *__restrict__ nxt,
+                                            bool update, int lane, int x0, int zb, bool xok,
+                                            int src, float fsrc, float4 *cen) {
+  const int col = L.origin + x0;
+  if (!update) {
+#pragma unroll
+    for (int j = 0; j < RZ; ++j) {
+      const int z = zb + j;
+      cen[j] = (xok && z < L.NZ) ? ldg4(cur + col + z * L.pitch) : zero4();
+    }
+    return;
+  }
+  float4 q[RZ + 8];
+#pragma unroll
+  for (int j = 0; j < RZ + 8; ++j) {
+    const int z = zb - kHaloR + j;
+    q[j] = (xok && z < L.NZ + kHaloR) ? ldg4(cur + col + z * L.pitch) : zero4();
+  }
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int z = zb + j;
+    cen[j] = q[j + 4];
+    if (z >= L.NZ) break;
+    const int o = col + z * L.pitch;
+    const float4 c = q[j + 4];
+    float4 lf = shfl_up4(c), rt = shfl_dn4(c);
+    if (lane == 0) lf = ldg4(cur + o - 4);
+    if (lane == 31) rt = ldg4(cur + o + 4);
+    if (xok) {
+      const float4 av = ldg4(a + o);
+      const float4 po = ld4(nxt + o);
+      float4 r = leap4<false>(lf, c, rt, &q[j], nullptr, po, av);
+      const int d = src - o;
+      if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
+      st4(nxt + o, r);
+    }
+  }
+}
+
+template <int RZ>
+__global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int x0 = blockIdx.x * kTileX + lane * 4;
+  const int zb = (blockIdx.y * k2dWarps + w) * RZ;
+  const bool xok = x0 < L.NX4;
+  const bool active = zb < L.NZ;  // warp-uniform
+  if (active) {
+    float4 cr[RZ], cb[RZ];
+    const int src = A.info->src_off;
+    const float fsrc = A.do_r ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
+    // Eq. 6: reconstruction (exact inverse of the forward step)
+    rev_field2d<RZ>(L, A.a, A.rc, A.rn, A.do_r != 0, lane, x0, zb, xok, src, fsrc, cr);
+    // Eq. 2: receiver wavefield (the record is added below, after the store)
+    rev_field2d<RZ>(L, A.a, A.bc, A.bn, A.do_b != 0, lane, x0, zb, xok, -1, 0.f, cb);
+    // Eq. 3: the two time integrals, interior only
+    if (xok && x0 + 3 >= A.ix0 && x0 < A.ix1) {
+#pragma unroll
+      for (int j = 0; j < RZ; ++j) {
+        const int z = zb + j;
+        if (z >= A.iz0 && z < A.iz1) {
+          const int o = L.origin + x0 + z * L.pitch;
+          st4(A.num + o, add4(ld4(A.num + o), masked_prod(cr[j], cb[j], x0, A.ix0, A.ix1)));
+          st4(A.den + o, add4(ld4(A.den + o), masked_prod(cr[j], cr[j], x0, A.ix0, A.ix1)));
+        }
+      }
+    }
+  }
+  if (A.do_b) inject_receivers(A, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// ------------------------------------------------------------------ 3-D ----
+// Block: 32 x BY threads = a 128 (x) x BY (y) column tile marching over zc
+// planes.  Each plane of the field is staged in shared memory with 4 halo
+// rows in y and one float4 of halo in x per side; z neighbours stay in a
+// 9-deep register queue.
+template <int BY>
+__global__ void __launch_bounds__(32 * BY) k_fwd3d(const StepArgs A) {
+  __shared__ float4 sm[BY + 8][34];
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int x0 = blockIdx.x * kTileX + lane * 4;
+  const int y0 = blockIdx.y * BY, y = y0 + w;
+  const int zb = blockIdx.z * A.zc;
+  const int ze = min(zb + A.zc, L.NZ);
+  const bool xok = x0 < L.NX4, yok = y < L.NY;
+  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  if (A.sample) sample_receivers(A, gridDim.x * gridDim.y * gridDim.z, bid);
+  const int col = L.origin + y * L.pitch + x0;
+  // y halo row fetched by this warp (warps 0-3 above the tile, the last 4 below)
+  const int hslot = (w < 4) ? w : (w >= BY - 4 ? w + 8 : -1);
+  const int hy = (w < 4) ? y0 - 4 + w : y0 + w + 4;
+  const int hcol = L.origin + hy * L.pitch + x0;
+  float4 q[9];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int z = zb - kHaloR + j;
+    q[j] = (xok && z < L.NZ + kHaloR) ? ldg4(A.cur + col + z * L.plane) : zero4();
+  }
+  const int src = A.info->src_off;
+  const float fsrc = A.wav[A.n] * A.info->src_fwd;
+#pragma unroll 1
+  for (int z = zb; z < ze; ++z) {
+    const int zo = z * L.plane;
+    q[8] = (xok && z + kHaloR < L.NZ + kHaloR) ? ldg4(A.cur + col + zo + kHaloR * L.plane) : zero4();
+    sm[w + 4][lane + 1] = q[4];
+    if (hslot >= 0) sm[hslot][lane + 1] = xok ? ldg4(A.cur + hcol + zo) : zero4();
+    if (lane == 0) sm[w + 4][0] = ldg4(A.cur + col + zo - 4);
+    if (lane == 31) sm[w + 4][33] = ldg4(A.cur + col + zo + 4);
+    __syncthreads();
+    if (xok && yok) {
+      float4 yq[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) yq[k] = sm[w + k][lane + 1];
+      const int o = col + zo;
+      const float4 av = ldg4(A.a + o);
+      const float4 po = ld4(A.nxt + o);
+      float4 r = leap4<true>(sm[w + 4][lane], q[4], sm[w + 4][lane + 2], q, yq, po, av);
+      const int d = src - o;
+      if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
+      st4(A.nxt + o, r);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+  }
+}
+
+template <int BY>
+__global__ void __launch_bounds__(32 * BY) k_rev3d(const RevArgs A) {
+  __shared__ float4 smr[BY + 8][34];
+  __shared__ float4 smb[BY + 8][34];
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int x0 = blockIdx.x * kTileX + lane * 4;
+  const int y0 = blockIdx.y * BY, y = y0 + w;
+  const int zb = blockIdx.z * A.zc;
+  const int ze = min(zb + A.zc, L.NZ);
+  const bool xok = x0 < L.NX4, yok = y < L.NY;
+  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const int col = L.origin + y * L.pitch + x0;
+  const int hslot = (w < 4) ? w : (w >= BY - 4 ? w + 8 : -1);
+  const int hy = (w < 4) ? y0 - 4 + w : y0 + w + 4;
+  const int hcol = L.origin + hy * L.pitch + x0;
+  const bool do_r = A.do_r != 0, do_b = A.do_b != 0;
+  const bool img_xy = xok && yok && y >= A.iy0 && y < A.iy1 && x0 + 3 >= A.ix0 && x0 < A.ix1;
+  float4 qr[9], qb[9];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int z = zb - kHaloR + j;
+    const bool ok = xok && z < L.NZ + kHaloR;
+    qr[j] = ok ? ldg4(A.rc + col + z * L.plane) : zero4();
+    qb[j] = ok ? ldg4(A.bc + col + z * L.plane) : zero4();
+  }
+  const int src = A.info->src_off;
+  const float fsrc = A.do_r ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
+#pragma unroll 1
+  for (int z = zb; z < ze; ++z) {
+    const int zo = z * L.plane;
+    const bool ok = xok && z + kHaloR < L.NZ + kHaloR;
+    qr[8] = ok ? ldg4(A.rc + col + zo + kHaloR * L.plane) : zero4();
+    qb[8] = ok ? ldg4(A.bc + col + zo + kHaloR * L.plane) : zero4();
+    if (do_r || do_b) {
+      smr[w + 4][lane + 1] = qr[4];
+      smb[w + 4][lane + 1] = qb[4];
+      if (hslot >= 0) {
+        smr[hslot][lane + 1] = xok ? ldg4(A.rc + hcol + zo) : zero4();
+        smb[hslot][lane + 1] = xok ? ldg4(A.bc + hcol + zo) : zero4();
+      }
+      if (lane == 0) {
+        smr[w + 4][0] = ldg4(A.rc + col + zo - 4);
+        smb[w + 4][0] = ldg4(A.bc + col + zo - 4);
+      }
+      if (lane == 31) {
+        smr[w + 4][33] = ldg4(A.rc + col + zo + 4);
+        smb[w + 4][33] = ldg4(A.bc + col + zo + 4);
+      }
+    }
+    __syncthreads();
+    if (xok && yok) {
+      const int o = col + zo;
+      const float4 av = ldg4(A.a + o);
+      float4 yq[9];
+      if (do_r) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) yq[k] = smr[w + k][lane + 1];
+        const float4 po = ld4(A.rn + o);
+        float4 r = leap4<true>(smr[w + 4][lane], qr[4], smr[w + 4][lane + 2], qr, yq, po, av);
+        const int d = src - o;
+        if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
+        st4(A.rn + o, r);
+      }
+      if (do_b) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) yq[k] = smb[w + k][lane + 1];
+        const float4 po = ld4(A.bn + o);
+        st4(A.bn + o, leap4<true>(smb[w + 4][lane], qb[4], smb[w + 4][lane + 2], qb, yq, po, av));
+      }
+      if (img_xy && z >= A.iz0 && z < A.iz1) {
+        st4(A.num + o, add4(ld4(A.num + o), masked_prod(qr[4], qb[4], x0, A.ix0, A.ix1)));
+        st4(A.den + o, add4(ld4(A.den + o), masked_prod(qr[4], qr[4], x0, A.ix0, A.ix1)));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      qr[k] = qr[k + 1];
+      qb[k] = qb[k + 1];
+    }
+  }
+  if (do_b) inject_receivers(A, bid);
+}
+
+// ------------------------------------------------------------ launchers ----
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+void launch_fwd(const StepArgs &A, cudaStream_t s) {
+  const Lay &L = A.L;
+  if (L.ndim == 2) {
+    dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarps * k2dRowsF));
+    k_fwd2d<k2dRowsF><<<grid, dim3(32, k2dWarps), 0, s>>>(A);
+  } else {
+    dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NY, k3dBY), cdiv(L.NZ, A.zc));
+    k_fwd3d<k3dBY><<<grid, dim3(32, k3dBY), 0, s>>>(A);
+  }
+}
+
+void rev_tiling(const Lay &L, int *gx, int *gy, int *gz, int *t) {
+  if (L.ndim == 2) {
+    *gx = cdiv(L.NX, kTileX);
+    *gy = cdiv(L.NZ, k2dWarps * k2dRowsR);
+    *gz = 1;
+    *t = k2dWarps * k2dRowsR;
+  } else {
+    *gx = cdiv(L.NX, kTileX);
+    *gy = cdiv(L.NY, k3dBY);
+    *gz = cdiv(L.NZ, k3dZC);
+    *t = k3dBY;
+  }
+}
+
+void launch_rev(const RevArgs &A, cudaStream_t s) {
+  int gx, gy, gz, t;
+  rev_tiling(A.L, &gx, &gy, &gz, &t);
+  if (A.L.ndim == 2) {
+    k_rev2d<k2dRowsR><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
+  } else {
+    k_rev3d<k3dBY><<<dim3(gx, gy, gz), dim3(32, k3dBY), 0, s>>>(A);
+  }
+}
+
+// ----------------------------------------------------------- auxiliaries ----
+__global__ void k_copy_in(const Lay L, const float *__restrict__ dense, float *__restrict__ pitched) {
+  const long long n = (long long)L.NX * L.NY * L.NZ;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L.NX);
+    const long long r = i / L.NX;
+    const int y = (int)(r % L.NY);
+    const int z = (int)(r / L.NY);
+    pitched[lay_off(L, x, y, z)] = dense[i];
+  }
+}
+
+__global__ void k_copy_out(const Lay L, const float *__restrict__ pitched, float *__restrict__ dense) {
+  const long long n = (long long)L.NX * L.NY * L.NZ;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L.NX);
+    const long long r = i / L.NX;
+    const int y = (int)(r % L.NY);
+    const int z = (int)(r / L.NY);
+    dense[i] = pitched[lay_off(L, x, y, z)];
+  }
+}
+
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+void launch_copy_in(const Lay &L, const float *dense, float *pitched, cudaStream_t s) {
+  const long long n = (long long)L.NX * L.NY * L.NZ;
+  k_copy_in<<<grid_for(n, 256), 256, 0, s>>>(L, dense, pitched);
+}
+
+void launch_copy_out(const Lay &L, const float *pitched, float *dense, cudaStream_t s) {
+  const long long n = (long long)L.NX * L.NY * L.NZ;
+  k_copy_out<<<grid_for(n, 256), 256, 0, s>>>(L, pitched, dense);
+}
+
+// out[c][r] = in[r][c] for an rows x cols matrix (32 x 32 shared tiles).
+__global__ void k_transpose(const float *__restrict__ in, float *__restrict__ out, int rows, int cols) {
+  __shared__ float t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[k][threadIdx.x] = in[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(long long)c * rows + r] = t[threadIdx.x][k];
+  }
+}
+
+void launch_transpose(const float *in, float *out, int rows, int cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  dim3 grid(cdiv(cols, 32), cdiv(rows, 32));
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
+}
+
+__global__ void k_accum_interior(const Lay L, const float *__restrict__ pitched, float *__restrict__ dense,
+                                 int nb, int nx, int ny, int nz, int overwrite) {
+  const long long n = (long long)nx * ny * nz;
+  const int yo = (L.ndim == 3) ? nb : 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny);
+    const int z = (int)(r / ny);
+    const float v = pitched[lay_off(L, x + nb, y + yo, z + nb)];
+    dense[i] = overwrite ? v : dense[i] + v;
+  }
+}
+
+void launch_accum_interior(const Lay &L, const float *pitched, float *dense, int nb, int nx, int ny,
+                           int nz, int overwrite, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  k_accum_interior<<<grid_for(n, 256), 256, 0, s>>>(L, pitched, dense, nb, nx, ny, nz, overwrite);
+}
+
+// Maximum of non-negative values as ordered uint bits (atomicMax).
+__global__ void k_max(const float *__restrict__ x, long long n, unsigned int *out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, x[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(out, __float_as_uint(m));
+  }
+}
+
+void launch_max(const float *x, long long n, unsigned int *out_bits, cudaStream_t s) {
+  k_max<<<grid_for(n, 256), 256, 0, s>>>(x, n, out_bits);
+}
+
+__global__ void k_image_stack(const float *__restrict__ num, const float *__restrict__ den,
+                              const unsigned int *__restrict__ maxbits, float eps_rel, int nx, int ny,
+                              int nz, int off_x, int off_y, int sx, int sy, float *__restrict__ image) {
+  const long long n = (long long)nx * ny * nz;
+  const float e = eps_rel * __uint_as_float(*maxbits);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny);
+    const int z = (int)(r / ny);
+    image[((long long)z * sy + y + off_y) * sx + x + off_x] += num[i] / (den[i] + e);
+  }
+}
+
+void launch_image_stack(const float *num, const float *den, const unsigned int *maxbits, float eps_rel,
+                        int nx, int ny, int nz, int off_x, int off_y, int sx, int sy, float *image,
+                        cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  k_image_stack<<<grid_for(n, 256), 256, 0, s>>>(num, den, maxbits, eps_rel, nx, ny, nz, off_x, off_y,
+                                                 sx, sy, image);
+}
+
+// ----------------------------------------------------- random boundary ----
+// splitmix64 (Steele, Lea & Flood 2014) as a counter generator: draw j of
+// stream `seed` is the finaliser applied to seed + j * golden-gamma.
+__device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t j) {
+  uint64_t z = seed + j * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double u01(uint64_t seed, uint64_t j) {
+  return (double)(sm64(seed, j) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ int pad_distance(int q, int nb, int n) {
+  return q < nb ? nb - q : (q >= nb + n ? q - (nb + n - 1) : 0);
+}
+
+// Section 4.3: random velocities in an nb-cell pad, blended towards the
+// nearest interior value with a coefficient between the Gaussian (Eq. 5) and
+// linear (Eq. 4) tapers; a = (v dt / h)^2.
+__global__ void k_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *__restrict__ v_int,
+                            double v_lo, double v_hi, double v_max, uint64_t seed, int mode, double dt,
+                            double h, float *__restrict__ v_pad, float *__restrict__ a) {
+  const int NX = nx + 2 * nb, NZ = nz + 2 * nb;
+  const int NY = (ndim == 3) ? ny + 2 * nb : 1;
+  const int nyi = (ndim == 3) ? ny : 1;
+  const long long n = (long long)NX * NY * NZ;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < n;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(L % NX);
+    const long long r = L / NX;
+    const int y = (int)(r % NY);
+    const int z = (int)(r / NY);
+    int i = max(pad_distance(x, nb, nx), pad_distance(z, nb, nz));
+    if (ndim == 3) i = max(i, pad_distance(y, nb, ny));
+    const int ex = min(max(x - nb, 0), nx - 1), ez = min(max(z - nb, 0), nz - 1);
+    const int ey = (ndim == 3) ? min(max(y - nb, 0), ny - 1) : 0;
+    double v = (double)v_int[((long long)ez * nyi + ey) * nx + ex];
+    if (i > 0) {
+      const double g = (double)(nb - i) / (double)(nb - 1);
+      const double uu = (double)(i - 1) / (double)(nb - 1);
+      const double hh = exp(-120.0 * uu * uu);
+      const double lo = hh < g ? hh : g, up = hh < g ? g : hh;
+      const double c = lo + (up - lo) * u01(seed, 2ULL * (uint64_t)L + 1ULL);
+      const double vr = v_lo + (v_hi - v_lo) * u01(seed, 2ULL * (uint64_t)L + 2ULL);
+      if (mode == 0) {
+        v = c * v + (1.0 - c) * vr;
+      } else {
+        v = c * vr;
+        if (v < v_lo) v = v_lo;
+      }
+      if (v > v_max) v = v_max;
+    }
+    if (v_pad) v_pad[L] = (float)v;
+    const double cc = v * dt / h;
+    a[L] = (float)(cc * cc);
+  }
+}
+
+void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_int, double v_lo,
+                      double v_hi, double v_max, uint64_t seed, int mode, double dt, double h,
+                      float *v_pad, float *a, cudaStream_t s) {
+  const long long n = (long long)(nx + 2 * nb) * (ndim == 3 ? ny + 2 * nb : 1) * (nz + 2 * nb);
+  k_rbc_build<<<grid_for(n, 256), 256, 0, s>>>(ndim, nx, ny, nz, nb, v_int, v_lo, v_hi, v_max, seed,
+                                               mode, dt, h, v_pad, a);
+}
+
+} // namespace rbc

@@ -1,0 +1,66 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/rbc.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rbc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rbc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as G
+    b = G._builder()
+    b.build()
+    return C.CDLL(b.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 8
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_exposes_the_same_names():
+    import paper_2204_03380_gb300 as R
+    assert sorted(R.EXPORTED) == _declared()
+
+
+def test_bad_arguments_are_rejected_on_the_host():
+    import paper_2204_03380_gb300 as R
+    lib = R._native._lib
+    g = R.make_grid(2, 10, 1, 10, 5, 10.0, 1e-3, 10)
+    out = C.c_void_p()
+    assert lib.rbc_create(None, None, C.byref(out)) == 1
+    assert "NULL" in R.rbc_last_error()
+    bad = R.make_grid(4, 10, 1, 10, 5, 10.0, 1e-3, 10)
+    assert lib.rbc_create(C.byref(bad), C.c_void_p(16), C.byref(out)) == 1
+    fs = R.make_grid(2, 10, 1, 10, 5, 10.0, 1e-3, 10, free_surface=1)
+    assert lib.rbc_create(C.byref(fs), C.c_void_p(16), C.byref(out)) == 6
+    nb1 = R.make_grid(2, 10, 1, 10, 1, 10.0, 1e-3, 10)
+    assert lib.rbc_build_velocity(C.byref(nb1), C.c_void_p(16), 1.0, 2.0, 2.0, 0, 0, None,
+                                  C.c_void_p(16), None) == 1
+    assert lib.rbc_build_velocity(C.byref(g), C.c_void_p(16), 1.0, 2.0, 2.0, 0, 2, None,
+                                  C.c_void_p(16), None) == 1
+    assert lib.rbc_build_velocity(C.byref(g), C.c_void_p(16), 3.0, 2.0, 2.0, 0, 0, None,
+                                  C.c_void_p(16), None) == 1
+    # image stack window checks
+    shot = R.make_grid(2, 10, 1, 8, 5, 10.0, 1e-3, 10)
+    survey = R.make_grid(2, 15, 1, 8, 5, 10.0, 1e-3, 10)
+    p = C.c_void_p(16)
+    assert lib.rbc_image_stack(C.byref(shot), p, p, 1e-6, 6, 0, C.byref(survey), p, None) == 1
+    assert lib.rbc_image_stack(C.byref(shot), p, p, 1e-6, 0, 1, C.byref(survey), p, None) == 1
+    other = R.make_grid(2, 15, 1, 9, 5, 10.0, 1e-3, 10)
+    assert lib.rbc_image_stack(C.byref(shot), p, p, 1e-6, 0, 0, C.byref(other), p, None) == 1
+    assert lib.rbc_model(None, None, None, 0, None, None, None) == 1
+    assert lib.rbc_set_snapshots(None, 0, None, None, None, None) == 1

@@ -1,0 +1,152 @@
+"""GPU (sm_103a, through the C ABI) against the FP64 oracle on the same seeded
+inputs: random boundary, seismograms (Algorithm 1), panels, reconstructed and
+receiver wavefields, the two integrals of Eq. 3 and the image (Algorithm 3).
+Tolerance: relative L2 <= 1e-4 for every floating-point output."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from rtm_cases import TOL, case_2d, case_3d, gpu_build, gpu_shot, oracle_a, oracle_shot, rel, rel_image
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_2204_03380_gb300 as R
+    return R
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("dims", [(2, 37, 1, 23, 6), (2, 300, 1, 200, 50), (3, 21, 17, 13, 5)])
+def test_random_boundary_matches_oracle(R, dims, mode):
+    ndim, nx, ny, nz, nb = dims
+    base = W.SMALL_2D if ndim == 2 else W.SHOT_3D
+    w = W.scaled(base, nx=nx, ny=ny, nz=nz, nb=nb, name="rbc")
+    v = (W.three_layers(nx, nz, (nz // 3, 2 * nz // 3)) if ndim == 2
+         else W.dipping_salt_3d(nx, ny, nz, 2))
+    _, a, vp = gpu_build(R, torch, w, v, mode)
+    vp_o, a_o = oracle_a(w, v, mode)
+    # one fp32 rounding of the same fp64 value: equal up to a possible last-bit tie
+    np.testing.assert_allclose(a.cpu().numpy(), a_o, rtol=1.2e-7, atol=0)
+    np.testing.assert_allclose(vp.cpu().numpy(), vp_o.astype(np.float32), rtol=1.2e-7, atol=0)
+
+
+CASES_2D = [
+    ("config1_full", 200, 200, 50, 1000),
+    ("ragged_small", 37, 23, 6, 400),
+    ("multi_tile_x", 300, 41, 9, 500),
+    ("one_column", 1, 30, 4, 200),
+    ("one_row", 50, 1, 4, 200),
+]
+
+
+def snap_err(g, o):
+    """Snapshot error relative to the largest snapshot of the same field: the
+    fp32 leapfrog (forward or reversed) carries an absolute rounding error at
+    the scale of the field over the whole record, so a level where the exact
+    field is still tiny is judged against that scale, not its own norm."""
+    scale = max(np.linalg.norm(x) for x in o)
+    return max(np.linalg.norm(a - b) for a, b in zip(g, o)) / scale
+
+
+@pytest.mark.parametrize("case", CASES_2D, ids=lambda c: c[0])
+def test_2d_modeling_and_rtm_match_oracle(R, case):
+    w, v, src, rec, wav = case_2d(*case)
+    snaps = (0, w.nt // 3, w.nt // 2, 3 * w.nt // 4, w.nt - 1, w.nt)
+    g = gpu_shot(R, torch, w, v, src, rec, wav, snaps=snaps)
+    o = oracle_shot(w, v, src, rec, wav, snaps=snaps)
+    assert rel(g["seis"], o["seis"]) <= TOL
+    assert rel(g["prev"], o["prev"]) <= TOL and rel(g["last"], o["last"]) <= TOL
+    assert snap_err(g["pf"], o["pf"]) <= TOL
+    assert snap_err(g["pr"], o["pf"]) <= TOL      # reconstruction against the forward field
+    assert snap_err(g["pr"], o["pr"]) <= TOL
+    assert snap_err(g["pb"], o["pb"]) <= TOL
+    assert rel(g["num"], o["num"]) <= TOL
+    assert rel(g["den"], o["den"]) <= TOL
+    e, frac = rel_image(g["img"], o["img"], o["den"])
+    assert e <= TOL and frac > 0.05, (e, frac)
+
+
+def test_2d_migration_with_a_different_model_and_edge_geometry(R):
+    # migrate data modeled in the true model with a smoothed model; receivers
+    # include duplicates, pad cells and the grid corners; source in the pad
+    w, v, _, _, wav = case_2d("edge", 70, 45, 7, 300, seed=4, layered=False)
+    vm = W.smooth_slowness(v, 4.0)
+    NX, NZ = w.nx + 2 * w.nb, w.nz + 2 * w.nb
+    rec = np.array([[0, 0, 0], [NX - 1, 0, NZ - 1], [10, 0, 8], [10, 0, 8], [NX - 1, 0, 0],
+                    [0, 0, NZ - 1], [33, 0, 9], [127, 0, 12] if NX > 127 else [NX - 2, 0, 12]], np.int32)
+    src = np.array([3, 0, 2], np.int32)
+    g = gpu_shot(R, torch, w, v, src, rec, wav, v_rtm=vm)
+    o = oracle_shot(w, v, src, rec, wav, v_rtm=vm)
+    assert rel(g["seis"], o["seis"]) <= TOL
+    for k in ("num", "den"):
+        assert rel(g[k], o[k]) <= TOL, k
+    assert rel_image(g["img"], o["img"], o["den"])[0] <= TOL
+
+
+def test_2d_literal_eq6_without_source_reinjection(R):
+    w, v, src, rec, wav = case_2d("noreinj", 60, 40, 8, 250)
+    g = gpu_shot(R, torch, w, v, src, rec, wav, reinject=False)
+    o = oracle_shot(w, v, src, rec, wav, reinject=False)
+    for k in ("num", "den"):
+        assert rel(g[k], o[k]) <= TOL, k
+
+
+def test_2d_no_receivers(R):
+    w, v, src, _, wav = case_2d("norec", 40, 30, 5, 100)
+    rec = np.zeros((0, 3), np.int32)
+    g = gpu_shot(R, torch, w, v, src, rec, wav, seis_in=np.zeros((0, w.nt + 1)))
+    o = oracle_shot(w, v, src, rec, wav, seis_in=np.zeros((0, w.nt + 1)))
+    assert np.all(g["num"] == 0) and np.all(o["num"] == 0)
+    assert rel(g["den"], o["den"]) <= TOL
+
+
+CASES_3D = [
+    ("small_ragged", 21, 17, 13, 5, 250),
+    ("two_z_chunks_three_y_tiles", 30, 26, 60, 6, 250),
+    ("wide_x", 150, 9, 10, 4, 250),
+]
+
+
+@pytest.mark.parametrize("case", CASES_3D, ids=lambda c: c[0])
+def test_3d_modeling_and_rtm_match_oracle(R, case):
+    w, v, src, rec, wav = case_3d(*case)
+    snaps = (w.nt // 2, 3 * w.nt // 4, w.nt)
+    g = gpu_shot(R, torch, w, v, src, rec, wav, snaps=snaps)
+    o = oracle_shot(w, v, src, rec, wav, snaps=snaps)
+    assert rel(g["seis"], o["seis"]) <= TOL
+    assert rel(g["last"], o["last"]) <= TOL
+    assert snap_err(g["pr"], o["pr"]) <= TOL
+    assert snap_err(g["pb"], o["pb"]) <= TOL
+    for k in ("num", "den"):
+        assert rel(g[k], o[k]) <= TOL, k
+    assert rel_image(g["img"], o["img"], o["den"])[0] <= TOL
+
+
+def test_unstable_model_is_rejected(R):
+    w = W.scaled(W.SMALL_2D, nx=20, nz=20, nb=4, nt=10, name="cfl")
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, 2.5e-3, w.nt)   # v dt/h = 1.125
+    a = torch.full(g.padded, 1.125 ** 2, dtype=torch.float32, device="cuda")
+    with pytest.raises(R.RBCError) as e:
+        R.rbc_create(g, a)
+    assert e.value.code == 2
+    ok = torch.full(g.padded, 0.3, dtype=torch.float32, device="cuda")   # a * 2 * 6.5 < 4
+    R.rbc_destroy(R.rbc_create(g, ok))
+
+
+def test_bad_nodes_are_rejected(R):
+    g = R.make_grid(2, 20, 1, 20, 4, 10.0, 1e-3, 10)
+    a = torch.full(g.padded, 0.1, dtype=torch.float32, device="cuda")
+    ctx = R.rbc_create(g, a)
+    try:
+        wav = torch.zeros(10, dtype=torch.float32, device="cuda")
+        seis = torch.zeros((1, 11), dtype=torch.float32, device="cuda")
+        for src, rec in (([28, 0, 5], [[1, 0, 1]]), ([5, 0, 5], [[1, 1, 1]]), ([5, 0, 5], [[-1, 0, 1]])):
+            with pytest.raises(R.RBCError) as e:
+                R.rbc_model(ctx, src, wav, rec, seis)
+            assert e.value.code == 1
+    finally:
+        R.rbc_destroy(ctx)

@@ -213,7 +213,7 @@ def survey_2d_inputs(w: Workload = SURVEY_2D, model_seed: int = 7):
     v_true = faulted_layers(w.nx, w.nz, model_seed, 1500.0, 5500.0)
     v_mig = smooth_slowness(v_true, 20.0)
     return dict(v_true=v_true, v_mig=v_mig, shots=shot_columns(w, w.nshots),
-                rec=surface_line(w, step=5), wavelet=ricker(w.nt, w.dt, w.f_peak))
+                rec=surface_line(w, step=5, x_to=5 * 460), wavelet=ricker(w.nt, w.dt, w.f_peak))
 
 
 def shot_3d_inputs(w: Workload = SHOT_3D, model_seed: int = 11):
