@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--shots-per-step", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--nt", type=int, default=None,
+                   help="record length override (default: the workload's 12500 steps); only for "
+                        "small profiler captures")
     return p.parse_args()
 
 
@@ -234,6 +237,8 @@ def main():
         torch.cuda.synchronize()
 
     w = W.SURVEY_2D
+    if args.nt:
+        w = W.dataclasses.replace(w, nt=args.nt, name=f"{w.name}_nt{args.nt}")
     inp = W.survey_2d_inputs(w)
     g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
     dev = torch.device("cuda", local)
