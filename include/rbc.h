@@ -185,6 +185,35 @@ int rbc_get_panels(rbc_ctx *ctx, float *prev_dev, float *last_dev,
  */
 int rbc_phase_timing(rbc_ctx *ctx, int enable, double *out);
 
+/*
+ * rbc_model_static -- the same seismic modeling as rbc_model (Algorithm 1,
+ * one shot), for callers that cannot allocate device memory.  The paper has
+ * no counterpart: it is an interface addition.
+ *   Some callers cannot call cudaMalloc: code that runs while a caching
+ *   allocator owns (or has exhausted) the device heap, plugins whose host
+ *   runtime forbids allocation on its worker threads, and real-time loops
+ *   where an allocation's implicit synchronisation or failure is not
+ *   acceptable.  This call needs no context and allocates nothing: its
+ *   scratch (coefficient in the zero-haloed layout, two wavefield panels,
+ *   the time-major record, the shot tables) lives in one file-scope device
+ *   array of 16 MiB (4 Mi floats) that every GPU loading the library holds
+ *   until the process exits.
+ *   Arguments are those of rbc_create (grid, a_dev) and rbc_model (source,
+ *   wavelet, receivers, seis_dev [nrec][nt + 1] output), all caller-owned.
+ *   Grids and records whose scratch exceeds the 16 MiB maximum return
+ *   RBC_EINVAL with the needed size in the message; nothing is queued.
+ *   All calls on a device share the array and it keeps the previous call's
+ *   contents; each call clears its fields itself.  Calls whose work overlaps
+ *   on the GPU (other streams or host threads) race on the array: serialise
+ *   them.  The first call on a device looks up the array's device address
+ *   with that device current; make it before any stream capture starts.
+ *   The stability check of rbc_create runs first and waits on `stream`.
+ * Errors: RBC_EINVAL, RBC_ECFL, RBC_ENOTSUP (free_surface), RBC_ECUDA.
+ */
+int rbc_model_static(const rbc_grid *g, const float *a_dev,
+                     const int *src_host, const float *wavelet_dev, int nrec,
+                     const int *rec_host, float *seis_dev, void *stream);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char *rbc_last_error(void);
 

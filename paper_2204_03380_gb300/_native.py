@@ -66,6 +66,8 @@ def _load():
     lib.rbc_set_snapshots.argtypes = [P, I, P, P, P, P]
     lib.rbc_get_panels.argtypes = [P, P, P, P]
     lib.rbc_phase_timing.argtypes = [P, I, P]
+    lib.rbc_model_static.argtypes = [G, P, P, P, I, P, P, P]
+    lib.rbc_model_static.restype = I
     lib.rbc_last_error.restype = C.c_char_p
     lib.rbc_launch_count.argtypes = [I]
     lib.rbc_launch_count.restype = C.c_longlong
@@ -78,7 +80,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc_rtm_shot",
             "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing",
-            "rbc_last_error", "rbc_launch_count")
+            "rbc_model_static", "rbc_last_error", "rbc_launch_count")
 
 
 def _check(code):
@@ -171,6 +173,18 @@ def rbc_phase_timing(ctx, enable):
         return None
     return dict(fwd_ms=out[0], rev_ms=out[1], fwd_launches=int(out[2]), rev_launches=int(out[3]),
                 shots=int(out[4]))
+
+
+def rbc_model_static(grid, a, src, wavelet, rec, seis, stream=None):
+    """Modeling without a context and without any device allocation: the
+    scratch is the library's fixed 16 MiB per-device workspace (for callers
+    that cannot call cudaMalloc).  Calls sharing a device must not overlap."""
+    s = _nodes(src, 1)
+    r = _nodes(rec)
+    _check(_lib.rbc_model_static(C.byref(grid), _dev(a, grid.padded, "a"), s.ctypes.data_as(C.c_void_p),
+                                 _dev(wavelet, None, "wavelet"), r.shape[0],
+                                 r.ctypes.data_as(C.c_void_p) if r.size else None,
+                                 _dev(seis, None, "seis") if r.shape[0] else None, _stream(stream)))
 
 
 def rbc_last_error() -> str:

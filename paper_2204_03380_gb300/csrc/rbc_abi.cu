@@ -82,6 +82,14 @@ Lay make_layout(const rbc_grid *g) {
 
 } // namespace
 
+namespace rbc {
+// Set this thread's error message from another translation unit.
+int set_error(int code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+} // namespace rbc
+
 struct rbc_ctx {
   rbc_grid g;
   Lay L;
