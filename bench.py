@@ -49,16 +49,26 @@ REFERENCE_STEP_STEPS = 40     # --impl reference: per step, one full-grid shot o
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=None, help="default 30 (survey2d), 3 (shot3d)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--shots-per-step", type=int, default=8)
+    p.add_argument("--shots-per-step", type=int, default=None, help="default 8 (survey2d), 1 (shot3d)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--nt", type=int, default=None,
-                   help="record length override (default: the workload's 12500 steps); only for "
+                   help="record length override (default: the workload's full record); only for "
                         "small profiler captures")
-    return p.parse_args()
+    p.add_argument("--interior", type=int, nargs="+", default=None,
+                   help="interior size override (nx nz | nx ny nz); only for small profiler captures")
+    p.add_argument("--workload", choices=["survey2d", "shot3d"], default="survey2d",
+                   help="survey2d: the 240-shot 2-D survey (default); shot3d: one 3-D shot on "
+                        "500 x 500 x 300 + 40 (one step = one RTM shot)")
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = 30 if a.workload == "survey2d" else 3
+    if a.shots_per_step is None:
+        a.shots_per_step = 8 if a.workload == "survey2d" else 1
+    return a
 
 
 # ----------------------------------------------------------------- clocks ---
@@ -153,6 +163,31 @@ def fwd_bytes_per_launch(w) -> int:
     return 16 * w.npad
 
 
+def load_workload(W, args):
+    """Workload preset, its inputs and one source node per shot (padded frame)."""
+    if args.workload == "survey2d":
+        w = W.SURVEY_2D
+        if args.interior:
+            w = W.scaled(w, nx=args.interior[0], nz=args.interior[-1], name=f"{w.name}_int{args.interior}")
+        if args.nt:
+            w = W.dataclasses.replace(w, nt=args.nt, name=f"{w.name}_nt{args.nt}")
+        inp = W.survey_2d_inputs(w)
+        inp["srcs"] = [W.source_at(w, int(x)) for x in inp["shots"]]
+    else:
+        w = W.SHOT_3D
+        if args.interior:
+            nx, ny, nz = args.interior
+            w = W.scaled(w, nx=nx, ny=ny, nz=nz, name=f"3d_{nx}x{ny}x{nz}_nb{w.nb}")
+        if args.nt:
+            w = W.dataclasses.replace(w, nt=args.nt, name=f"{w.name}_nt{args.nt}")
+        inp = W.shot_3d_inputs(w)
+        inp["v_true"] = inp["v"]
+        inp["v_mig"] = W.smooth_slowness(inp["v"], 8.0)
+        inp["srcs"] = [inp["src"]]
+        inp["shots"] = np.array([w.nx // 2])
+    return w, inp
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -168,12 +203,13 @@ def oracle_rtm_sample(w, inp, nsteps: int):
     ws = W.dataclasses.replace(w, nt=nsteps)
     vp = oracle.rbc_velocity(inp["v_mig"].astype(np.float32), ws.nb, ws.v_lo, ws.v_hi, ws.v_max, ws.rbc_seed)
     a = oracle.coef(vp, ws.dt, ws.h)[1].astype(np.float64)
-    src = W.source_at(ws, int(inp["shots"][0]))
+    src = inp["srcs"][0]
     rec = inp["rec"]
     wav = inp["wavelet"][:nsteps]
     seis = np.zeros((len(rec), nsteps + 1))
     t0 = time.perf_counter()
-    r = oracle.rtm_shot(a, ws.h, nsteps, src, wav, rec, seis, ws.nb, (ws.nx, 1, ws.nz))
+    r = oracle.rtm_shot(a, ws.h, nsteps, src, wav, rec, seis, ws.nb,
+                        (ws.nx, ws.ny if ws.ndim == 3 else 1, ws.nz))
     img = oracle.image(r["num"], r["den"], EPS_REL)
     dt = time.perf_counter() - t0
     assert np.isfinite(img).all()
@@ -189,19 +225,19 @@ def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
         return
-    w = W.SURVEY_2D
-    inp = W.survey_2d_inputs(w)
+    w, inp = load_workload(W, args)
+    nsamp = REFERENCE_STEP_STEPS if w.ndim == 2 else 4
     for _ in range(args.warmup):
-        oracle_rtm_sample(w, inp, REFERENCE_STEP_STEPS)
+        oracle_rtm_sample(w, inp, nsamp)
     t0 = time.perf_counter()
     total_upd = 0
     for _ in range(args.steps):
-        oracle_rtm_sample(w, inp, REFERENCE_STEP_STEPS)
-        total_upd += updates_per_shot(W.dataclasses.replace(w, nt=REFERENCE_STEP_STEPS))
+        oracle_rtm_sample(w, inp, nsamp)
+        total_upd += updates_per_shot(W.dataclasses.replace(w, nt=nsamp))
     el = time.perf_counter() - t0
     val = total_upd / el / 1e9
-    sample = (f"per step one full-grid shot ({w.nx}x{w.nz} + nb {w.nb}) of Algorithm 3 with "
-              f"{REFERENCE_STEP_STEPS} of the {w.nt} time steps")
+    sample = (f"per step one full-grid shot ({'x'.join(map(str, w.padded[::-1]))} padded) of Algorithm 3 "
+              f"with {nsamp} of the {w.nt} time steps")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gpts/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -236,11 +272,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = W.SURVEY_2D
-    if args.nt:
-        w = W.dataclasses.replace(w, nt=args.nt, name=f"{w.name}_nt{args.nt}")
-    inp = W.survey_2d_inputs(w)
-    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    w, inp = load_workload(W, args)
+    g = R.make_grid(w.ndim, w.nx, w.ny, w.nz, w.nb, w.h, w.dt, w.nt)
     dev = torch.device("cuda", local)
     a_true = torch.empty(g.padded, dtype=torch.float32, device=dev)
     a_mig = torch.empty_like(a_true)
@@ -254,7 +287,7 @@ def main():
     B = args.shots_per_step
     plan = shot_plan(w.nshots, args.steps, args.warmup, B, rank, world)
     needed = sorted({s for step in plan for s in step})
-    srcs = {s: W.source_at(w, int(inp["shots"][s])) for s in needed}
+    srcs = {s: inp["srcs"][s] for s in needed}
 
     # observed records, modeled in the true model (setup, untimed)
     ctx_true = R.rbc_create(g, a_true)
@@ -341,16 +374,19 @@ def main():
     rev_launch_s = phases["rev_ms"] / 1e3 / max(phases["rev_launches"], 1)
     achieved = rev_bytes_per_launch(w) / rev_launch_s / 1e9
     fwd_launch_s = phases["fwd_ms"] / 1e3 / max(phases["fwd_launches"], 1)
-    roofline = {"bound": "hbm", "kernel": "k_rev2d (fused reverse pass)", "achieved": achieved, "peak": peak,
+    kname = "k_rev2d" if w.ndim == 2 else "k_rev3d_tma"
+    roofline = {"bound": "hbm", "kernel": f"{kname} (fused reverse pass)", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
                 "traffic": None,
                 "bytes_per_launch": rev_bytes_per_launch(w), "launch_us": rev_launch_s * 1e6,
-                "forward_kernel": {"kernel": "k_fwd2d", "achieved": fwd_bytes_per_launch(w) / fwd_launch_s / 1e9,
+                "forward_kernel": {"kernel": "k_fwd2d" if w.ndim == 2 else "k_fwd3d_tma",
+                                   "achieved": fwd_bytes_per_launch(w) / fwd_launch_s / 1e9,
                                    "launch_us": fwd_launch_s * 1e6,
                                    "bytes_per_launch": fwd_bytes_per_launch(w)},
-                "note": "one shot's working set (about 56 MB) is L2-resident during its time loop, "
-                        "so achieved can exceed the HBM copy bandwidth"}
+                "note": ("one shot's working set (about 56 MB) is L2-resident during its time loop, "
+                         "so achieved can exceed the HBM copy bandwidth") if w.ndim == 2 else
+                        "working set of 4 GB: DRAM-bound"}
 
     if rank != 0:
         if dist is not None:
@@ -358,16 +394,18 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt = oracle_rtm_sample(w, inp, ORACLE_SAMPLE_STEPS)
+        ns = ORACLE_SAMPLE_STEPS if w.ndim == 2 else 8
+        v, dt = oracle_rtm_sample(w, inp, ns)
         cpu = {"value": v, "unit": "Gpts/s", "cores": cores_used(), "kind": "oracle",
-               "sample": f"one full-grid shot ({w.padded[1]}x{w.padded[0]} padded) of Algorithm 3 with "
-                         f"{ORACLE_SAMPLE_STEPS} of the {w.nt} time steps, {dt:.1f} s"}
+               "sample": f"one full-grid shot ({'x'.join(map(str, w.padded[::-1]))} padded) of Algorithm 3 "
+                         f"with {ns} of the {w.nt} time steps, {dt:.1f} s"}
     out = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "padded_grid": list(w.padded[::-1]), "nt": w.nt, "dt": w.dt,
                       "h": w.h, "receivers": nrec, "shots_per_step": B, "shots_timed": shots_total,
-                      "s_per_shot": el / (args.steps * B), "survey_s_240_shots": el / (args.steps * B) * 240,
+                      "s_per_shot": el / (args.steps * B),
+                      "survey_s": el / (args.steps * B) * w.nshots,
                       "updates_per_shot": updates_per_shot(w),
                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                       "parallelism": f"shots sharded over {world} GPU(s)"},

@@ -114,11 +114,15 @@ struct rbc_ctx {
   std::vector<cudaEvent_t> ev;  // three events per timed shot
   std::vector<cudaEvent_t> ev_free;
   bool use_graph = true;
+  int zc = k3dZC;  // z planes per block of the 3-D kernels
   // snapshots
   std::vector<int> snap;
   float *pf = nullptr, *pr = nullptr, *pb = nullptr;
   // panel location after the last forward phase
   int have_panels = 0;
+  // error word of the kernels' bounded waits (mapped host memory)
+  int *err_host = nullptr;
+  int *err_dev = nullptr;
 };
 
 namespace {
@@ -128,6 +132,16 @@ void drop_graphs(rbc_ctx *c) {
     if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
     c->gexec[k] = nullptr;
   }
+}
+
+// Report (once) a bounded device wait that gave up in an earlier launch.
+int check_device_error(rbc_ctx *c) {
+  if (c->err_host && *(volatile int *)c->err_host) {
+    *(volatile int *)c->err_host = 0;
+    return fail(RBC_ETIMEOUT, "a kernel's bounded wait gave up (data in flight did not arrive); results of the "
+                              "calls since the last check are invalid");
+  }
+  return RBC_OK;
 }
 
 int ensure_receivers(rbc_ctx *c, int nrec) {
@@ -178,7 +192,7 @@ int upload_shot(rbc_ctx *c, const int *src, int nrec, const int *rec, int reinje
   info.src_rev = reinject ? (float)ps : 0.f;
   info.rec_scale = (float)ps;
   int gx, gy, gz, t;
-  rev_tiling(L, &gx, &gy, &gz, &t);
+  rev_tiling(L, c->zc, &gx, &gy, &gz, &t);
   std::vector<int> off(std::max(nrec, 1)), tile(std::max(nrec, 1)), ptr(c->ntiles + 1, 0),
       order(std::max(nrec, 1));
   for (int r = 0; r < nrec; ++r) {
@@ -186,7 +200,7 @@ int upload_shot(rbc_ctx *c, const int *src, int nrec, const int *rec, int reinje
     off[r] = lay_off(L, x, y, z);
     int b;
     if (L.ndim == 2) b = (z / t) * gx + x / kTileX;
-    else b = ((z / k3dZC) * gy + y / t) * gx + x / kTileX;
+    else b = ((z / c->zc) * gy + y / t) * gx + x / kTileX;
     tile[r] = b;
     ptr[b + 1]++;
   }
@@ -225,7 +239,8 @@ int enqueue_forward(rbc_ctx *c, cudaStream_t s, int sample) {
   A.rec_off = c->rec_off;
   A.seis_t = c->seis_t;
   A.sample = sample;
-  A.zc = k3dZC;
+  A.zc = c->zc;
+  A.err = c->err_dev;
   const int nt = c->g.nt;
   for (int n = 0; n < nt; ++n) {
     const int k = snap_index(c, n);
@@ -236,7 +251,7 @@ int enqueue_forward(rbc_ctx *c, cudaStream_t s, int sample) {
     A.cur = c->p[n & 1];
     A.nxt = c->p[(n + 1) & 1];
     A.n = n;
-    launch_fwd(A, s);
+    if (!launch_fwd(A, s)) return fail(RBC_ECUDA, "tensor map encoding failed");
     ++g_launches;
   }
   const int k = snap_index(c, nt);
@@ -281,7 +296,8 @@ int enqueue_reverse(rbc_ctx *c, cudaStream_t s) {
   A.iz1 = nb + c->g.nz;
   A.iy0 = (L.ndim == 3) ? nb : 0;
   A.iy1 = (L.ndim == 3) ? nb + c->g.ny : 1;
-  A.zc = k3dZC;
+  A.zc = c->zc;
+  A.err = c->err_dev;
   const int nt = c->g.nt;
   for (int n = nt; n >= 0; --n) {
     const int k = snap_index(c, n);
@@ -294,7 +310,7 @@ int enqueue_reverse(rbc_ctx *c, cudaStream_t s) {
     A.n = n;
     A.do_r = (n < nt && n > 0) ? 1 : 0;  // p^R_{nt-1} is the stored panel
     A.do_b = (n > 0) ? 1 : 0;
-    launch_rev(A, s);
+    if (!launch_rev(A, s)) return fail(RBC_ECUDA, "tensor map encoding failed");
     ++g_launches;
   }
   CKL();
@@ -414,6 +430,8 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   cudaGetDevice(&c->dev);
   const char *env = getenv("RBC_GRAPH");
   c->use_graph = !(env && env[0] == '0');
+  const char *zenv = getenv("RBC_ZC");  // tuning knob: z planes per 3-D block
+  if (zenv && atoi(zenv) >= 8) c->zc = atoi(zenv);
   const size_t fb = sizeof(float) * (size_t)L.total;
   cudaError_t ea = cudaMalloc(&c->buf, 7 * fb);
   if (ea != cudaSuccess) {
@@ -428,8 +446,14 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   c->num = c->buf + 5 * L.total;
   c->den = c->buf + 6 * L.total;
   int gx, gy, gz, t;
-  rev_tiling(L, &gx, &gy, &gz, &t);
+  rev_tiling(L, c->zc, &gx, &gy, &gz, &t);
   c->ntiles = gx * gy * gz;
+  if (cudaHostAlloc((void **)&c->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&c->err_dev, c->err_host, 0) != cudaSuccess) {
+    rbc_destroy(c);
+    return fail(RBC_ENOMEM, "error word allocation failed");
+  }
+  *c->err_host = 0;
   if (cudaMalloc(&c->tile_ptr, sizeof(int) * (c->ntiles + 1)) != cudaSuccess ||
       cudaMalloc(&c->info, sizeof(ShotInfo)) != cudaSuccess ||
       cudaMalloc(&c->wav, sizeof(float) * g->nt) != cudaSuccess ||
@@ -460,6 +484,7 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
 int rbc_destroy(rbc_ctx *c) {
   if (!c) return RBC_OK;
   cudaDeviceSynchronize();
+  const int pending = check_device_error(c);
   drop_graphs(c);
   cudaFree(c->buf);
   cudaFree(c->info);
@@ -469,10 +494,11 @@ int rbc_destroy(rbc_ctx *c) {
   cudaFree(c->tile_ptr);
   cudaFree(c->seis_t);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->err_host) cudaFreeHost(c->err_host);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   delete c;
-  return RBC_OK;
+  return pending;
 }
 
 int rbc_model(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nrec, const int *rec_host,
@@ -480,7 +506,9 @@ int rbc_model(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nre
   if (!c) return fail(RBC_EINVAL, "ctx is NULL");
   if (!wavelet_dev || (nrec > 0 && !seis_dev)) return fail(RBC_EINVAL, "wavelet_dev / seis_dev is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = upload_shot(c, src_host, nrec, rec_host, 1, s);
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  rc = upload_shot(c, src_host, nrec, rec_host, 1, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(c->wav, wavelet_dev, sizeof(float) * c->g.nt, cudaMemcpyDeviceToDevice, s));
   rc = run_loop(c, 0, enq_model, s);
@@ -501,7 +529,9 @@ int rbc_rtm_shot(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int 
     return fail(RBC_EINVAL, "NULL device pointer");
   if (flags & ~(RBC_REINJECT_SOURCE | RBC_ZERO_FIRST)) return fail(RBC_EINVAL, "unknown flags 0x%x", flags);
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = upload_shot(c, src_host, nrec, rec_host, flags & RBC_REINJECT_SOURCE, s);
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  rc = upload_shot(c, src_host, nrec, rec_host, flags & RBC_REINJECT_SOURCE, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(c->wav, wavelet_dev, sizeof(float) * c->g.nt, cudaMemcpyDeviceToDevice, s));
   if (nrec > 0) {
@@ -586,6 +616,9 @@ int rbc_phase_timing(rbc_ctx *c, int enable, double *out) {
   }
   for (cudaEvent_t e : c->ev) c->ev_free.push_back(e);
   c->ev.clear();
+  CK(cudaDeviceSynchronize());
+  int perr = check_device_error(c);
+  if (perr) return perr;
   if (out) {
     out[0] = fwd;
     out[1] = rev;

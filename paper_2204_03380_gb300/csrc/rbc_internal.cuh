@@ -69,6 +69,7 @@ struct StepArgs {
   int n;                          // time level held in `cur`
   int sample;                     // record cur at the receivers
   int zc;                         // z planes per block (3-D)
+  int *err;                       // error word (bounded waits that gave up)
 };
 
 struct RevArgs {
@@ -90,22 +91,27 @@ struct RevArgs {
   int do_r, do_b;                 // update p^R / pbar at this level
   int ix0, ix1, iy0, iy1, iz0, iz1; // interior box [lo, hi) in padded nodes
   int zc;
+  int *err;
 };
 
 // ---- launch geometry shared by the host (CSR) and the kernels ----
 constexpr int k2dWarps = 8;   // warps per block, stacked in z (2-D)
 constexpr int k2dRowsF = 4;   // rows per warp, forward kernel
 constexpr int k2dRowsR = 2;   // rows per warp, reverse kernel
-constexpr int k3dBY = 16;     // warps per block = y rows (3-D)
-constexpr int k3dZC = 64;     // z planes per block (3-D)
+constexpr int k3dBY = 16;     // y rows covered by the layout's row padding (3-D)
+constexpr int k3dZC = 32;     // z planes per block (3-D)
 
 } // namespace rbc
 
 // kernel launchers (rbc_kernels.cu)
 namespace rbc {
-void launch_fwd(const StepArgs &A, cudaStream_t s);
-void launch_rev(const RevArgs &A, cudaStream_t s);
-void rev_tiling(const Lay &L, int *gx, int *gy, int *gz, int *tz_or_by);
+bool launch_fwd(const StepArgs &A, cudaStream_t s);
+bool launch_rev(const RevArgs &A, cudaStream_t s);
+// rbc_kernels3d.cu (TMA-fed 3-D kernels)
+bool launch_fwd3d(const StepArgs &A, cudaStream_t s);
+bool launch_rev3d(const RevArgs &A, cudaStream_t s);
+int tile_rows_3d();
+void rev_tiling(const Lay &L, int zc, int *gx, int *gy, int *gz, int *tz_or_by);
 void launch_copy_in(const Lay &L, const float *dense, float *pitched, cudaStream_t s);
 void launch_copy_out(const Lay &L, const float *pitched, float *dense, cudaStream_t s);
 void launch_transpose(const float *in, float *out, int rows, int cols, cudaStream_t s);

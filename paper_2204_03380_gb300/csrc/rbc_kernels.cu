@@ -11,11 +11,12 @@
 //                       both updates.
 // All are HBM/L2 streaming kernels (about 2 flop/byte): no tensor cores.
 // Every lane owns a float4 (4 consecutive x) so a warp covers a 128-float,
-// 512-byte row segment with fully coalesced 16-byte accesses; x neighbours
-// come from the adjacent lanes by warp shuffles (lanes 0/31 fetch the
-// 4-float halo), z neighbours from a register queue marching down z, and in
-// 3-D the y neighbours from a shared-memory plane tile.
+// 512-byte row segment with fully coalesced 16-byte accesses; in 2-D the x
+// neighbours come from the adjacent lanes by warp shuffles (lanes 0/31 fetch
+// the 4-float halo) and the z neighbours from a register queue marching down
+// z.  The 3-D kernels (TMA-fed plane rings) are in rbc_kernels3d.cu.
 #include "rbc_internal.cuh"
+#include "rbc_stencil.cuh"
 
 namespace rbc {
 
@@ -41,34 +42,12 @@ __device__ __forceinline__ float4 shfl_dn4(float4 v) {
   return v;
 }
 
-// Leapfrog update of 4 consecutive nodes:
-//   out = (2 p - p_old) + a * sum_axes sum_k c_k [(p_{-k} - p) + (p_{+k} - p)]
-// lf/c/rt: x window (x0-4 .. x0+7); zq[0..8]: z window centred on zq[4] == c;
-// yq[0..8]: y window (3-D only).
-template <bool kThreeD>
-__device__ __forceinline__ float4 leap4(const float4 lf, const float4 c, const float4 rt,
-                                        const float4 *zq, const float4 *yq, const float4 po,
-                                        const float4 av) {
+// Leapfrog update of 4 consecutive nodes from the x window (lf, c, rt) and
+// the z window zq[0..8] (zq[4] == c); see rbc_stencil.cuh.
+__device__ __forceinline__ float4 leap4_2d(const float4 lf, const float4 c, const float4 rt, const float4 *zq,
+                                           const float4 po, const float4 av) {
   const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w, rt.x, rt.y, rt.z, rt.w};
-  float out[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float p = w[4 + i];
-    float s[5];
-#pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-      float t = (w[4 + i - k] - p) + (w[4 + i + k] - p);
-      t += (cmp(zq[4 - k], i) - p) + (cmp(zq[4 + k], i) - p);
-      if (kThreeD) t += (cmp(yq[4 - k], i) - p) + (cmp(yq[4 + k], i) - p);
-      s[k] = t;
-    }
-    float lap = kC4 * s[4];
-    lap = fmaf(kC3, s[3], lap);
-    lap = fmaf(kC2, s[2], lap);
-    lap = fmaf(kC1, s[1], lap);
-    out[i] = fmaf(cmp(av, i), lap, 2.0f * p - cmp(po, i));
-  }
-  return make_float4(out[0], out[1], out[2], out[3]);
+  return leap4p<false>(w, zq, nullptr, nullptr, po, av);
 }
 
 // Subtract a point term from component (src - o) of v when the source node
@@ -154,7 +133,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d(const StepArgs A) {
     if (xok) {
       const float4 av = ldg4(A.a + o);
       const float4 po = ld4(A.nxt + o);
-      float4 r = leap4<false>(lf, c, rt, &q[j], nullptr, po, av);
+      float4 r = leap4_2d(lf, c, rt, &q[j], po, av);
       const int d = src - o;
       if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
       st4(A.nxt + o, r);
@@ -197,7 +176,7 @@ __device__ __forceinline__ void rev_field2d(const Lay &L, const float *__restric
     if (xok) {
       const float4 av = ldg4(a + o);
       const float4 po = ld4(nxt + o);
-      float4 r = leap4<false>(lf, c, rt, &q[j], nullptr, po, av);
+      float4 r = leap4_2d(lf, c, rt, &q[j], po, av);
       const int d = src - o;
       if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
       st4(nxt + o, r);
@@ -237,163 +216,18 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
   if (A.do_b) inject_receivers(A, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
-// ------------------------------------------------------------------ 3-D ----
-// Block: 32 x BY threads = a 128 (x) x BY (y) column tile marching over zc
-// planes.  Each plane of the field is staged in shared memory with 4 halo
-// rows in y and one float4 of halo in x per side; z neighbours stay in a
-// 9-deep register queue.
-template <int BY>
-__global__ void __launch_bounds__(32 * BY) k_fwd3d(const StepArgs A) {
-  __shared__ float4 sm[BY + 8][34];
-  const Lay &L = A.L;
-  const int lane = threadIdx.x, w = threadIdx.y;
-  const int x0 = blockIdx.x * kTileX + lane * 4;
-  const int y0 = blockIdx.y * BY, y = y0 + w;
-  const int zb = blockIdx.z * A.zc;
-  const int ze = min(zb + A.zc, L.NZ);
-  const bool xok = x0 < L.NX4, yok = y < L.NY;
-  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  if (A.sample) sample_receivers(A, gridDim.x * gridDim.y * gridDim.z, bid);
-  const int col = L.origin + y * L.pitch + x0;
-  // y halo row fetched by this warp (warps 0-3 above the tile, the last 4 below)
-  const int hslot = (w < 4) ? w : (w >= BY - 4 ? w + 8 : -1);
-  const int hy = (w < 4) ? y0 - 4 + w : y0 + w + 4;
-  const int hcol = L.origin + hy * L.pitch + x0;
-  float4 q[9];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int z = zb - kHaloR + j;
-    q[j] = (xok && z < L.NZ + kHaloR) ? ldg4(A.cur + col + z * L.plane) : zero4();
-  }
-  const int src = A.info->src_off;
-  const float fsrc = A.wav[A.n] * A.info->src_fwd;
-#pragma unroll 1
-  for (int z = zb; z < ze; ++z) {
-    const int zo = z * L.plane;
-    q[8] = (xok && z + kHaloR < L.NZ + kHaloR) ? ldg4(A.cur + col + zo + kHaloR * L.plane) : zero4();
-    sm[w + 4][lane + 1] = q[4];
-    if (hslot >= 0) sm[hslot][lane + 1] = xok ? ldg4(A.cur + hcol + zo) : zero4();
-    if (lane == 0) sm[w + 4][0] = ldg4(A.cur + col + zo - 4);
-    if (lane == 31) sm[w + 4][33] = ldg4(A.cur + col + zo + 4);
-    __syncthreads();
-    if (xok && yok) {
-      float4 yq[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) yq[k] = sm[w + k][lane + 1];
-      const int o = col + zo;
-      const float4 av = ldg4(A.a + o);
-      const float4 po = ld4(A.nxt + o);
-      float4 r = leap4<true>(sm[w + 4][lane], q[4], sm[w + 4][lane + 2], q, yq, po, av);
-      const int d = src - o;
-      if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
-      st4(A.nxt + o, r);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
-  }
-}
-
-template <int BY>
-__global__ void __launch_bounds__(32 * BY) k_rev3d(const RevArgs A) {
-  __shared__ float4 smr[BY + 8][34];
-  __shared__ float4 smb[BY + 8][34];
-  const Lay &L = A.L;
-  const int lane = threadIdx.x, w = threadIdx.y;
-  const int x0 = blockIdx.x * kTileX + lane * 4;
-  const int y0 = blockIdx.y * BY, y = y0 + w;
-  const int zb = blockIdx.z * A.zc;
-  const int ze = min(zb + A.zc, L.NZ);
-  const bool xok = x0 < L.NX4, yok = y < L.NY;
-  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  const int col = L.origin + y * L.pitch + x0;
-  const int hslot = (w < 4) ? w : (w >= BY - 4 ? w + 8 : -1);
-  const int hy = (w < 4) ? y0 - 4 + w : y0 + w + 4;
-  const int hcol = L.origin + hy * L.pitch + x0;
-  const bool do_r = A.do_r != 0, do_b = A.do_b != 0;
-  const bool img_xy = xok && yok && y >= A.iy0 && y < A.iy1 && x0 + 3 >= A.ix0 && x0 < A.ix1;
-  float4 qr[9], qb[9];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int z = zb - kHaloR + j;
-    const bool ok = xok && z < L.NZ + kHaloR;
-    qr[j] = ok ? ldg4(A.rc + col + z * L.plane) : zero4();
-    qb[j] = ok ? ldg4(A.bc + col + z * L.plane) : zero4();
-  }
-  const int src = A.info->src_off;
-  const float fsrc = A.do_r ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
-#pragma unroll 1
-  for (int z = zb; z < ze; ++z) {
-    const int zo = z * L.plane;
-    const bool ok = xok && z + kHaloR < L.NZ + kHaloR;
-    qr[8] = ok ? ldg4(A.rc + col + zo + kHaloR * L.plane) : zero4();
-    qb[8] = ok ? ldg4(A.bc + col + zo + kHaloR * L.plane) : zero4();
-    if (do_r || do_b) {
-      smr[w + 4][lane + 1] = qr[4];
-      smb[w + 4][lane + 1] = qb[4];
-      if (hslot >= 0) {
-        smr[hslot][lane + 1] = xok ? ldg4(A.rc + hcol + zo) : zero4();
-        smb[hslot][lane + 1] = xok ? ldg4(A.bc + hcol + zo) : zero4();
-      }
-      if (lane == 0) {
-        smr[w + 4][0] = ldg4(A.rc + col + zo - 4);
-        smb[w + 4][0] = ldg4(A.bc + col + zo - 4);
-      }
-      if (lane == 31) {
-        smr[w + 4][33] = ldg4(A.rc + col + zo + 4);
-        smb[w + 4][33] = ldg4(A.bc + col + zo + 4);
-      }
-    }
-    __syncthreads();
-    if (xok && yok) {
-      const int o = col + zo;
-      const float4 av = ldg4(A.a + o);
-      float4 yq[9];
-      if (do_r) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) yq[k] = smr[w + k][lane + 1];
-        const float4 po = ld4(A.rn + o);
-        float4 r = leap4<true>(smr[w + 4][lane], qr[4], smr[w + 4][lane + 2], qr, yq, po, av);
-        const int d = src - o;
-        if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
-        st4(A.rn + o, r);
-      }
-      if (do_b) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) yq[k] = smb[w + k][lane + 1];
-        const float4 po = ld4(A.bn + o);
-        st4(A.bn + o, leap4<true>(smb[w + 4][lane], qb[4], smb[w + 4][lane + 2], qb, yq, po, av));
-      }
-      if (img_xy && z >= A.iz0 && z < A.iz1) {
-        st4(A.num + o, add4(ld4(A.num + o), masked_prod(qr[4], qb[4], x0, A.ix0, A.ix1)));
-        st4(A.den + o, add4(ld4(A.den + o), masked_prod(qr[4], qr[4], x0, A.ix0, A.ix1)));
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      qr[k] = qr[k + 1];
-      qb[k] = qb[k + 1];
-    }
-  }
-  if (do_b) inject_receivers(A, bid);
-}
-
 // ------------------------------------------------------------ launchers ----
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
-void launch_fwd(const StepArgs &A, cudaStream_t s) {
+bool launch_fwd(const StepArgs &A, cudaStream_t s) {
   const Lay &L = A.L;
-  if (L.ndim == 2) {
-    dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarps * k2dRowsF));
-    k_fwd2d<k2dRowsF><<<grid, dim3(32, k2dWarps), 0, s>>>(A);
-  } else {
-    dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NY, k3dBY), cdiv(L.NZ, A.zc));
-    k_fwd3d<k3dBY><<<grid, dim3(32, k3dBY), 0, s>>>(A);
-  }
+  if (L.ndim == 3) return launch_fwd3d(A, s);
+  dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarps * k2dRowsF));
+  k_fwd2d<k2dRowsF><<<grid, dim3(32, k2dWarps), 0, s>>>(A);
+  return true;
 }
 
-void rev_tiling(const Lay &L, int *gx, int *gy, int *gz, int *t) {
+void rev_tiling(const Lay &L, int zc, int *gx, int *gy, int *gz, int *t) {
   if (L.ndim == 2) {
     *gx = cdiv(L.NX, kTileX);
     *gy = cdiv(L.NZ, k2dWarps * k2dRowsR);
@@ -401,20 +235,18 @@ void rev_tiling(const Lay &L, int *gx, int *gy, int *gz, int *t) {
     *t = k2dWarps * k2dRowsR;
   } else {
     *gx = cdiv(L.NX, kTileX);
-    *gy = cdiv(L.NY, k3dBY);
-    *gz = cdiv(L.NZ, k3dZC);
-    *t = k3dBY;
+    *gy = cdiv(L.NY, tile_rows_3d());
+    *gz = cdiv(L.NZ, zc);
+    *t = tile_rows_3d();
   }
 }
 
-void launch_rev(const RevArgs &A, cudaStream_t s) {
+bool launch_rev(const RevArgs &A, cudaStream_t s) {
+  if (A.L.ndim == 3) return launch_rev3d(A, s);
   int gx, gy, gz, t;
-  rev_tiling(A.L, &gx, &gy, &gz, &t);
-  if (A.L.ndim == 2) {
-    k_rev2d<k2dRowsR><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
-  } else {
-    k_rev3d<k3dBY><<<dim3(gx, gy, gz), dim3(32, k3dBY), 0, s>>>(A);
-  }
+  rev_tiling(A.L, A.zc, &gx, &gy, &gz, &t);
+  k_rev2d<k2dRowsR><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
+  return true;
 }
 
 // ----------------------------------------------------------- auxiliaries ----

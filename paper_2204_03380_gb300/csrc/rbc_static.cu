@@ -178,11 +178,12 @@ extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int
   A.seis_t = seis_t;
   A.sample = nrec > 0 ? 1 : 0;
   A.zc = k3dZC;
+  A.err = reinterpret_cast<int *>(amax) + 1;  // bounded-wait error word (not reported)
   for (int n = 0; n < g->nt; ++n) {
     A.cur = p[n & 1];
     A.nxt = p[(n + 1) & 1];
     A.n = n;
-    launch_fwd(A, s);
+    if (!launch_fwd(A, s)) return set_err(RBC_ECUDA, "rbc_model_static: tensor map encoding failed");
   }
   if (nrec > 0) {
     k_static_sample<<<(nrec + 255) / 256, 256, 0, s>>>(p[g->nt & 1], rec_off, nrec,
