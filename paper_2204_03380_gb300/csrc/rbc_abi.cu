@@ -200,7 +200,7 @@ int upload_shot(rbc_ctx *c, const int *src, int nrec, const int *rec, int reinje
     off[r] = lay_off(L, x, y, z);
     int b;
     if (L.ndim == 2) b = (z / t) * gx + x / kTileX;
-    else b = ((z / c->zc) * gy + y / t) * gx + x / kTileX;
+    else b = (((z / c->zc) * gy + y / t) * gx + x / kTileX) * t + y % t;  // (tile, row) cells
     tile[r] = b;
     ptr[b + 1]++;
   }
@@ -447,7 +447,7 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   c->den = c->buf + 6 * L.total;
   int gx, gy, gz, t;
   rev_tiling(L, c->zc, &gx, &gy, &gz, &t);
-  c->ntiles = gx * gy * gz;
+  c->ntiles = gx * gy * gz * (L.ndim == 3 ? t : 1);  // 3-D: one receiver list per (tile, row)
   if (cudaHostAlloc((void **)&c->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer((void **)&c->err_dev, c->err_host, 0) != cudaSuccess) {
     rbc_destroy(c);

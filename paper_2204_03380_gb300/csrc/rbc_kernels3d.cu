@@ -25,11 +25,15 @@ namespace rbc {
 
 namespace {
 
-constexpr int kTY = 8;        // y rows per block (one warp each)
+constexpr int kTY = 8;        // y rows per reverse tile (one warp per field each)
+#ifndef RBC_FWD3D_ROWS
+#define RBC_FWD3D_ROWS 16
+#endif
+constexpr int kTYf = RBC_FWD3D_ROWS;  // y rows per forward tile (one warp each)
 constexpr int kRP = 8;        // forward P ring: 5 live planes + 3 in flight
 constexpr int kRT = 5;        // forward T ring: 1 live plane + 4 in flight
-constexpr int kRPr = 7;       // reverse P ring (two fields): 5 live + 2 in flight
-constexpr int kRTr = 4;       // reverse T ring (a, p^R, pbar, num, den): 1 live + 3 in flight
+constexpr int kRPr = 8;       // reverse P ring (two fields): 5 live + 3 in flight
+constexpr int kRTr = 3;       // reverse T ring (a, p^R, pbar, num, den): 1 live + 2 in flight
 constexpr int kHaloW = 136;   // 128 + 2 x 4 halo floats
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
@@ -122,300 +126,364 @@ __device__ __forceinline__ void flag_error(int *err, int code) {
   if (err) atomicOr_system(err, code);
 }
 
-// ------------------------------------------------------------- forward ----
-// Shared memory: P ring (kRP stages of one halo plane), T ring (kRT stages of
-// a and p^{n-1} tiles), barriers.
-constexpr size_t kFwdSmem = sizeof(float) * (kRP * kPStage + kRT * 2 * kTTile) + 8 * (kRP + kRT) + 16;
+// Warp-specialised pipeline: warps 0..kTY-1 (and kTY..2kTY-1 in the reverse
+// kernel) consume, the last warp produces.  Each ring stage has a "full"
+// barrier (one arrival + the TMA byte count) and an "empty" barrier (one
+// arrival per consumer warp when it is done with the stage), so consumer warps
+// never meet at a block-wide barrier inside the plane loop and the producer
+// refills a stage as soon as every consumer has released it.
 
-__global__ void __launch_bounds__(32 * kTY) k_fwd3d_tma(const __grid_constant__ CUtensorMap tm_cur,
-                                                         const __grid_constant__ CUtensorMap tm_a,
-                                                         const __grid_constant__ CUtensorMap tm_old,
-                                                         const StepArgs A) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another thread of the block has
+// flagged an abort; sets the flag itself when its own time runs out.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, volatile int *abort_blk) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_blk) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_blk = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Persistent blocks: the grid has one block per resident slot and every block
+// walks a strided list of tiles (128 x kTY columns x one z chunk).  Per tile
+// the P sequence is the planes zb-4 .. ze+3 (the first four only feed the z
+// queue) and the T sequence the planes zb .. ze-1; sequence numbers keep
+// counting across tiles, so the producer streams the next tile's planes while
+// the consumers finish the current one.  A P ring of at least 8 stages holds a
+// tile's first 8 planes at once.
+
+struct Tile3 {
+  int bx, by, zb, ze;
+};
+
+__device__ __forceinline__ Tile3 tile_of(int t, int gx, int gy, int zc, int NZ) {
+  Tile3 T;
+  T.bx = t % gx;
+  const int u = t / gx;
+  T.by = u % gy;
+  T.zb = (u / gy) * zc;
+  T.ze = min(T.zb + zc, NZ);
+  return T;
+}
+
+// ------------------------------------------------------------- forward ----
+template <int TY>
+constexpr size_t fwd_smem() {
+  return sizeof(float) * (kRP * (TY + 8) * kHaloW + kRT * 2 * TY * 128) + 16 * (kRP + kRT) + 16;
+}
+static_assert(kRP >= 8, "the P ring must hold a tile's first 8 planes");
+
+// TY rows per tile (one consumer warp each) plus one producer warp.
+template <int TY>
+__global__ void __launch_bounds__(32 * (TY + 1)) k_fwd3d_tma(const __grid_constant__ CUtensorMap tm_cur,
+                                                               const __grid_constant__ CUtensorMap tm_a,
+                                                               const __grid_constant__ CUtensorMap tm_old,
+                                                               const StepArgs A) {
+  constexpr int kPStage = (TY + 8) * kHaloW;
+  constexpr int kTTile = TY * 128;
   extern __shared__ __align__(128) float smem[];
-  float *sp = smem;                         // [kRP][kTY + 8][136]
-  float *st = sp + kRP * kPStage;           // [kRT][2][kTY][128]  (a, old)
-  uint64_t *barP = reinterpret_cast<uint64_t *>(st + kRT * 2 * kTTile);
-  uint64_t *barT = barP + kRP;
-  int &abort_blk = *reinterpret_cast<int *>(barT + kRT);
-  int armP[kRP], armT[kRT];  // phases armed per stage (thread 0 only)
+  float *sp = smem;                         // [kRP][TY + 8][136]
+  float *st = sp + kRP * kPStage;           // [kRT][2][TY][128]  (a, old)
+  uint64_t *fullP = reinterpret_cast<uint64_t *>(st + kRT * 2 * kTTile);
+  uint64_t *emptyP = fullP + kRP;
+  uint64_t *fullT = emptyP + kRP;
+  uint64_t *emptyT = fullT + kRT;
+  volatile int *abort_blk = reinterpret_cast<volatile int *>(emptyT + kRT);
   const Lay &L = A.L;
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
-  const int bx = blockIdx.x, by = blockIdx.y;
-  const int x0 = bx * kTileX + lane * 4, y = by * kTY + w;
-  const int zb = blockIdx.z * A.zc, ze = min(zb + A.zc, L.NZ);
-  const bool xok = x0 < L.NX4, yok = y < L.NY;
+  const int nthr = blockDim.x * blockDim.y;
+  const int gx = (L.NX + kTileX - 1) / kTileX, gy = (L.NY + TY - 1) / TY;
+  const int ntiles = gx * gy * ((L.NZ + A.zc - 1) / A.zc);
   if (A.sample) {
-    const int nb = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = (blockIdx.z * gridDim.y + by) * gridDim.x + bx;
     const int nrec = A.info->nrec;
-    for (int r = bid * blockDim.x * blockDim.y + tid; r < nrec; r += nb * blockDim.x * blockDim.y)
+    for (int r = blockIdx.x * nthr + tid; r < nrec; r += gridDim.x * nthr)
       A.seis_t[(long long)A.n * nrec + r] = A.cur[A.rec_off[r]];
   }
-  // tensor-map coordinates: padded node (x, y, z) -> (x + 32, y + 4, z + 4)
-  const int hx = bx * kTileX + kHaloX - 4, hy = by * kTY;        // halo box origin
-  const int tx = bx * kTileX + kHaloX, ty = by * kTY + kHaloR;   // tile box origin
-  const uint32_t pbytes = sizeof(float) * kPStage, tbytes = sizeof(float) * 2 * kTTile;
-  for (int s = 0; s < kRP; ++s) armP[s] = 0;
-  for (int s = 0; s < kRT; ++s) armT[s] = 0;
   if (tid == 0) {
-    abort_blk = 0;
-    for (int s = 0; s < kRP; ++s) mbar_init(&barP[s], 1);
-    for (int s = 0; s < kRT; ++s) mbar_init(&barT[s], 1);
+    *abort_blk = 0;
+    for (int s = 0; s < kRP; ++s) mbar_init(&fullP[s], 1), mbar_init(&emptyP[s], TY);
+    for (int s = 0; s < kRT; ++s) mbar_init(&fullT[s], 1), mbar_init(&emptyT[s], TY);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int last_p = ze + 3;  // last plane pushed onto a queue
-  if (tid == 0) {
-    for (int r = 0; r < kRP && zb + r <= last_p; ++r) {
-      mbar_expect_tx(&barP[r], pbytes);
-        ++armP[r];
-      tma3(sp + r * kPStage, &tm_cur, hx, hy, zb + r + kHaloR, &barP[r]);
+  if (w == TY) {
+    // ---- producer (one lane): P planes and T tiles in the order they are consumed
+    if (lane == 0) {
+      const uint32_t pbytes = sizeof(float) * kPStage, tbytes = sizeof(float) * 2 * kTTile;
+      int gp = 0, gt = 0;  // sequence numbers
+      bool ok = true;
+      auto issueP = [&](int plane, int hx, int hy) {
+        const int s = gp % kRP, f = gp / kRP;
+        if (f > 0) ok = mbar_wait_ab(&emptyP[s], (f - 1) & 1, abort_blk);
+        if (!ok) return;
+        mbar_expect_tx(&fullP[s], pbytes);
+        tma3(sp + s * kPStage, &tm_cur, hx, hy, plane + kHaloR, &fullP[s]);
+        ++gp;
+      };
+      auto issueT = [&](int plane, int tx, int ty) {
+        const int s = gt % kRT, f = gt / kRT;
+        if (f > 0) ok = mbar_wait_ab(&emptyT[s], (f - 1) & 1, abort_blk);
+        if (!ok) return;
+        mbar_expect_tx(&fullT[s], tbytes);
+        tma3(st + s * 2 * kTTile, &tm_a, tx, ty, plane + kHaloR, &fullT[s]);
+        tma3(st + s * 2 * kTTile + kTTile, &tm_old, tx, ty, plane + kHaloR, &fullT[s]);
+        ++gt;
+      };
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        const Tile3 T = tile_of(t, gx, gy, A.zc, L.NZ);
+        const int hx = T.bx * kTileX + kHaloX - 4, hy = T.by * TY;       // halo box (tensor coords)
+        const int tx = T.bx * kTileX + kHaloX, ty = T.by * TY + kHaloR;  // tile box
+        for (int i = 0; ok && i < 8; ++i) issueP(T.zb - 4 + i, hx, hy);
+        for (int r = 0; ok && r < T.ze - T.zb; ++r) {
+          issueP(T.zb + r + 4, hx, hy);
+          if (ok) issueT(T.zb + r, tx, ty);
+        }
+      }
+      if (*abort_blk) {
+        flag_error(A.err, 1);
+        // let every issued copy land before the block's shared memory is released
+        for (int k = max(0, gp - kRP); k < gp; ++k) mbar_wait(&fullP[k % kRP], (k / kRP) & 1);
+        for (int k = max(0, gt - kRT); k < gt; ++k) mbar_wait(&fullT[k % kRT], (k / kRT) & 1);
+      }
     }
-    for (int r = 0; r < kRT && zb + r < ze; ++r) {
-      mbar_expect_tx(&barT[r], tbytes);
-        ++armT[r];
-      tma3(st + r * 2 * kTTile, &tm_a, tx, ty, zb + r + kHaloR, &barT[r]);
-      tma3(st + r * 2 * kTTile + kTTile, &tm_old, tx, ty, zb + r + kHaloR, &barT[r]);
-    }
+    return;
   }
-  // z queue: planes zb-4 .. zb-1 straight from global, zb .. zb+3 from the ring
-  float4 q[9];
-  const int col = L.origin + y * L.pitch + x0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) q[j] = (xok && zb - 4 + j >= -kHaloR) ? ldg4(A.cur + col + (zb - 4 + j) * L.plane) : zero4();
-  bool ok = true;
-  const int rowc = (w + 4) * kHaloW + lane * 4;  // this thread's halo-row float offset
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (zb + j <= last_p) {
-      ok = mbar_wait(&barP[j], 0) && ok;
-      q[4 + j] = lds4(sp + j * kPStage + rowc + 4);
-    } else {
-      q[4 + j] = zero4();
-    }
-  }
+  // ---- consumers: one row of the tile per warp, a float4 of x per lane
   const int src = A.info->src_off;
   const float fsrc = A.wav[A.n] * A.info->src_fwd;
-  for (int z = zb; z < ze; ++z) {
-    const int r = z - zb;
-    const int rp = (r + 4) % kRP;
-    ok = mbar_wait(&barP[rp], ((r + 4) / kRP) & 1) && ok;
-    q[8] = lds4(sp + rp * kPStage + rowc + 4);
-    ok = mbar_wait(&barT[r % kRT], (r / kRT) & 1) && ok;
-    if (xok && yok) {
-      const float *tt = st + (r % kRT) * 2 * kTTile + w * 128 + lane * 4;
-      const float4 av = lds4(tt), po = lds4(tt + kTTile);
-      float4 v = leap4_3d(sp + (r % kRP) * kPStage + rowc, q, po, av);
-      const int o = col + z * L.plane;
-      const int d = src - o;
-      if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * fsrc);
-      st4(A.nxt + o, v);
-    }
-    if (!ok) abort_blk = 1;
-    __syncthreads();
-    if (abort_blk) break;
-    if (tid == 0) {
-      const int np = z + kRP;  // refill the stage of plane z
-      if (np <= last_p) {
-        const int s = r % kRP;
-        mbar_expect_tx(&barP[s], pbytes);
-        ++armP[s];
-        tma3(sp + s * kPStage, &tm_cur, hx, hy, np + kHaloR, &barP[s]);
-      }
-      const int nt_ = z + kRT;
-      if (nt_ < ze) {
-        const int s = r % kRT;
-        mbar_expect_tx(&barT[s], tbytes);
-        ++armT[s];
-        tma3(st + s * 2 * kTTile, &tm_a, tx, ty, nt_ + kHaloR, &barT[s]);
-        tma3(st + s * 2 * kTTile + kTTile, &tm_old, tx, ty, nt_ + kHaloR, &barT[s]);
-      }
-    }
+  const int rowc = (w + 4) * kHaloW + lane * 4;
+  int gp = 0, gt = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile3 T = tile_of(t, gx, gy, A.zc, L.NZ);
+    const int x0 = T.bx * kTileX + lane * 4, y = T.by * TY + w;
+    const bool xok = x0 < L.NX4, yok = y < L.NY;
+    const int col = L.origin + y * L.pitch + x0;
+    const int nplanes = T.ze - T.zb;
+    float4 q[9];
+    bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
-  }
-  if (abort_blk && tid == 0) {
-    flag_error(A.err, 1);
-    // let every copy already issued land before the block's shared memory is released
-    for (int s = 0; s < kRP; ++s)
-      if (armP[s]) mbar_wait(&barP[s], (armP[s] - 1) & 1);
-    for (int s = 0; s < kRT; ++s)
-      if (armT[s]) mbar_wait(&barT[s], (armT[s] - 1) & 1);
+    for (int j = 0; j < 8; ++j) {
+      ok = ok && mbar_wait_ab(&fullP[(gp + j) % kRP], ((gp + j) / kRP) & 1, abort_blk);
+      q[j] = lds4(sp + ((gp + j) % kRP) * kPStage + rowc + 4);
+    }
+    ok = __all_sync(0xffffffffu, ok);  // keep the warp's decision uniform
+    if (lane == 0)
+      for (int j = 0; j < 4; ++j) mbar_arrive(&emptyP[(gp + j) % kRP]);
+    for (int r = 0; ok && r < nplanes; ++r) {
+      const int z = T.zb + r;
+      const int top = gp + r + 8, cen = gp + r + 4, tk = gt + r;
+      ok = mbar_wait_ab(&fullP[top % kRP], (top / kRP) & 1, abort_blk) &&
+           mbar_wait_ab(&fullT[tk % kRT], (tk / kRT) & 1, abort_blk);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      q[8] = lds4(sp + (top % kRP) * kPStage + rowc + 4);
+      if (xok && yok) {
+        const float *tt = st + (tk % kRT) * 2 * kTTile + w * 128 + lane * 4;
+        const float4 av = lds4(tt), po = lds4(tt + kTTile);
+        float4 v = leap4_3d(sp + (cen % kRP) * kPStage + rowc, q, po, av);
+        const int o = col + z * L.plane;
+        const int d = src - o;
+        if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * fsrc);
+        st4(A.nxt + o, v);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&emptyP[cen % kRP]);
+        mbar_arrive(&emptyT[tk % kRT]);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+    }
+    if (!ok) break;
+    __syncwarp();
+    if (lane == 0)
+      for (int j = nplanes + 4; j < nplanes + 8; ++j) mbar_arrive(&emptyP[(gp + j) % kRP]);
+    gp += nplanes + 8;
+    gt += nplanes;
   }
 }
 
 // ------------------------------------------------------------- reverse ----
-// Two fields: P rings for p^R and pbar halo planes; T ring for the a, p^R and
-// pbar tiles overwritten in place and the num/den tiles (loaded only where the
-// tile meets the image box).
-constexpr size_t kRevSmem = sizeof(float) * (2 * kRPr * kPStage + kRTr * 5 * kTTile) + 8 * (kRPr + kRTr) + 16;
+// 2 x kTY consumer warps: warps 0..kTY-1 advance p^R and accumulate the
+// imaging integrals (reading pbar at the centre plane from the pbar ring),
+// warps kTY..2kTY-1 advance pbar and then add the record at the receivers of
+// their own row of the tile; the last warp produces.  P stage: the p^R and
+// pbar halo planes; T stage: a, p^R and pbar tiles overwritten in place, and
+// the num/den tiles where the tile meets the image box.
+constexpr size_t kRevSmem =
+    sizeof(float) * (2 * kRPr * kPStage + kRTr * 5 * kTTile) + 16 * (kRPr + kRTr) + 16;
+static_assert(kRPr >= 8, "the P ring must hold a tile's first 8 planes");
 
-__global__ void __launch_bounds__(32 * kTY) k_rev3d_tma(const __grid_constant__ CUtensorMap tm_rc,
-                                                         const __grid_constant__ CUtensorMap tm_bc,
-                                                         const __grid_constant__ CUtensorMap tm_a,
-                                                         const __grid_constant__ CUtensorMap tm_rn,
-                                                         const __grid_constant__ CUtensorMap tm_bn,
-                                                         const __grid_constant__ CUtensorMap tm_num,
-                                                         const __grid_constant__ CUtensorMap tm_den,
-                                                         const RevArgs A) {
+__global__ void __launch_bounds__(32 * (2 * kTY + 1)) k_rev3d_tma(const __grid_constant__ CUtensorMap tm_rc,
+                                                                   const __grid_constant__ CUtensorMap tm_bc,
+                                                                   const __grid_constant__ CUtensorMap tm_a,
+                                                                   const __grid_constant__ CUtensorMap tm_rn,
+                                                                   const __grid_constant__ CUtensorMap tm_bn,
+                                                                   const __grid_constant__ CUtensorMap tm_num,
+                                                                   const __grid_constant__ CUtensorMap tm_den,
+                                                                   const RevArgs A) {
   extern __shared__ __align__(128) float smem[];
   float *spr = smem;                        // [kRPr][kTY + 8][136]  p^R
   float *spb = spr + kRPr * kPStage;        // [kRPr][kTY + 8][136]  pbar
   float *st = spb + kRPr * kPStage;         // [kRTr][5][kTY][128]  a, p^R old, pbar old, num, den
-  uint64_t *barP = reinterpret_cast<uint64_t *>(st + kRTr * 5 * kTTile);
-  uint64_t *barT = barP + kRPr;
-  int &abort_blk = *reinterpret_cast<int *>(barT + kRTr);
-  int armP[kRPr], armT[kRTr];
+  uint64_t *fullP = reinterpret_cast<uint64_t *>(st + kRTr * 5 * kTTile);
+  uint64_t *emptyP = fullP + kRPr;
+  uint64_t *fullT = emptyP + kRPr;
+  uint64_t *emptyT = fullT + kRTr;
+  volatile int *abort_blk = reinterpret_cast<volatile int *>(emptyT + kRTr);
   const Lay &L = A.L;
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
-  const int bx = blockIdx.x, by = blockIdx.y;
-  const int x0 = bx * kTileX + lane * 4, y = by * kTY + w;
-  const int zb = blockIdx.z * A.zc, ze = min(zb + A.zc, L.NZ);
-  const bool xok = x0 < L.NX4, yok = y < L.NY;
+  const int gx = (L.NX + kTileX - 1) / kTileX, gy = (L.NY + kTY - 1) / kTY;
+  const int ntiles = gx * gy * ((L.NZ + A.zc - 1) / A.zc);
   const bool do_r = A.do_r != 0, do_b = A.do_b != 0;
-  const bool img_xy = xok && yok && y >= A.iy0 && y < A.iy1 && x0 + 3 >= A.ix0 && x0 < A.ix1;
-  const int hx = bx * kTileX + kHaloX - 4, hy = by * kTY;
-  const int tx = bx * kTileX + kHaloX, ty = by * kTY + kHaloR;
-  const uint32_t pbytes = 2 * sizeof(float) * kPStage;
-  // num/den tiles are streamed only for planes and tiles that meet the image box
-  const bool tile_img = (by * kTY < A.iy1) && (by * kTY + kTY > A.iy0) && (bx * kTileX < A.ix1) &&
-                        (bx * kTileX + kTileX > A.ix0);
-  auto tbytes_of = [&](int plane) -> uint32_t {
-    const bool img = tile_img && plane >= A.iz0 && plane < A.iz1;
-    return (img ? 5u : 3u) * sizeof(float) * kTTile;
-  };
-  for (int s = 0; s < kRPr; ++s) armP[s] = 0;
-  for (int s = 0; s < kRTr; ++s) armT[s] = 0;
   if (tid == 0) {
-    abort_blk = 0;
-    for (int s = 0; s < kRPr; ++s) mbar_init(&barP[s], 1);
-    for (int s = 0; s < kRTr; ++s) mbar_init(&barT[s], 1);
+    *abort_blk = 0;
+    for (int s = 0; s < kRPr; ++s) mbar_init(&fullP[s], 1), mbar_init(&emptyP[s], 2 * kTY);
+    for (int s = 0; s < kRTr; ++s) mbar_init(&fullT[s], 1), mbar_init(&emptyT[s], 2 * kTY);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int last_p = ze + 3;
-  if (tid == 0) {
-    for (int r = 0; r < kRPr && zb + r <= last_p; ++r) {
-      mbar_expect_tx(&barP[r], pbytes);
-        ++armP[r];
-      tma3(spr + r * kPStage, &tm_rc, hx, hy, zb + r + kHaloR, &barP[r]);
-      tma3(spb + r * kPStage, &tm_bc, hx, hy, zb + r + kHaloR, &barP[r]);
-    }
-    for (int r = 0; r < kRTr && zb + r < ze; ++r) {
-      const uint32_t tb = tbytes_of(zb + r);
-      mbar_expect_tx(&barT[r], tb);
-      ++armT[r];
-      float *t = st + r * 5 * kTTile;
-      tma3(t, &tm_a, tx, ty, zb + r + kHaloR, &barT[r]);
-      tma3(t + kTTile, &tm_rn, tx, ty, zb + r + kHaloR, &barT[r]);
-      tma3(t + 2 * kTTile, &tm_bn, tx, ty, zb + r + kHaloR, &barT[r]);
-      if (tb > 3u * sizeof(float) * kTTile) {
-        tma3(t + 3 * kTTile, &tm_num, tx, ty, zb + r + kHaloR, &barT[r]);
-        tma3(t + 4 * kTTile, &tm_den, tx, ty, zb + r + kHaloR, &barT[r]);
-      }
-    }
-  }
-  float4 qr[9], qb[9];
-  const int col = L.origin + y * L.pitch + x0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const bool in = xok && zb - 4 + j >= -kHaloR;
-    qr[j] = in ? ldg4(A.rc + col + (zb - 4 + j) * L.plane) : zero4();
-    qb[j] = in ? ldg4(A.bc + col + (zb - 4 + j) * L.plane) : zero4();
-  }
-  bool ok = true;
-  const int rowc = (w + 4) * kHaloW + lane * 4;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (zb + j <= last_p) {
-      ok = mbar_wait(&barP[j], 0) && ok;
-      qr[4 + j] = lds4(spr + j * kPStage + rowc + 4);
-      qb[4 + j] = lds4(spb + j * kPStage + rowc + 4);
-    } else {
-      qr[4 + j] = zero4();
-      qb[4 + j] = zero4();
-    }
-  }
-  const int src = A.info->src_off;
-  const float fsrc = do_r ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
-  for (int z = zb; z < ze; ++z) {
-    const int r = z - zb;
-    const int rp = (r + 4) % kRPr;
-    ok = mbar_wait(&barP[rp], ((r + 4) / kRPr) & 1) && ok;
-    qr[8] = lds4(spr + rp * kPStage + rowc + 4);
-    qb[8] = lds4(spb + rp * kPStage + rowc + 4);
-    ok = mbar_wait(&barT[r % kRTr], (r / kRTr) & 1) && ok;
-    if (xok && yok) {
-      const int o = col + z * L.plane;
-      const float *tt = st + (r % kRTr) * 5 * kTTile + w * 128 + lane * 4;
-      const float4 av = lds4(tt);
-      const int sc = (r % kRPr) * kPStage + rowc;
-      if (do_r) {
-        float4 v = leap4_3d(spr + sc, qr, lds4(tt + kTTile), av);
-        const int d = src - o;
-        if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * fsrc);
-        st4(A.rn + o, v);
-      }
-      if (do_b) st4(A.bn + o, leap4_3d(spb + sc, qb, lds4(tt + 2 * kTTile), av));
-      if (img_xy && z >= A.iz0 && z < A.iz1) {
-        st4(A.num + o, add4(lds4(tt + 3 * kTTile), masked_prod(qr[4], qb[4], x0, A.ix0, A.ix1)));
-        st4(A.den + o, add4(lds4(tt + 4 * kTTile), masked_prod(qr[4], qr[4], x0, A.ix0, A.ix1)));
-      }
-    }
-    if (!ok) abort_blk = 1;
-    __syncthreads();
-    if (abort_blk) break;
-    if (tid == 0) {
-      const int np = z + kRPr;
-      if (np <= last_p) {
-        const int s = r % kRPr;
-        mbar_expect_tx(&barP[s], pbytes);
-        ++armP[s];
-        tma3(spr + s * kPStage, &tm_rc, hx, hy, np + kHaloR, &barP[s]);
-        tma3(spb + s * kPStage, &tm_bc, hx, hy, np + kHaloR, &barP[s]);
-      }
-      const int nt_ = z + kRTr;
-      if (nt_ < ze) {
-        const int s = r % kRTr;
-        float *t = st + s * 5 * kTTile;
-        const uint32_t tb = tbytes_of(nt_);
-        mbar_expect_tx(&barT[s], tb);
-        ++armT[s];
-        tma3(t, &tm_a, tx, ty, nt_ + kHaloR, &barT[s]);
-        tma3(t + kTTile, &tm_rn, tx, ty, nt_ + kHaloR, &barT[s]);
-        tma3(t + 2 * kTTile, &tm_bn, tx, ty, nt_ + kHaloR, &barT[s]);
-        if (tb > 3u * sizeof(float) * kTTile) {
-          tma3(t + 3 * kTTile, &tm_num, tx, ty, nt_ + kHaloR, &barT[s]);
-          tma3(t + 4 * kTTile, &tm_den, tx, ty, nt_ + kHaloR, &barT[s]);
+  if (w == 2 * kTY) {
+    if (lane == 0) {
+      const uint32_t pbytes = 2 * sizeof(float) * kPStage;
+      int gp = 0, gt = 0;
+      bool ok = true;
+      auto issueP = [&](int plane, int hx, int hy) {
+        const int s = gp % kRPr, f = gp / kRPr;
+        if (f > 0) ok = mbar_wait_ab(&emptyP[s], (f - 1) & 1, abort_blk);
+        if (!ok) return;
+        mbar_expect_tx(&fullP[s], pbytes);
+        tma3(spr + s * kPStage, &tm_rc, hx, hy, plane + kHaloR, &fullP[s]);
+        tma3(spb + s * kPStage, &tm_bc, hx, hy, plane + kHaloR, &fullP[s]);
+        ++gp;
+      };
+      auto issueT = [&](int plane, int tx, int ty, bool tile_img) {
+        const int s = gt % kRTr, f = gt / kRTr;
+        if (f > 0) ok = mbar_wait_ab(&emptyT[s], (f - 1) & 1, abort_blk);
+        if (!ok) return;
+        const bool img = tile_img && plane >= A.iz0 && plane < A.iz1;
+        mbar_expect_tx(&fullT[s], (img ? 5u : 3u) * sizeof(float) * kTTile);
+        float *t5 = st + s * 5 * kTTile;
+        tma3(t5, &tm_a, tx, ty, plane + kHaloR, &fullT[s]);
+        tma3(t5 + kTTile, &tm_rn, tx, ty, plane + kHaloR, &fullT[s]);
+        tma3(t5 + 2 * kTTile, &tm_bn, tx, ty, plane + kHaloR, &fullT[s]);
+        if (img) {
+          tma3(t5 + 3 * kTTile, &tm_num, tx, ty, plane + kHaloR, &fullT[s]);
+          tma3(t5 + 4 * kTTile, &tm_den, tx, ty, plane + kHaloR, &fullT[s]);
+        }
+        ++gt;
+      };
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        const Tile3 T = tile_of(t, gx, gy, A.zc, L.NZ);
+        const int hx = T.bx * kTileX + kHaloX - 4, hy = T.by * kTY;
+        const int tx = T.bx * kTileX + kHaloX, ty = T.by * kTY + kHaloR;
+        // num/den tiles are streamed only where the tile meets the image box
+        const bool tile_img = (T.by * kTY < A.iy1) && (T.by * kTY + kTY > A.iy0) && (T.bx * kTileX < A.ix1) &&
+                              (T.bx * kTileX + kTileX > A.ix0);
+        for (int i = 0; ok && i < 8; ++i) issueP(T.zb - 4 + i, hx, hy);
+        for (int r = 0; ok && r < T.ze - T.zb; ++r) {
+          issueP(T.zb + r + 4, hx, hy);
+          if (ok) issueT(T.zb + r, tx, ty, tile_img);
         }
       }
+      if (*abort_blk) {
+        flag_error(A.err, 1);
+        for (int k = max(0, gp - kRPr); k < gp; ++k) mbar_wait(&fullP[k % kRPr], (k / kRPr) & 1);
+        for (int k = max(0, gt - kRTr); k < gt; ++k) mbar_wait(&fullT[k % kRTr], (k / kRTr) & 1);
+      }
     }
+    return;
+  }
+  const bool is_r = w < kTY;                // p^R group, else pbar group
+  const int row = is_r ? w : w - kTY;
+  const bool upd = is_r ? do_r : do_b;
+  const float *cur = is_r ? A.rc : A.bc;
+  float *nxt = is_r ? A.rn : A.bn;
+  const float *sp = is_r ? spr : spb;
+  const int tslot = is_r ? 1 : 2;
+  const int src = is_r ? A.info->src_off : -1;
+  const float fsrc = (is_r && do_r) ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
+  const int rowc = (row + 4) * kHaloW + lane * 4;
+  int gp = 0, gt = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile3 T = tile_of(t, gx, gy, A.zc, L.NZ);
+    const int x0 = T.bx * kTileX + lane * 4, y = T.by * kTY + row;
+    const bool xok = x0 < L.NX4, yok = y < L.NY;
+    const bool img_xy = is_r && xok && yok && y >= A.iy0 && y < A.iy1 && x0 + 3 >= A.ix0 && x0 < A.ix1;
+    const int col = L.origin + y * L.pitch + x0;
+    const int nplanes = T.ze - T.zb;
+    float4 q[9];
+    bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      qr[k] = qr[k + 1];
-      qb[k] = qb[k + 1];
+    for (int j = 0; j < 8; ++j) {
+      ok = ok && mbar_wait_ab(&fullP[(gp + j) % kRPr], ((gp + j) / kRPr) & 1, abort_blk);
+      q[j] = lds4(sp + ((gp + j) % kRPr) * kPStage + rowc + 4);
     }
-  }
-  if (abort_blk && tid == 0) {
-    flag_error(A.err, 1);
-    for (int s = 0; s < kRPr; ++s)
-      if (armP[s]) mbar_wait(&barP[s], (armP[s] - 1) & 1);
-    for (int s = 0; s < kRTr; ++s)
-      if (armT[s]) mbar_wait(&barT[s], (armT[s] - 1) & 1);
-  }
-  // receivers of this tile (Eq. 2 source term) after the block's stores
-  if (do_b) {
-    const int bid = (blockIdx.z * gridDim.y + by) * gridDim.x + bx;
-    const int beg = A.tile_ptr[bid], end = A.tile_ptr[bid + 1];
-    if (end > beg) {
-      __threadfence();
-      __syncthreads();
-      const int nrec = A.info->nrec;
-      const float sc = A.info->rec_scale;
-      for (int k = beg + tid; k < end; k += blockDim.x * blockDim.y) {
-        const int rr = A.tile_rec[k];
-        const int o = A.rec_off[rr];
-        atomicAdd(A.bn + o, sc * A.a[o] * A.seis_t[(long long)A.n * nrec + rr]);
+    ok = __all_sync(0xffffffffu, ok);  // keep the warp's decision uniform
+    if (lane == 0)
+      for (int j = 0; j < 4; ++j) mbar_arrive(&emptyP[(gp + j) % kRPr]);
+    for (int r = 0; ok && r < nplanes; ++r) {
+      const int z = T.zb + r;
+      const int top = gp + r + 8, cen = gp + r + 4, tk = gt + r;
+      ok = mbar_wait_ab(&fullP[top % kRPr], (top / kRPr) & 1, abort_blk) &&
+           mbar_wait_ab(&fullT[tk % kRTr], (tk / kRTr) & 1, abort_blk);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      q[8] = lds4(sp + (top % kRPr) * kPStage + rowc + 4);
+      if (xok && yok) {
+        const int o = col + z * L.plane;
+        const float *tt = st + (tk % kRTr) * 5 * kTTile + row * 128 + lane * 4;
+        const float4 av = lds4(tt);
+        const int cs = (cen % kRPr) * kPStage + rowc;
+        if (upd) {
+          float4 v = leap4_3d(sp + cs, q, lds4(tt + tslot * kTTile), av);
+          const int d = src - o;
+          if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * fsrc);
+          st4(nxt + o, v);
+        }
+        if (img_xy && z >= A.iz0 && z < A.iz1) {
+          const float4 b = lds4(spb + cs + 4);  // pbar_n at this node
+          st4(A.num + o, add4(lds4(tt + 3 * kTTile), masked_prod(q[4], b, x0, A.ix0, A.ix1)));
+          st4(A.den + o, add4(lds4(tt + 4 * kTTile), masked_prod(q[4], q[4], x0, A.ix0, A.ix1)));
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&emptyP[cen % kRPr]);
+        mbar_arrive(&emptyT[tk % kRTr]);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+    }
+    if (!ok) break;
+    __syncwarp();
+    if (lane == 0)
+      for (int j = nplanes + 4; j < nplanes + 8; ++j) mbar_arrive(&emptyP[(gp + j) % kRPr]);
+    gp += nplanes + 8;
+    gt += nplanes;
+    // Eq. 2 source term at this warp's receivers (its row of the tile), after
+    // the warp's own stores of pbar_{n-1}
+    if (!is_r && do_b) {
+      const int cell = t * kTY + row;
+      const int beg = A.tile_ptr[cell], end = A.tile_ptr[cell + 1];
+      if (end > beg) {
+        __threadfence();
+        __syncwarp();
+        const int nrec = A.info->nrec;
+        const float sc = A.info->rec_scale;
+        for (int k = beg + lane; k < end; k += 32) {
+          const int rr = A.tile_rec[k];
+          const int o = A.rec_off[rr];
+          atomicAdd(A.bn + o, sc * A.a[o] * A.seis_t[(long long)A.n * nrec + rr]);
+        }
       }
     }
   }
@@ -451,6 +519,17 @@ bool make_map(CUtensorMap *m, const Lay &L, const float *buf, int box_x, int box
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// One block per resident slot (at most one per tile).
+int persistent_grid(const Lay &L, int zc, int ty, const void *fn, int threads, size_t smem) {
+  const int ntiles = cdiv(L.NX, kTileX) * cdiv(L.NY, ty) * cdiv(L.NZ, zc);
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+  const int slots = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  return ntiles < slots ? ntiles : slots;
+}
+
 } // namespace
 
 int tile_rows_3d() { return kTY; }
@@ -459,17 +538,19 @@ int tile_rows_3d() { return kTY; }
 // padded node plus (32, 4, 4).  Field pointers passed in StepArgs/RevArgs are
 // buffer starts (the kernels add L.origin for plain loads and stores).
 bool launch_fwd3d(const StepArgs &A, cudaStream_t s) {
+  constexpr int TY = kTYf;
+  constexpr size_t smem = fwd_smem<TY>();
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fwd3d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    cudaFuncSetAttribute(k_fwd3d_tma<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   CUtensorMap mc, ma, mo;
-  if (!make_map(&mc, A.L, A.cur, kHaloW, kTY + 8) || !make_map(&ma, A.L, A.a, kTileX, kTY) ||
-      !make_map(&mo, A.L, A.nxt, kTileX, kTY))
+  if (!make_map(&mc, A.L, A.cur, kHaloW, TY + 8) || !make_map(&ma, A.L, A.a, kTileX, TY) ||
+      !make_map(&mo, A.L, A.nxt, kTileX, TY))
     return false;
-  dim3 grid(cdiv(A.L.NX, kTileX), cdiv(A.L.NY, kTY), cdiv(A.L.NZ, A.zc));
-  k_fwd3d_tma<<<grid, dim3(32, kTY), kFwdSmem, s>>>(mc, ma, mo, A);
+  k_fwd3d_tma<TY><<<persistent_grid(A.L, A.zc, TY, (const void *)k_fwd3d_tma<TY>, 32 * (TY + 1), smem),
+                    dim3(32, TY + 1), smem, s>>>(mc, ma, mo, A);
   return true;
 }
 
@@ -485,8 +566,8 @@ bool launch_rev3d(const RevArgs &A, cudaStream_t s) {
       !make_map(&mbn, A.L, A.bn, kTileX, kTY) || !make_map(&mnum, A.L, A.num, kTileX, kTY) ||
       !make_map(&mden, A.L, A.den, kTileX, kTY))
     return false;
-  dim3 grid(cdiv(A.L.NX, kTileX), cdiv(A.L.NY, kTY), cdiv(A.L.NZ, A.zc));
-  k_rev3d_tma<<<grid, dim3(32, kTY), kRevSmem, s>>>(mr, mb, ma, mrn, mbn, mnum, mden, A);
+  k_rev3d_tma<<<persistent_grid(A.L, A.zc, kTY, (const void *)k_rev3d_tma, 32 * (2 * kTY + 1), kRevSmem),
+                dim3(32, 2 * kTY + 1), kRevSmem, s>>>(mr, mb, ma, mrn, mbn, mnum, mden, A);
   return true;
 }
 
