@@ -68,6 +68,10 @@ def _L():
             lib.orc_rbc_velocity.restype = i
             lib.orc_coef.argtypes = [C.c_long, P, d, d, P, P]
             lib.orc_stencil_weights.argtypes = [P]
+            lib.orc_fwi_grad.argtypes = [i, i, i, i, P, d, d, i, P, P, i, P, P, i, i, i, i, P]
+            lib.orc_fwi_grad.restype = d
+            lib.orc_misfit.argtypes = [i, i, i, i, P, d, i, P, P, i, P, P]
+            lib.orc_misfit.restype = d
             _lib = lib
     return _lib
 
@@ -241,3 +245,26 @@ def coef(v, dt, h):
     a32 = np.empty(v.shape, np.float32)
     _L().orc_coef(v.size, _p(v), float(dt), float(h), _p(a64), _p(a32))
     return a64, a32
+
+
+def fwi_grad(a, h, dt, nt, src, wavelet, rec, d_obs, nb, interior):
+    """Exact discrete adjoint gradient of J = 1/2 ||record - d_obs||^2 with
+    respect to the interior velocity (random boundary fixed).  Returns (J, g)."""
+    a = _f64(a)
+    nd, NX, NY, NZ = _dims(a.shape)
+    nx, ny, nz = interior
+    g = np.zeros((nz, nx) if nd == 2 else (nz, ny, nx))
+    rec = _i32(np.asarray(rec).reshape(-1, 3))
+    J = _L().orc_fwi_grad(nd, NX, NY, NZ, _p(a), float(h), float(dt), int(nt), _p(_i32(src)),
+                          _p(_f64(wavelet)), rec.shape[0], _p(rec), _p(_f64(d_obs)), int(nb), int(nx),
+                          int(ny if nd == 3 else 1), int(nz), _p(g))
+    return J, g
+
+
+def misfit(a, h, nt, src, wavelet, rec, d_obs):
+    """J = 1/2 sum (record - d_obs)^2 of Algorithm 1's record."""
+    a = _f64(a)
+    nd, NX, NY, NZ = _dims(a.shape)
+    rec = _i32(np.asarray(rec).reshape(-1, 3))
+    return _L().orc_misfit(nd, NX, NY, NZ, _p(a), float(h), int(nt), _p(_i32(src)), _p(_f64(wavelet)),
+                           rec.shape[0], _p(rec), _p(_f64(d_obs)))

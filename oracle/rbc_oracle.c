@@ -412,3 +412,96 @@ void orc_coef(long n, const double *v, double dt, double h, double *a64,
     if (a32) a32[i] = (float)a;
   }
 }
+
+/* ------------------- FWI velocity gradient (exact discrete adjoint) -------------------
+ * Not in the paper: the gradient of the least-squares misfit of Algorithm 1's
+ * record, J = 1/2 sum_n sum_r (p^n(rec_r) - d_obs[r][n])^2, with respect to the
+ * interior velocity, the random boundary held fixed.  Written from the
+ * Lagrangian of the recursion C_{n+1} = p^{n+1} - 2p^n + p^{n-1} - A L8 p^n - s_n
+ * (A = diag(a), s_n = -a_s f[n] h^(2-d) e_s), n = 0..N-1:
+ *   adjoint:  lambda^n = 2 lambda^{n+1} - lambda^{n+2} + L8(a lambda^{n+1}) - R^T r_n,
+ *             n = N..1, lambda^{N+1} = lambda^{N+2} = 0, r_n = R p^n - d_obs[.][n];
+ *   gradient: dJ/da_i = sum_{n=0}^{N-1} lambda_i^{n+1} (-(L8 p^n)_i + delta_is f[n] h^(2-d));
+ *             dJ/dv_i = dJ/da_i * 2 a_i / v_i,  v_i = sqrt(a_i) h / dt.
+ * p^n is rebuilt backwards from p^{N-1}, p^N (the random boundary keeps the
+ * recursion reversible).  grad_v: interior (nz, ny, nx), written.  Returns J.
+ */
+double orc_fwi_grad(int ndim, int NX, int NY, int NZ, const double *a, double h, double dt, int nt,
+                    const int *src, const double *wavelet, int nrec, const int *rec,
+                    const double *d_obs, int nb, int nx, int ny, int nz, double *grad_v) {
+  dims_t g = mkdims(ndim, NX, NY, NZ);
+  long N = npts(&g);
+  if (ndim == 2) ny = 1;
+  long yoff = (ndim == 3) ? nb : 0;
+  double *seis = malloc((size_t)nrec * (nt + 1) * sizeof(double));
+  double *pA = malloc(N * sizeof(double)), *pB = malloc(N * sizeof(double)), *pC = calloc(N, sizeof(double));
+  double *l0 = calloc(N, sizeof(double)), *l1 = calloc(N, sizeof(double)), *l2 = calloc(N, sizeof(double));
+  double *al = calloc(N, sizeof(double)), *ga = calloc(N, sizeof(double));
+  double J = 0.0;
+  orc_model(ndim, NX, NY, NZ, a, h, nt, src, wavelet, nrec, rec, seis, pA, pB, 0, NULL, NULL);
+  for (long k = 0; k < (long)nrec * (nt + 1); ++k) {
+    seis[k] -= d_obs[k]; /* residual */
+    J += 0.5 * seis[k] * seis[k];
+  }
+  long s = ridx(&g, src);
+  double ps = point_scale(ndim, h);
+  double *p_next = pC;  /* p^{n+1} (unused at n = N) */
+  double *p_cur = pB;   /* p^n                       */
+  double *p_prev = pA;  /* p^{n-1}                   */
+  double *lam1 = l1;    /* lambda^{n+1}              */
+  double *lam2 = l2;    /* lambda^{n+2}              */
+  double *lam0 = l0;    /* lambda^n (being formed)   */
+  for (int n = nt; n >= 0; --n) {
+    /* gradient term of constraint C_{n+1} */
+    if (n <= nt - 1) {
+      for (long z = 0; z < g.NZ; ++z)
+        for (long y = 0; y < g.NY; ++y)
+          for (long x = 0; x < g.NX; ++x) {
+            long i = idx(&g, x, y, z);
+            double t = -lap8(p_cur, &g, x, y, z);
+            if (i == s) t += wavelet[n] * ps;
+            ga[i] += lam1[i] * t;
+          }
+    }
+    if (n == 0) break;
+    /* adjoint step: lambda^n */
+    for (long i = 0; i < N; ++i) al[i] = a[i] * lam1[i];
+    for (long z = 0; z < g.NZ; ++z)
+      for (long y = 0; y < g.NY; ++y)
+        for (long x = 0; x < g.NX; ++x) {
+          long i = idx(&g, x, y, z);
+          lam0[i] = 2.0 * lam1[i] - lam2[i] + lap8(al, &g, x, y, z);
+        }
+    for (int r = 0; r < nrec; ++r) lam0[ridx(&g, rec + 3 * r)] -= seis[(long)r * (nt + 1) + n];
+    /* rebuild p^{n-1} (stored panel at n = N) */
+    if (n < nt) {
+      leapfrog(&g, a, p_next, p_cur, p_prev);
+      p_prev[s] -= a[s] * wavelet[n] * ps;
+    }
+    double *t1 = p_next; p_next = p_cur; p_cur = p_prev; p_prev = t1;
+    double *t2 = lam2; lam2 = lam1; lam1 = lam0; lam0 = t2;
+  }
+  for (long z = 0; z < nz; ++z)
+    for (long y = 0; y < ny; ++y)
+      for (long x = 0; x < nx; ++x) {
+        long i = idx(&g, x + nb, y + yoff, z + nb);
+        double v = sqrt(a[i]) * h / dt;
+        grad_v[(z * ny + y) * (long)nx + x] = ga[i] * 2.0 * a[i] / v;
+      }
+  free(seis); free(pA); free(pB); free(pC); free(l0); free(l1); free(l2); free(al); free(ga);
+  return J;
+}
+
+/* J alone (for finite differences): 1/2 sum (record - d_obs)^2. */
+double orc_misfit(int ndim, int NX, int NY, int NZ, const double *a, double h, int nt, const int *src,
+                  const double *wavelet, int nrec, const int *rec, const double *d_obs) {
+  double *seis = malloc((size_t)nrec * (nt + 1) * sizeof(double));
+  orc_model(ndim, NX, NY, NZ, a, h, nt, src, wavelet, nrec, rec, seis, NULL, NULL, 0, NULL, NULL);
+  double J = 0.0;
+  for (long k = 0; k < (long)nrec * (nt + 1); ++k) {
+    double r = seis[k] - d_obs[k];
+    J += 0.5 * r * r;
+  }
+  free(seis);
+  return J;
+}
