@@ -153,6 +153,39 @@ int rbc_image_stack(const rbc_grid *shot, const float *num_dev,
                     const rbc_grid *survey, float *image_dev, void *stream);
 
 /*
+ * rbc_fwi_forward -- misfit of one shot for full-waveform inversion (an
+ * extension built on Algorithm 1; 2-D grids).
+ *   Models the shot like rbc_model, then resid = record - dobs_dev and
+ *   misfit_dev += 1/2 sum resid^2 (fp64).  dobs_dev, resid_dev: (nrec, nt + 1)
+ *   fp32; misfit_dev: one double; panels_dev (may be NULL): 2 dense padded
+ *   fields, p^{nt-1} then p^{nt} -- the only state the gradient needs, since
+ *   the random boundary lets rbc_fwi_backward rebuild the wavefield backwards
+ *   instead of storing or checkpointing it.
+ * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D), RBC_ECUDA.
+ */
+int rbc_fwi_forward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
+                    int nrec, const int *rec_host, const float *dobs_dev,
+                    float *resid_dev, double *misfit_dev, float *panels_dev,
+                    void *stream);
+
+/*
+ * rbc_fwi_backward -- gradient of that misfit with respect to the interior
+ * velocity (random boundary held fixed), by the exact discrete adjoint of the
+ * leapfrog: with mu = a lambda the adjoint is the same recursion run backwards
+ * with -a_r resid injected, and
+ *   dJ/da_i = -(1/a_i^2) sum_n mu_i^{n+1} (p^{n+1} - 2 p^n + p^{n-1})_i,
+ *   dJ/dv_i = dJ/da_i * 2 a_i / v_i,
+ * p^n rebuilt backwards from the two panels (Eq. 6 with the source
+ * re-subtracted).  resid_dev: from rbc_fwi_forward; panels_dev: the panels
+ * it exported, or NULL to use those the context still holds from that call.
+ * grad_dev: interior (nz, nx) fp32, ACCUMULATED (+=).
+ * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D), RBC_ECUDA.
+ */
+int rbc_fwi_backward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
+                     int nrec, const int *rec_host, const float *resid_dev,
+                     const float *panels_dev, float *grad_dev, void *stream);
+
+/*
  * rbc_set_snapshots -- ask the next rbc_model / rbc_rtm_shot on this context
  * to copy wavefields at chosen time levels (Figure 1's propagation and
  * reconstruction panels).  levels_host[k] in [0, nt]; pf_dev / pr_dev / pb_dev

@@ -66,6 +66,10 @@ def _load():
     lib.rbc_set_snapshots.argtypes = [P, I, P, P, P, P]
     lib.rbc_get_panels.argtypes = [P, P, P, P]
     lib.rbc_phase_timing.argtypes = [P, I, P]
+    lib.rbc_fwi_forward.argtypes = [P, P, P, I, P, P, P, P, P, P]
+    lib.rbc_fwi_backward.argtypes = [P, P, P, I, P, P, P, P, P]
+    lib.rbc_fwi_forward.restype = I
+    lib.rbc_fwi_backward.restype = I
     lib.rbc_model_static.argtypes = [G, P, P, P, I, P, P, P]
     lib.rbc_model_static.restype = I
     lib.rbc_last_error.restype = C.c_char_p
@@ -80,7 +84,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc_rtm_shot",
             "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing",
-            "rbc_model_static", "rbc_last_error", "rbc_launch_count")
+            "rbc_model_static", "rbc_fwi_forward", "rbc_fwi_backward", "rbc_last_error",
+            "rbc_launch_count")
 
 
 def _check(code):
@@ -185,6 +190,28 @@ def rbc_model_static(grid, a, src, wavelet, rec, seis, stream=None):
                                  _dev(wavelet, None, "wavelet"), r.shape[0],
                                  r.ctypes.data_as(C.c_void_p) if r.size else None,
                                  _dev(seis, None, "seis") if r.shape[0] else None, _stream(stream)))
+
+
+def rbc_fwi_forward(ctx, src, wavelet, rec, dobs, resid, misfit, panels=None, stream=None):
+    """misfit (float64 CUDA tensor of one element) += 1/2 ||record - dobs||^2;
+    resid = record - dobs; panels (2, *padded) receives p^{nt-1}, p^{nt}."""
+    s = _nodes(src, 1)
+    r = _nodes(rec)
+    if not (misfit.is_cuda and misfit.dtype == torch.float64 and misfit.numel() == 1):
+        raise TypeError("misfit must be a one-element float64 CUDA tensor")
+    _check(_lib.rbc_fwi_forward(C.c_void_p(ctx), s.ctypes.data_as(C.c_void_p), _dev(wavelet, None, "wavelet"),
+                                r.shape[0], r.ctypes.data_as(C.c_void_p), _dev(dobs, None, "dobs"),
+                                _dev(resid, None, "resid"), C.c_void_p(misfit.data_ptr()),
+                                _dev(panels, None, "panels"), _stream(stream)))
+
+
+def rbc_fwi_backward(ctx, src, wavelet, rec, resid, panels, grad, stream=None):
+    """grad (interior) += dJ/dv by the adjoint, from the residual and the two panels."""
+    s = _nodes(src, 1)
+    r = _nodes(rec)
+    _check(_lib.rbc_fwi_backward(C.c_void_p(ctx), s.ctypes.data_as(C.c_void_p), _dev(wavelet, None, "wavelet"),
+                                 r.shape[0], r.ctypes.data_as(C.c_void_p), _dev(resid, None, "resid"),
+                                 _dev(panels, None, "panels"), _dev(grad, None, "grad"), _stream(stream)))
 
 
 def rbc_last_error() -> str:

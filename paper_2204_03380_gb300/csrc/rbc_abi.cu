@@ -106,9 +106,11 @@ struct rbc_ctx {
   int ntiles = 0;
   float *seis_t = nullptr;
   cudaStream_t cap = nullptr;
-  // cached graphs: 0 = modeling loop, 1 = RTM forward phase, 2 = RTM reverse phase
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
-  long long gnodes[3] = {0, 0, 0};
+  // cached graphs: 0 = modeling loop, 1 = RTM forward phase, 2 = RTM reverse phase,
+  // 3 = FWI adjoint phase
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long gnodes[4] = {0, 0, 0, 0};
+  double *misfit_tmp = nullptr;
   // phase timing (rbc_phase_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // three events per timed shot
@@ -128,7 +130,7 @@ struct rbc_ctx {
 namespace {
 
 void drop_graphs(rbc_ctx *c) {
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
     c->gexec[k] = nullptr;
   }
@@ -157,7 +159,7 @@ int ensure_receivers(rbc_ctx *c, int nrec) {
   c->rec_cap = 0;
   CK(cudaMalloc(&c->rec_off, sizeof(int) * cap));
   CK(cudaMalloc(&c->tile_rec, sizeof(int) * cap));
-  CK(cudaMalloc(&c->seis_t, sizeof(float) * (size_t)cap * (c->g.nt + 1)));
+  CK(cudaMalloc(&c->seis_t, sizeof(float) * (size_t)cap * (c->g.nt + 2)));  // + 1 row for the FWI adjoint
   c->rec_cap = cap;
   return RBC_OK;
 }
@@ -310,6 +312,8 @@ int enqueue_reverse(rbc_ctx *c, cudaStream_t s) {
     A.n = n;
     A.do_r = (n < nt && n > 0) ? 1 : 0;  // p^R_{nt-1} is the stored panel
     A.do_b = (n > 0) ? 1 : 0;
+    A.n_src = n;
+    A.mode = 0;
     if (!launch_rev(A, s)) return fail(RBC_ECUDA, "tensor map encoding failed");
     ++g_launches;
   }
@@ -332,6 +336,54 @@ int enq_model(rbc_ctx *c, cudaStream_t s, int) {
 int enq_rtm_fwd(rbc_ctx *c, cudaStream_t s, int) { return enqueue_forward(c, s, 0); }
 
 int enq_rtm_rev(rbc_ctx *c, cudaStream_t s, int) { return enqueue_reverse(c, s); }
+
+// FWI adjoint phase (2-D): at kernel level m = nt+1 .. 1 the adjoint field
+// mu = a lambda goes from (mu^m, mu^{m+1}) to mu^{m-1} with the adjoint record
+// row m injected, while the reconstruction runs one level behind: (p^{m-1},
+// p^m) -> p^{m-2}, so that num += mu^m (p^m - 2 p^{m-1} + p^{m-2}).
+int enq_fwi_adj(rbc_ctx *c, cudaStream_t s, int) {
+  const Lay &L = c->L;
+  const size_t bytes = sizeof(float) * (size_t)L.total;
+  CK(cudaMemsetAsync(c->q[0], 0, bytes, s));
+  CK(cudaMemsetAsync(c->q[1], 0, bytes, s));
+  CK(cudaMemsetAsync(c->num, 0, bytes, s));
+  RevArgs A{};
+  A.L = L;
+  A.a = c->a;
+  A.num = c->num;
+  A.den = c->den;
+  A.info = c->info;
+  A.wav = c->wav;
+  A.rec_off = c->rec_off;
+  A.tile_ptr = c->tile_ptr;
+  A.tile_rec = c->tile_rec;
+  A.seis_t = c->seis_t;
+  const int nb = c->g.nb;
+  A.ix0 = nb;
+  A.ix1 = nb + c->g.nx;
+  A.iz0 = nb;
+  A.iz1 = nb + c->g.nz;
+  A.iy0 = 0;
+  A.iy1 = 1;
+  A.zc = c->zc;
+  A.err = c->err_dev;
+  A.mode = 1;
+  const int nt = c->g.nt;
+  for (int m = nt + 1; m >= 1; --m) {
+    A.rc = c->p[(m - 1) & 1];
+    A.rn = c->p[m & 1];
+    A.bc = c->q[m & 1];
+    A.bn = c->q[(m + 1) & 1];
+    A.n = m;           // adjoint record row injected
+    A.n_src = m - 1;   // source term of the reconstructed step
+    A.do_r = (m <= nt) ? 1 : 0;  // p^{nt-1} is a stored panel
+    A.do_b = 1;
+    if (!launch_rev(A, s)) return fail(RBC_ECUDA, "launch failed");
+    ++g_launches;
+  }
+  CKL();
+  return RBC_OK;
+}
 
 int record_event(rbc_ctx *c, cudaStream_t s) {
   cudaEvent_t e;
@@ -578,6 +630,64 @@ int rbc_image_stack(const rbc_grid *shot, const float *num_dev, const float *den
   g_launches += 2;
   CKL();
   CK(cudaFreeAsync(dmax, s));
+  return RBC_OK;
+}
+
+int rbc_fwi_forward(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nrec, const int *rec_host,
+                    const float *dobs_dev, float *resid_dev, double *misfit_dev, float *panels_dev, void *stream) {
+  if (!c) return fail(RBC_EINVAL, "ctx is NULL");
+  if (c->L.ndim != 2) return fail(RBC_ENOTSUP, "the FWI gradient is built for 2-D grids");
+  if (!wavelet_dev || nrec < 1 || !dobs_dev || !resid_dev || !misfit_dev)
+    return fail(RBC_EINVAL, "NULL pointer or no receivers");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  rc = upload_shot(c, src_host, nrec, rec_host, 1, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->wav, wavelet_dev, sizeof(float) * c->g.nt, cudaMemcpyDeviceToDevice, s));
+  rc = run_loop(c, 0, enq_model, s);
+  if (rc) return rc;
+  launch_fwi_residual(c->seis_t, dobs_dev, resid_dev, misfit_dev, nrec, c->g.nt, s);
+  ++g_launches;
+  const int nt = c->g.nt;
+  const long long n = field_elems(c);
+  if (panels_dev) {
+    launch_copy_out(c->L, c->p[(nt - 1) & 1], panels_dev, s);
+    launch_copy_out(c->L, c->p[nt & 1], panels_dev + n, s);
+    g_launches += 2;
+  }
+  CKL();
+  c->have_panels = 1;
+  return RBC_OK;
+}
+
+int rbc_fwi_backward(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nrec, const int *rec_host,
+                     const float *resid_dev, const float *panels_dev, float *grad_dev, void *stream) {
+  if (!c) return fail(RBC_EINVAL, "ctx is NULL");
+  if (c->L.ndim != 2) return fail(RBC_ENOTSUP, "the FWI gradient is built for 2-D grids");
+  if (!wavelet_dev || nrec < 1 || !resid_dev || !grad_dev) return fail(RBC_EINVAL, "NULL pointer or no receivers");
+  if (!panels_dev && !c->have_panels) return fail(RBC_EINVAL, "no panels: pass panels_dev or run rbc_fwi_forward");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  rc = upload_shot(c, src_host, nrec, rec_host, 1, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->wav, wavelet_dev, sizeof(float) * c->g.nt, cudaMemcpyDeviceToDevice, s));
+  const int nt = c->g.nt;
+  if (panels_dev) {
+    launch_copy_in(c->L, panels_dev, c->p[(nt - 1) & 1], s);
+    launch_copy_in(c->L, panels_dev + field_elems(c), c->p[nt & 1], s);
+    g_launches += 2;
+  }
+  // adjoint record: row m = -resid[.][m-1] / h^(2-d), injected as + h^(2-d) a row
+  launch_fwi_adjoint_source(resid_dev, c->seis_t, nrec, nt, -1.0f, s);
+  ++g_launches;
+  rc = run_loop(c, 3, enq_fwi_adj, s);
+  if (rc) return rc;
+  launch_fwi_finalize(c->L, c->num, c->a, grad_dev, c->g.nb, c->g.nx, c->g.nz, c->g.dt, c->g.h, s);
+  ++g_launches;
+  CKL();
+  c->have_panels = 0;
   return RBC_OK;
 }
 

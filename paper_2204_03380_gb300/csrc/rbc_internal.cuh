@@ -92,6 +92,8 @@ struct RevArgs {
   int ix0, ix1, iy0, iy1, iz0, iz1; // interior box [lo, hi) in padded nodes
   int zc;
   int *err;
+  int mode;                       // 0: imaging integrals; 1: FWI gradient (2-D)
+  int n_src;                      // time index of the re-subtracted source
 };
 
 // ---- launch geometry shared by the host (CSR) and the kernels ----
@@ -121,6 +123,12 @@ void launch_max(const float *x, long long n, unsigned int *out_bits, cudaStream_
 void launch_image_stack(const float *num, const float *den, const unsigned int *maxbits,
                         float eps_rel, int nx, int ny, int nz, int off_x, int off_y, int sx,
                         int sy, float *image, cudaStream_t s);
+void launch_fwi_residual(const float *seis_t, const float *dobs, float *resid, double *misfit, int nrec,
+                         int nt, cudaStream_t s);
+void launch_fwi_adjoint_source(const float *resid, float *seis_t, int nrec, int nt, float scale,
+                               cudaStream_t s);
+void launch_fwi_finalize(const Lay &L, const float *num, const float *a, float *grad, int nb, int nx,
+                         int nz, double dt, double h, cudaStream_t s);
 void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_int, double v_lo,
                       double v_hi, double v_max, uint64_t seed, int mode, double dt, double h,
                       float *v_pad, float *a, cudaStream_t s);

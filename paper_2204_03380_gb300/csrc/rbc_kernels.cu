@@ -143,11 +143,11 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d(const StepArgs A) {
 
 // One field of the reverse pass: advance (cur, nxt) and return the centre
 // values of `cur` for the imaging condition.
-template <int RZ>
+template <int RZ, bool kInc>
 __device__ __forceinline__ void rev_field2d(const Lay &L, const float *__restrict__ a,
                                             const float *__restrict__ cur, float *__restrict__ nxt,
                                             bool update, int lane, int x0, int zb, bool xok,
-                                            int src, float fsrc, float4 *cen) {
+                                            int src, float fsrc, float4 *cen, float4 *inc) {
   const int col = L.origin + x0;
   if (!update) {
 #pragma unroll
@@ -176,15 +176,27 @@ __device__ __forceinline__ void rev_field2d(const Lay &L, const float *__restric
     if (xok) {
       const float4 av = ldg4(a + o);
       const float4 po = ld4(nxt + o);
-      float4 r = leap4_2d(lf, c, rt, &q[j], po, av);
-      const int d = src - o;
-      if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
+      float4 r;
+      if (kInc) {
+        // the increment p^{n+1} - 2 p^n + p^{n-1} (point term included)
+        const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w, rt.x, rt.y, rt.z, rt.w};
+        r = leap4p_inc(w, &q[j], po, av, &inc[j]);
+        const int d = src - o;
+        if ((unsigned)d < 4u) {
+          point_sub(r, d, cmp(av, d) * fsrc);
+          point_sub(inc[j], d, cmp(av, d) * fsrc);
+        }
+      } else {
+        r = leap4_2d(lf, c, rt, &q[j], po, av);
+        const int d = src - o;
+        if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
+      }
       st4(nxt + o, r);
     }
   }
 }
 
-template <int RZ>
+template <int RZ, bool kGrad>
 __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
   const Lay &L = A.L;
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -193,15 +205,27 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
   const bool xok = x0 < L.NX4;
   const bool active = zb < L.NZ;  // warp-uniform
   if (active) {
-    float4 cr[RZ], cb[RZ];
+    float4 cr[RZ], cb[RZ], inc[RZ];
     const int src = A.info->src_off;
-    const float fsrc = A.do_r ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
+    const float fsrc = A.do_r ? A.wav[A.n_src] * A.info->src_rev : 0.f;  // f[nt] does not exist
     // Eq. 6: reconstruction (exact inverse of the forward step)
-    rev_field2d<RZ>(L, A.a, A.rc, A.rn, A.do_r != 0, lane, x0, zb, xok, src, fsrc, cr);
-    // Eq. 2: receiver wavefield (the record is added below, after the store)
-    rev_field2d<RZ>(L, A.a, A.bc, A.bn, A.do_b != 0, lane, x0, zb, xok, -1, 0.f, cb);
-    // Eq. 3: the two time integrals, interior only
-    if (xok && x0 + 3 >= A.ix0 && x0 < A.ix1) {
+    rev_field2d<RZ, kGrad>(L, A.a, A.rc, A.rn, A.do_r != 0, lane, x0, zb, xok, src, fsrc, cr, inc);
+    // Eq. 2 (or the FWI adjoint): receiver wavefield; the record is added below, after the store
+    rev_field2d<RZ, false>(L, A.a, A.bc, A.bn, A.do_b != 0, lane, x0, zb, xok, -1, 0.f, cb, inc);
+    if (kGrad) {
+      // FWI: num += mu^m (p^m - 2 p^{m-1} + p^{m-2}) on the interior
+      if (A.do_r && xok && x0 + 3 >= A.ix0 && x0 < A.ix1) {
+#pragma unroll
+        for (int j = 0; j < RZ; ++j) {
+          const int z = zb + j;
+          if (z >= A.iz0 && z < A.iz1) {
+            const int o = L.origin + x0 + z * L.pitch;
+            st4(A.num + o, add4(ld4(A.num + o), masked_prod(cb[j], inc[j], x0, A.ix0, A.ix1)));
+          }
+        }
+      }
+    } else if (xok && x0 + 3 >= A.ix0 && x0 < A.ix1) {
+      // Eq. 3: the two time integrals, interior only
 #pragma unroll
       for (int j = 0; j < RZ; ++j) {
         const int z = zb + j;
@@ -245,7 +269,10 @@ bool launch_rev(const RevArgs &A, cudaStream_t s) {
   if (A.L.ndim == 3) return launch_rev3d(A, s);
   int gx, gy, gz, t;
   rev_tiling(A.L, A.zc, &gx, &gy, &gz, &t);
-  k_rev2d<k2dRowsR><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
+  if (A.mode == 1)
+    k_rev2d<k2dRowsR, true><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
+  else
+    k_rev2d<k2dRowsR, false><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
   return true;
 }
 
@@ -374,6 +401,67 @@ void launch_image_stack(const float *num, const float *den, const unsigned int *
   const long long n = (long long)nx * ny * nz;
   k_image_stack<<<grid_for(n, 256), 256, 0, s>>>(num, den, maxbits, eps_rel, nx, ny, nz, off_x, off_y,
                                                  sx, sy, image);
+}
+
+// ------------------------------------------------------------------ FWI ----
+// resid[r][n] = seis_t[n][r] - dobs[r][n]; misfit += 1/2 sum resid^2 (fp64).
+__global__ void k_fwi_residual(const float *__restrict__ seis_t, const float *__restrict__ dobs,
+                               float *__restrict__ resid, double *misfit, int nrec, int nt) {
+  const long long n = (long long)nrec * (nt + 1);
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / (nt + 1)), t = (int)(i % (nt + 1));
+    const float d = seis_t[(long long)t * nrec + r] - dobs[i];
+    resid[i] = d;
+    acc += 0.5 * (double)d * (double)d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(misfit, acc);
+}
+
+void launch_fwi_residual(const float *seis_t, const float *dobs, float *resid, double *misfit, int nrec, int nt,
+                         cudaStream_t s) {
+  const long long n = (long long)nrec * (nt + 1);
+  k_fwi_residual<<<grid_for(n, 256), 256, 0, s>>>(seis_t, dobs, resid, misfit, nrec, nt);
+}
+
+// Adjoint record, time-major with nt + 2 rows: row m = scale * resid[.][m-1]
+// for m = 1..nt+1, row 0 = 0 (the reverse kernel injects row m when it forms
+// level m - 1 of the adjoint field).
+__global__ void k_fwi_adjoint_source(const float *__restrict__ resid, float *__restrict__ seis_t, int nrec, int nt,
+                                     float scale) {
+  const long long n = (long long)nrec * (nt + 2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / nrec), r = (int)(i % nrec);
+    seis_t[i] = m == 0 ? 0.f : scale * resid[(long long)r * (nt + 1) + m - 1];
+  }
+}
+
+void launch_fwi_adjoint_source(const float *resid, float *seis_t, int nrec, int nt, float scale, cudaStream_t s) {
+  const long long n = (long long)nrec * (nt + 2);
+  k_fwi_adjoint_source<<<grid_for(n, 256), 256, 0, s>>>(resid, seis_t, nrec, nt, scale);
+}
+
+// dJ/dv = dJ/da * da/dv with dJ/da = -num / a^2 (num = sum mu p_tt, mu = a
+// lambda) and da/dv = 2 a / v, v = sqrt(a) h / dt:  grad += -2 num dt / (a^1.5 h).
+__global__ void k_fwi_finalize(const Lay L, const float *__restrict__ num, const float *__restrict__ a,
+                               float *__restrict__ grad, int nb, int nx, int nz, double dt, double h) {
+  const long long n = (long long)nx * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), z = (int)(i / nx);
+    const int o = lay_off(L, x + nb, 0, z + nb);
+    const double av = a[o];
+    grad[i] += (float)(-2.0 * (double)num[o] * dt / (av * sqrt(av) * h));
+  }
+}
+
+void launch_fwi_finalize(const Lay &L, const float *num, const float *a, float *grad, int nb, int nx, int nz,
+                         double dt, double h, cudaStream_t s) {
+  const long long n = (long long)nx * nz;
+  k_fwi_finalize<<<grid_for(n, 256), 256, 0, s>>>(L, num, a, grad, nb, nx, nz, dt, h);
 }
 
 // ----------------------------------------------------- random boundary ----

@@ -80,9 +80,7 @@ __device__ __forceinline__ void tma3(float *dst, const CUtensorMap *tm, int x, i
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ float cmp(const float4 &v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
@@ -405,12 +403,11 @@ __global__ void __launch_bounds__(32 * (2 * kTY + 1)) k_rev3d_tma(const __grid_c
   const bool is_r = w < kTY;                // p^R group, else pbar group
   const int row = is_r ? w : w - kTY;
   const bool upd = is_r ? do_r : do_b;
-  const float *cur = is_r ? A.rc : A.bc;
   float *nxt = is_r ? A.rn : A.bn;
   const float *sp = is_r ? spr : spb;
   const int tslot = is_r ? 1 : 2;
   const int src = is_r ? A.info->src_off : -1;
-  const float fsrc = (is_r && do_r) ? A.wav[A.n] * A.info->src_rev : 0.f;  // f[nt] does not exist
+  const float fsrc = (is_r && do_r) ? A.wav[A.n_src] * A.info->src_rev : 0.f;  // f[nt] does not exist
   const int rowc = (row + 4) * kHaloW + lane * 4;
   int gp = 0, gt = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {

@@ -53,4 +53,35 @@ __device__ __forceinline__ float4 leap4p(const float *w, const float4 *zq, const
   return make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
 }
 
+// Same update split as out = base + inc, inc = a * lap (the discrete second
+// time difference p^{n+1} - 2 p^n + p^{n-1} without the point terms), for
+// callers that need the increment itself (the FWI gradient).
+__device__ __forceinline__ float4 leap4p_inc(const float *w, const float4 *zq, const float4 po, const float4 av,
+                                             float4 *inc) {
+  float2 out[2], dd[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float2 p = make_float2(w[4 + 2 * j], w[5 + 2 * j]);
+    const float2 np = neg2(p);
+    float2 s[5];
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+      const float2 xm = make_float2(w[4 + 2 * j - k], w[5 + 2 * j - k]);
+      const float2 xp = make_float2(w[4 + 2 * j + k], w[5 + 2 * j + k]);
+      float2 t = sum_diff2(xm, xp, np);
+      t = __fadd2_rn(t, sum_diff2(half2of(zq[4 - k], j), half2of(zq[4 + k], j), np));
+      s[k] = t;
+    }
+    float2 lap = __fmul2_rn(make_float2(kC4, kC4), s[4]);
+    lap = __ffma2_rn(make_float2(kC3, kC3), s[3], lap);
+    lap = __ffma2_rn(make_float2(kC2, kC2), s[2], lap);
+    lap = __ffma2_rn(make_float2(kC1, kC1), s[1], lap);
+    const float2 base = __fadd2_rn(__fadd2_rn(p, p), neg2(half2of(po, j)));
+    dd[j] = __fmul2_rn(half2of(av, j), lap);
+    out[j] = __fadd2_rn(base, dd[j]);
+  }
+  *inc = make_float4(dd[0].x, dd[0].y, dd[1].x, dd[1].y);
+  return make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+}
+
 } // namespace rbc

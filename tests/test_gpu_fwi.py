@@ -1,0 +1,90 @@
+"""FWI velocity gradient on the GPU (rbc_fwi_forward / rbc_fwi_backward and the
+torch.autograd.Function above them) against the FP64 oracle's exact adjoint
+gradient, itself pinned by finite differences in test_oracle_fwi.py."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from rtm_cases import TOL, f32, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _fwi_case(nx, nz, nb, nt, nshots, seed=0):
+    w = W.scaled(W.SMALL_2D, nx=nx, nz=nz, nb=nb, nt=nt, name="fwi")
+    vt = W.three_layers(nx, nz, (nz * 7 // 20, nz * 14 // 20))
+    zz, xx = np.mgrid[0:nz, 0:nx]
+    vt = vt * (1 + 0.1 * np.exp(-((zz - nz / 2) ** 2 + (xx - nx / 2) ** 2) / (2 * (nz / 20) ** 2)))
+    v0 = W.smooth_slowness(vt, nz / 20)
+    vt, v0 = f32(vt), f32(v0)
+    shots = [W.source_at(w, int(x)) for x in W.shot_columns(w, nshots)]
+    rec = W.surface_line(w, step=2)
+    wav = f32(W.ricker(nt, w.dt, w.f_peak))
+    return w, vt, v0, shots, rec, wav
+
+
+@pytest.mark.parametrize("dims", [(60, 50, 10, 400, 2), (300, 300, 50, 1000, 4)], ids=["small", "300x300_4shots"])
+def test_fwi_gradient_matches_oracle(dims):
+    """The residual record - d_obs is a small difference of two records (their
+    direct waves cancel), so its fp32 error is judged at the scale of the
+    record; the adjoint (the gradient) is judged against the oracle run on the
+    same adjoint source, i.e. d_obs shifted so that the oracle's residual is the
+    GPU's."""
+    import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300.fwi import fwi_misfit
+    w, vt, v0, shots, rec, wav = _fwi_case(*dims)
+
+    def a_of(v):
+        return oracle.coef(oracle.rbc_velocity(v, w.nb, w.v_lo, w.v_hi, w.v_max, w.rbc_seed), w.dt, w.h)[1].astype(float)
+
+    dobs = [oracle.model(a_of(vt), w.h, w.nt, s, wav, rec)["seis"] for s in shots]
+    dsyn = [oracle.model(a_of(v0), w.h, w.nt, s, wav, rec)["seis"] for s in shots]
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    dev = "cuda"
+    v = torch.tensor(v0, dtype=torch.float32, device=dev, requires_grad=True)
+    dt_ = [torch.tensor(d, dtype=torch.float32, device=dev) for d in dobs]
+    wt = torch.tensor(wav, dtype=torch.float32, device=dev)
+    J = fwi_misfit(v, g, shots, wt, rec, dt_, (w.v_lo, w.v_hi, w.v_max, w.rbc_seed))
+    J.backward()
+    # the residuals the GPU formed (same calls as inside the autograd function)
+    a = torch.empty(g.padded, dtype=torch.float32, device=dev)
+    R.rbc_build_velocity(g, v.detach(), w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, a)
+    ctx = R.rbc_create(g, a)
+    misfit = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = []
+    for s, d in zip(shots, dt_):
+        r = torch.empty_like(d)
+        R.rbc_fwi_forward(ctx, s, wt, rec, d, r, misfit)
+        res.append(r.cpu().numpy().astype(np.float64))
+    R.rbc_destroy(ctx)
+    for r, ds, do in zip(res, dsyn, dobs):
+        assert np.linalg.norm(r - (ds - f32(do))) <= TOL * np.linalg.norm(ds)
+    J_gpu = 0.5 * sum(float((r ** 2).sum()) for r in res)
+    assert float(J.detach()) == pytest.approx(J_gpu, rel=1e-5)
+    assert float(misfit) == pytest.approx(J_gpu, rel=1e-6)
+    g_o = np.zeros(v0.shape)
+    for s, r, ds in zip(shots, res, dsyn):
+        _, gs = oracle.fwi_grad(a_of(v0), w.h, w.dt, w.nt, s, wav, rec, ds - r, w.nb, (w.nx, 1, w.nz))
+        g_o += gs
+    gg = v.grad.cpu().numpy()
+    assert rel(gg, g_o) <= TOL, rel(gg, g_o)
+
+
+def test_fwi_gradient_is_zero_at_the_true_model():
+    import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300.fwi import fwi_misfit
+    w, vt, v0, shots, rec, wav = _fwi_case(60, 50, 10, 300, 1)
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    v = torch.tensor(vt, dtype=torch.float32, device="cuda", requires_grad=True)
+    wt = torch.tensor(wav, dtype=torch.float32, device="cuda")
+    a = torch.empty(g.padded, dtype=torch.float32, device="cuda")
+    R.rbc_build_velocity(g, v.detach(), w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, a)
+    ctx = R.rbc_create(g, a)
+    d = torch.empty((len(rec), w.nt + 1), dtype=torch.float32, device="cuda")
+    R.rbc_model(ctx, shots[0], wt, rec, d)
+    R.rbc_destroy(ctx)
+    J = fwi_misfit(v, g, shots, wt, rec, [d], (w.v_lo, w.v_hi, w.v_max, w.rbc_seed))
+    J.backward()
+    assert float(J.detach()) == 0.0 and float(v.grad.abs().max()) == 0.0
