@@ -60,12 +60,13 @@ def parse():
                         "small profiler captures")
     p.add_argument("--interior", type=int, nargs="+", default=None,
                    help="interior size override (nx nz | nx ny nz); only for small profiler captures")
-    p.add_argument("--workload", choices=["survey2d", "shot3d"], default="survey2d",
+    p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d"], default="survey2d",
                    help="survey2d: the 240-shot 2-D survey (default); shot3d: one 3-D shot on "
-                        "500 x 500 x 300 + 40 (one step = one RTM shot)")
+                        "500 x 500 x 300 + 40 (one step = one RTM shot); batch2d: 64 shots of "
+                        "400-1200 columns x 600 rows in one launch per time step (one step = the batch)")
     a = p.parse_args()
     if a.steps is None:
-        a.steps = 30 if a.workload == "survey2d" else 3
+        a.steps = {"survey2d": 30, "shot3d": 3, "batch2d": 5}[a.workload]
     if a.shots_per_step is None:
         a.shots_per_step = 8 if a.workload == "survey2d" else 1
     return a
@@ -221,6 +222,127 @@ def cores_used():
     return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
 
 
+def run_batch(args, rank, world):
+    """batch2d: one step = rbc_batch_rtm over the 64 uneven-aperture shots."""
+    import torch
+    import paper_2204_03380_gb300 as R
+    import workloads as W
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = W.BATCH_2D
+    if args.nt:
+        w = W.dataclasses.replace(w, nt=args.nt, name=f"{w.name}_nt{args.nt}")
+    inp = W.batch_2d_inputs(w)
+    dev = torch.device("cuda", local)
+    wav = torch.tensor(inp["wavelet"], dtype=torch.float32, device=dev)
+    a_mig, seis = [], []
+    for sh in inp["shots"]:
+        g = R.make_grid(2, sh["width"], 1, w.nz, w.nb, w.h, w.dt, w.nt)
+        pair = []
+        for v in (inp["v_true"], inp["v_mig"]):
+            vw = torch.tensor(np.ascontiguousarray(v[:, sh["off_x"]:sh["off_x"] + sh["width"]]),
+                              dtype=torch.float32, device=dev)
+            a = torch.empty(g.padded, dtype=torch.float32, device=dev)
+            R.rbc_build_velocity(g, vw, w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, a)
+            pair.append(a)
+        ctx = R.rbc_create(g, pair[0])
+        d = torch.empty((len(sh["rec"]), w.nt + 1), dtype=torch.float32, device=dev)
+        R.rbc_model(ctx, sh["src"], wav, sh["rec"], d)
+        torch.cuda.synchronize()
+        R.rbc_destroy(ctx)
+        a_mig.append(pair[1])
+        seis.append(d)
+    base = R.make_grid(2, 1, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    b = R.rbc_batch_create(base, [sh["width"] for sh in inp["shots"]], a_mig)
+    info = R.rbc_batch_info(b)
+    image = torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)
+    shots = [dict(src=sh["src"], rec=sh["rec"], seis=d, off_x=sh["off_x"]) for sh, d in zip(inp["shots"], seis)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        R.rbc_batch_rtm(b, shots, wav, R.RBC_REINJECT_SOURCE, EPS_REL, image)
+    barrier()
+    smi = ClockSampler(smi_device_id(torch, local))
+    smi.start()
+    time.sleep(0.3)
+    R.rbc_launch_count(reset=True)
+    R.rbc_batch_timing(b, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record()
+    for _ in range(args.steps):
+        flush.zero_()
+        R.rbc_batch_rtm(b, shots, wav, R.RBC_REINJECT_SOURCE, EPS_REL, image)
+    ev1.record()
+    barrier()
+    phases = R.rbc_batch_timing(b, False)
+    launches = R.rbc_launch_count()
+    clocks = smi.stop()
+    el = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([el], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    npads = [(sh["width"] + 2 * w.nb) * (w.nz + 2 * w.nb) for sh in inp["shots"]]
+    nints = [sh["width"] * w.nz for sh in inp["shots"]]
+    upd = sum(npads) * (3 * w.nt - 1) * args.steps * world
+    value = upd / el / 1e9
+    e2e = None
+    if not args.no_e2e:
+        host = [d.cpu().pin_memory() for d in seis]
+        stage = [torch.empty_like(d) for d in seis]
+        img_host = torch.empty(image.shape, dtype=torch.float32).pin_memory()
+        shots_s = [dict(sh, seis=st) for sh, st in zip(shots, stage)]
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            for st, hs in zip(stage, host):
+                st.copy_(hs, non_blocking=True)
+            R.rbc_batch_rtm(b, shots_s, wav, R.RBC_REINJECT_SOURCE, EPS_REL, image)
+            img_host.copy_(image, non_blocking=True)
+        barrier()
+        el_e = time.perf_counter() - t0
+        e2e = {"value": upd / world / el_e / 1e9 * world, "unit": "Gpts/s",
+               "h2d_bytes_per_step": int(sum(d.numel() for d in seis)) * 4,
+               "d2h_bytes_per_step": int(image.numel()) * 4}
+    R.rbc_batch_destroy(b)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    rev_bytes = sum(28 * p + 16 * q for p, q in zip(npads, nints))
+    rev_s = phases["rev_ms"] / 1e3 / max(phases["rev_launches"], 1)
+    fwd_s = phases["fwd_ms"] / 1e3 / max(phases["fwd_launches"], 1)
+    achieved = rev_bytes / rev_s / 1e9
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "shots": len(shots), "widths": [min(s["width"] for s in inp["shots"]),
+                                                                         max(s["width"] for s in inp["shots"])],
+                      "nt": w.nt, "autotuned": info, "s_per_shot": el / args.steps / len(shots),
+                      "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+           "roofline": {"bound": "hbm", "kernel": "k_rev2d_batch (fused reverse pass, all shots)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
+                        "traffic": None, "bytes_per_launch": rev_bytes, "launch_us": rev_s * 1e6,
+                        "forward_kernel": {"kernel": "k_fwd2d_batch", "launch_us": fwd_s * 1e6,
+                                           "achieved": 16 * sum(npads) / fwd_s / 1e9}},
+           "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -256,6 +378,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch2d":
+        run_batch(args, rank, world)
         return
     import torch
     import paper_2204_03380_gb300 as R

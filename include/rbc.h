@@ -185,6 +185,59 @@ int rbc_fwi_backward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev
                      int nrec, const int *rec_host, const float *resid_dev,
                      const float *panels_dev, float *grad_dev, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched RTM of many 2-D shots of uneven aperture (Algorithm 3's shot loop
+ * folded into one launch per time step).
+ * ------------------------------------------------------------------------ */
+typedef struct rbc_batch rbc_batch;
+
+typedef struct {
+  int src[3];            /* source node in the shot's own padded grid (y = 0)  */
+  int nrec;              /* receivers of the shot (>= 0)                       */
+  const int *rec_host;   /* nrec x (x, 0, z) nodes in the shot's padded grid   */
+  const float *seis_dev; /* (nrec, nt + 1) fp32 record                         */
+  int off_x;             /* survey image column of the shot's interior x = 0   */
+} rbc_shot;
+
+/*
+ * rbc_batch_create -- contexts for nshots 2-D shots that share nz, nb, h, dt
+ * and nt (taken from g; g->nx is ignored) and have interior widths
+ * nx_host[s].  a_dev[s]: the shot's padded (v dt/h)^2, dense (nz + 2nb,
+ * nx_host[s] + 2nb) fp32, read during the call.  Checks every shot's
+ * stability, lays all fields out in one allocation, and times the candidate
+ * tile shapes (rows per warp of the forward and reverse kernels) on the batch
+ * to keep the fastest.  Synchronous.
+ * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D), RBC_ECFL, RBC_ENOMEM, RBC_ECUDA.
+ */
+int rbc_batch_create(const rbc_grid *g, int nshots, const int *nx_host,
+                     const float *const *a_dev, rbc_batch **out);
+
+/* rbc_batch_destroy -- free a batch (synchronises first); NULL is ignored. */
+int rbc_batch_destroy(rbc_batch *b);
+
+/*
+ * rbc_batch_rtm -- Algorithm 3 for every shot of the batch: each time step
+ * of the forward phase and of the fused reverse phase is one launch over a
+ * work list of (shot, tile) items; then, per shot, I = num / (den + eps_rel
+ * max den) (Eq. 3) is stacked into image_dev (nz, survey_nx) at column off_x
+ * (+=, shots may overlap).  shots: nshots descriptors (host); flags must be
+ * RBC_REINJECT_SOURCE.  Both time loops run as CUDA graphs captured on the
+ * first call and replayed afterwards.
+ * Errors: RBC_EINVAL (window, nodes, flags), RBC_ENOMEM, RBC_ECUDA.
+ */
+int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
+                  int flags, float eps_rel, float *image_dev, int survey_nx,
+                  void *stream);
+
+/* rbc_batch_timing -- as rbc_phase_timing, for the forward and reverse
+ * phases of every rbc_batch_rtm call while enabled (out[0..4]: forward ms,
+ * reverse ms, forward launches, reverse launches, calls). */
+int rbc_batch_timing(rbc_batch *b, int enable, double *out);
+
+/* rbc_batch_info -- out[0..5]: forward and reverse rows per warp chosen by the
+ * autotuner, work items of both kernels, and their persistent grid sizes. */
+int rbc_batch_info(const rbc_batch *b, int *out);
+
 /*
  * rbc_set_snapshots -- ask the next rbc_model / rbc_rtm_shot on this context
  * to copy wavefields at chosen time levels (Figure 1's propagation and

@@ -45,6 +45,11 @@ class rbc_grid(C.Structure):
         return (self.nz, self.nx) if self.ndim == 2 else (self.nz, self.ny, self.nx)
 
 
+class rbc_shot(C.Structure):
+    _fields_ = [("src", C.c_int * 3), ("nrec", C.c_int), ("rec_host", C.c_void_p), ("seis_dev", C.c_void_p),
+                ("off_x", C.c_int)]
+
+
 def make_grid(ndim, nx, ny, nz, nb, h, dt, nt, free_surface=0) -> rbc_grid:
     return rbc_grid(int(ndim), int(nx), int(ny if ndim == 3 else 1), int(nz), int(nb),
                     int(free_surface), float(h), float(dt), int(nt))
@@ -70,6 +75,13 @@ def _load():
     lib.rbc_fwi_backward.argtypes = [P, P, P, I, P, P, P, P, P]
     lib.rbc_fwi_forward.restype = I
     lib.rbc_fwi_backward.restype = I
+    lib.rbc_batch_create.argtypes = [G, I, P, P, C.POINTER(C.c_void_p)]
+    lib.rbc_batch_destroy.argtypes = [P]
+    lib.rbc_batch_rtm.argtypes = [P, P, P, I, F, P, I, P]
+    lib.rbc_batch_info.argtypes = [P, P]
+    lib.rbc_batch_timing.argtypes = [P, I, P]
+    for name in ("rbc_batch_create", "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing"):
+        getattr(lib, name).restype = I
     lib.rbc_model_static.argtypes = [G, P, P, P, I, P, P, P]
     lib.rbc_model_static.restype = I
     lib.rbc_last_error.restype = C.c_char_p
@@ -84,7 +96,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc_rtm_shot",
             "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing",
-            "rbc_model_static", "rbc_fwi_forward", "rbc_fwi_backward", "rbc_last_error",
+            "rbc_model_static", "rbc_fwi_forward", "rbc_fwi_backward", "rbc_batch_create",
+            "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing", "rbc_last_error",
             "rbc_launch_count")
 
 
@@ -212,6 +225,60 @@ def rbc_fwi_backward(ctx, src, wavelet, rec, resid, panels, grad, stream=None):
     _check(_lib.rbc_fwi_backward(C.c_void_p(ctx), s.ctypes.data_as(C.c_void_p), _dev(wavelet, None, "wavelet"),
                                  r.shape[0], r.ctypes.data_as(C.c_void_p), _dev(resid, None, "resid"),
                                  _dev(panels, None, "panels"), _dev(grad, None, "grad"), _stream(stream)))
+
+
+def rbc_batch_create(grid, nx_list, a_list):
+    """Batch of 2-D shots sharing grid's nz/nb/h/dt/nt with widths nx_list and
+    padded coefficients a_list (one CUDA tensor per shot).  Returns a handle."""
+    n = len(nx_list)
+    nx = (C.c_int * n)(*[int(x) for x in nx_list])
+    ptrs = (C.c_void_p * n)()
+    for k, (x, a) in enumerate(zip(nx_list, a_list)):
+        ptrs[k] = _dev(a, (grid.nz + 2 * grid.nb, int(x) + 2 * grid.nb), "a")
+    out = C.c_void_p()
+    torch.cuda.synchronize()
+    _check(_lib.rbc_batch_create(C.byref(grid), n, nx, ptrs, C.byref(out)))
+    return out.value
+
+
+def rbc_batch_destroy(batch):
+    _check(_lib.rbc_batch_destroy(C.c_void_p(batch)))
+
+
+def rbc_batch_rtm(batch, shots, wavelet, flags, eps_rel, image, stream=None):
+    """shots: list of dict(src=(x, 0, z), rec=(nrec, 3) int array, seis=(nrec, nt+1)
+    CUDA tensor, off_x=int).  image: survey interior (nz, survey_nx), += stacked."""
+    n = len(shots)
+    arr = (rbc_shot * n)()
+    keep = []
+    for k, sh in enumerate(shots):
+        r = _nodes(sh["rec"])
+        keep.append(r)
+        arr[k].src[:] = [int(x) for x in np.asarray(sh["src"]).ravel()[:3]]
+        arr[k].nrec = r.shape[0]
+        arr[k].rec_host = r.ctypes.data if r.size else None
+        arr[k].seis_dev = _dev(sh["seis"], None, "seis").value if r.shape[0] else None
+        arr[k].off_x = int(sh["off_x"])
+    _check(_lib.rbc_batch_rtm(C.c_void_p(batch), arr, _dev(wavelet, None, "wavelet"), int(flags),
+                              float(eps_rel), _dev(image, None, "image"), int(image.shape[-1]),
+                              _stream(stream)))
+
+
+def rbc_batch_timing(batch, enable):
+    """Phase timing of rbc_batch_rtm calls (see rbc_phase_timing)."""
+    out = (C.c_double * 5)()
+    _check(_lib.rbc_batch_timing(C.c_void_p(batch), 1 if enable else 0, out))
+    if enable:
+        return None
+    return dict(fwd_ms=out[0], rev_ms=out[1], fwd_launches=int(out[2]), rev_launches=int(out[3]),
+                calls=int(out[4]))
+
+
+def rbc_batch_info(batch):
+    out = (C.c_int * 6)()
+    _check(_lib.rbc_batch_info(C.c_void_p(batch), out))
+    return dict(rows_fwd=out[0], rows_rev=out[1], items_fwd=out[2], items_rev=out[3], grid_fwd=out[4],
+                grid_rev=out[5])
 
 
 def rbc_last_error() -> str:

@@ -88,6 +88,8 @@ int set_error(int code, const char *msg) {
   g_err = msg;
   return code;
 }
+// Count kernel launches queued by another translation unit.
+void add_launches(long long n) { g_launches += n; }
 } // namespace rbc
 
 struct rbc_ctx {

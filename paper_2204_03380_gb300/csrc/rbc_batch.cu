@@ -1,0 +1,639 @@
+// rbc_batch.cu -- RTM of many 2-D shots with uneven apertures in one launch
+// per time step (Algorithm 3's shot loop folded into the grid).
+//
+// Every shot keeps its own padded grid (its aperture window plus the random
+// boundary) in the pitched, zero-haloed layout; all grids share nz, nb, h,
+// dt and nt.  One kernel launch per time step walks a global work list of
+// (shot, tile) items with persistent blocks, so shots of any width share the
+// machine without a tail per shot; the shot descriptors live in device memory
+// and each time loop is one CUDA graph replayed for every batch.  Rows per
+// warp of the forward and reverse kernels are chosen at creation by timing
+// the candidates on the batch itself.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/rbc.h"
+#include "rbc_tile2d.cuh"
+
+using namespace rbc;
+
+namespace rbc {
+int set_error(int code, const char *msg);  // rbc_abi.cu
+void add_launches(long long n);            // rbc_abi.cu
+}
+
+namespace {
+
+struct BShot {
+  Lay L;
+  float *a, *p0, *p1, *q0, *q1, *num, *den;
+  int src_off;
+  int nrec;
+  const int *rec_off;   // receiver offsets in this shot's layout
+  const int *tile_ptr;  // receivers of each reverse tile (CSR, local tiles)
+  const int *tile_rec;
+  const float *seis_t;  // [nt+1][nrec]
+  int gx, gzf, gzr;     // x tiles, z tiles of the forward / reverse kernels
+  int tbase_f, tbase_r; // first global work item of this shot
+  int ix0, ix1, iz0, iz1;
+  int off_x;            // survey column of this shot's interior x = 0
+  unsigned int maxbits; // max(den) of the shot (image ratio)
+};
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- kernels --
+template <int RZ>
+__global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d_batch(const BShot *__restrict__ shots,
+                                                                const int *__restrict__ item_shot, int nitems,
+                                                                int n, const float *__restrict__ wav,
+                                                                float src_scale) {
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const float f = wav[n] * src_scale;
+  for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+    const BShot &S = shots[item_shot[t]];
+    const int loc = t - S.tbase_f;
+    const int bx = loc % S.gx, bz = loc / S.gx;
+    const int zb = (bz * k2dWarps + w) * RZ;
+    if (zb >= S.L.NZ) continue;  // warp-uniform
+    const float *cur = (n & 1) ? S.p1 : S.p0;
+    float *nxt = (n & 1) ? S.p0 : S.p1;
+    fwd2d_rows<RZ>(S.L, S.a, cur, nxt, lane, bx * kTileX + lane * 4, zb, S.src_off, f);
+  }
+}
+
+template <int RZ>
+__global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__restrict__ shots,
+                                                                const int *__restrict__ item_shot, int nitems,
+                                                                int n, int nt, const float *__restrict__ wav,
+                                                                float src_scale, float rec_scale) {
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const bool do_r = n < nt && n > 0, do_b = n > 0;
+  const float fsrc = do_r ? wav[n] * src_scale : 0.f;  // f[nt] does not exist
+  for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+    const BShot &S = shots[item_shot[t]];
+    const Lay &L = S.L;
+    const int loc = t - S.tbase_r;
+    const int bx = loc % S.gx, bz = loc / S.gx;
+    const int x0 = bx * kTileX + lane * 4;
+    const int zb = (bz * k2dWarps + w) * RZ;
+    const bool xok = x0 < L.NX4;
+    // p^R_n in p[n & 1], pbar_n in q[n & 1]
+    const float *rc = (n & 1) ? S.p1 : S.p0;
+    float *rn = (n & 1) ? S.p0 : S.p1;
+    const float *bc = (n & 1) ? S.q1 : S.q0;
+    float *bn = (n & 1) ? S.q0 : S.q1;
+    if (zb < L.NZ) {  // warp-uniform
+      float4 cr[RZ], cb[RZ], inc[RZ];
+      rev_field2d<RZ, false>(L, S.a, rc, rn, do_r, lane, x0, zb, xok, S.src_off, fsrc, cr, inc);
+      rev_field2d<RZ, false>(L, S.a, bc, bn, do_b, lane, x0, zb, xok, -1, 0.f, cb, inc);
+      if (xok && x0 + 3 >= S.ix0 && x0 < S.ix1) {
+#pragma unroll
+        for (int j = 0; j < RZ; ++j) {
+          const int z = zb + j;
+          if (z >= S.iz0 && z < S.iz1) {
+            const int o = L.origin + x0 + z * L.pitch;
+            st4(S.num + o, add4(ld4(S.num + o), masked_prod(cr[j], cb[j], x0, S.ix0, S.ix1)));
+            st4(S.den + o, add4(ld4(S.den + o), masked_prod(cr[j], cr[j], x0, S.ix0, S.ix1)));
+          }
+        }
+      }
+    }
+    // Eq. 2 source term at this tile's receivers, after the block's stores
+    if (do_b) {
+      const int beg = S.tile_ptr[loc], end = S.tile_ptr[loc + 1];
+      if (end > beg) {
+        __threadfence();
+        __syncthreads();
+        for (int k = beg + w * 32 + lane; k < end; k += 32 * k2dWarps) {
+          const int r = S.tile_rec[k];
+          const int o = S.rec_off[r];
+          atomicAdd(bn + o, rec_scale * S.a[o] * S.seis_t[(long long)n * S.nrec + r]);
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// Per-shot max(den) on the interior (blockIdx.y = shot).
+__global__ void k_batch_max(BShot *shots, const int *ncols, int nz) {
+  BShot &S = shots[blockIdx.y];
+  const int nx = ncols[blockIdx.y];
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)nx * nz;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), z = (int)(i / nx);
+    m = fmaxf(m, S.den[lay_off(S.L, x + S.ix0, 0, z + S.iz0)]);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&S.maxbits, __float_as_uint(m));
+}
+
+// Eq. 3 ratio of every shot, stacked at its aperture offset (blockIdx.y = shot).
+__global__ void k_batch_image(const BShot *shots, const int *ncols, int nz, float eps_rel, float *image, int sx) {
+  const BShot &S = shots[blockIdx.y];
+  const int nx = ncols[blockIdx.y];
+  const float e = eps_rel * __uint_as_float(S.maxbits);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)nx * nz;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), z = (int)(i / nx);
+    const int o = lay_off(S.L, x + S.ix0, 0, z + S.iz0);
+    atomicAdd(image + (long long)z * sx + x + S.off_x, S.num[o] / (S.den[o] + e));
+  }
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ host --
+struct rbc_batch {
+  rbc_grid g;  // shared nz, nb, h, dt, nt (nx per shot)
+  int nshots = 0;
+  std::vector<int> nx;
+  std::vector<Lay> L;
+  std::vector<BShot> hs;
+  float *arena = nullptr;
+  BShot *ds = nullptr;
+  int *d_ncols = nullptr;
+  int *d_item_f = nullptr, *d_item_r = nullptr;
+  int nitems_f = 0, nitems_r = 0;
+  int rzf = 4, rzr = 2;
+  int grid_f = 0, grid_r = 0;
+  int rec_cap = 0, tile_cap = 0;
+  int *d_rec_off = nullptr, *d_tile_ptr = nullptr, *d_tile_rec = nullptr;
+  float *d_seis_t = nullptr;
+  float *d_wav = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  long long gnodes[2] = {0, 0};
+  bool use_graph = true;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // three per timed call
+};
+
+namespace {
+
+int bfail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return rbc::set_error(code, buf);
+}
+
+#define BCK(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bfail(e_ == cudaErrorMemoryAllocation ? RBC_ENOMEM : RBC_ECUDA, "%s: %s", #call, \
+                   cudaGetErrorString(e_));                                                \
+  } while (0)
+
+void drop_graphs(rbc_batch *b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
+    b->gexec[k] = nullptr;
+  }
+}
+
+// Work lists for the chosen rows per warp: item -> shot, per-shot tile bases.
+int build_items(rbc_batch *b) {
+  std::vector<int> itf, itr;
+  for (int s = 0; s < b->nshots; ++s) {
+    BShot &S = b->hs[s];
+    S.gx = cdiv(S.L.NX, kTileX);
+    S.gzf = cdiv(S.L.NZ, k2dWarps * b->rzf);
+    S.gzr = cdiv(S.L.NZ, k2dWarps * b->rzr);
+    S.tbase_f = (int)itf.size();
+    S.tbase_r = (int)itr.size();
+    itf.insert(itf.end(), (size_t)S.gx * S.gzf, s);
+    itr.insert(itr.end(), (size_t)S.gx * S.gzr, s);
+  }
+  cudaFree(b->d_item_f);
+  cudaFree(b->d_item_r);
+  b->d_item_f = b->d_item_r = nullptr;
+  b->nitems_f = (int)itf.size();
+  b->nitems_r = (int)itr.size();
+  BCK(cudaMalloc(&b->d_item_f, sizeof(int) * itf.size()));
+  BCK(cudaMalloc(&b->d_item_r, sizeof(int) * itr.size()));
+  BCK(cudaMemcpy(b->d_item_f, itf.data(), sizeof(int) * itf.size(), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->d_item_r, itr.data(), sizeof(int) * itr.size(), cudaMemcpyHostToDevice));
+  return RBC_OK;
+}
+
+template <typename K>
+int resident_grid(K kern, int items) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * k2dWarps, 0);
+  const int slots = std::max(1, sms) * std::max(1, per);
+  return std::max(1, std::min(items, slots));
+}
+
+bool launch_fwd_b(rbc_batch *b, int n, cudaStream_t s) {
+  const dim3 blk(32, k2dWarps);
+  const float sc = 1.0f;  // h^(2-d) in 2-D
+  switch (b->rzf) {
+  case 1: k_fwd2d_batch<1><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
+  case 2: k_fwd2d_batch<2><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
+  default: k_fwd2d_batch<4><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
+  }
+  return cudaPeekAtLastError() == cudaSuccess;
+}
+
+bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s) {
+  const dim3 blk(32, k2dWarps);
+  const int nt = b->g.nt;
+  switch (b->rzr) {
+  case 1:
+    k_rev2d_batch<1><<<b->grid_r, blk, 0, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f);
+    break;
+  default:
+    k_rev2d_batch<2><<<b->grid_r, blk, 0, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f);
+    break;
+  }
+  return cudaPeekAtLastError() == cudaSuccess;
+}
+
+void set_grids(rbc_batch *b) {
+  switch (b->rzf) {
+  case 1: b->grid_f = resident_grid(k_fwd2d_batch<1>, b->nitems_f); break;
+  case 2: b->grid_f = resident_grid(k_fwd2d_batch<2>, b->nitems_f); break;
+  default: b->grid_f = resident_grid(k_fwd2d_batch<4>, b->nitems_f); break;
+  }
+  b->grid_r = (b->rzr == 1) ? resident_grid(k_rev2d_batch<1>, b->nitems_r) : resident_grid(k_rev2d_batch<2>, b->nitems_r);
+}
+
+// Autotuner: time every rows-per-warp candidate of both kernels on the batch
+// itself (zero fields, no receivers) and keep the fastest.
+int autotune(rbc_batch *b) {
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  auto time_it = [&](bool fwd) -> float {
+    set_grids(b);
+    for (int k = 0; k < 3; ++k) fwd ? launch_fwd_b(b, 10, 0) : launch_rev_b(b, 10, 0);
+    cudaEventRecord(e0, 0);
+    for (int k = 0; k < 20; ++k) fwd ? launch_fwd_b(b, 10 + (k & 1), 0) : launch_rev_b(b, 10 + (k & 1), 0);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  int best_f = 4, best_r = 2;
+  float tf = 1e30f, tr = 1e30f;
+  for (int rz : {1, 2, 4}) {
+    b->rzf = rz;
+    int rc = build_items(b);
+    if (rc) return rc;
+    BCK(cudaMemcpy(b->ds, b->hs.data(), sizeof(BShot) * b->nshots, cudaMemcpyHostToDevice));
+    const float t = time_it(true);
+    if (t < tf) tf = t, best_f = rz;
+  }
+  b->rzf = best_f;
+  for (int rz : {1, 2}) {
+    b->rzr = rz;
+    int rc = build_items(b);
+    if (rc) return rc;
+    BCK(cudaMemcpy(b->ds, b->hs.data(), sizeof(BShot) * b->nshots, cudaMemcpyHostToDevice));
+    const float t = time_it(false);
+    if (t < tr) tr = t, best_r = rz;
+  }
+  b->rzr = best_r;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc = build_items(b);
+  if (rc) return rc;
+  set_grids(b);
+  BCK(cudaMemcpy(b->ds, b->hs.data(), sizeof(BShot) * b->nshots, cudaMemcpyHostToDevice));
+  BCK(cudaGetLastError());
+  return RBC_OK;
+}
+
+int enq_fwd(rbc_batch *b, cudaStream_t s) {
+  for (int i = 0; i < b->nshots; ++i) {
+    const size_t bytes = sizeof(float) * (size_t)b->L[i].total;
+    BCK(cudaMemsetAsync(b->hs[i].p0, 0, bytes, s));
+    BCK(cudaMemsetAsync(b->hs[i].p1, 0, bytes, s));
+  }
+  for (int n = 0; n < b->g.nt; ++n)
+    if (!launch_fwd_b(b, n, s)) return bfail(RBC_ECUDA, "batched forward launch failed");
+  return RBC_OK;
+}
+
+int enq_rev(rbc_batch *b, cudaStream_t s) {
+  for (int i = 0; i < b->nshots; ++i) {
+    const size_t bytes = sizeof(float) * (size_t)b->L[i].total;
+    BCK(cudaMemsetAsync(b->hs[i].q0, 0, bytes, s));
+    BCK(cudaMemsetAsync(b->hs[i].q1, 0, bytes, s));
+    BCK(cudaMemsetAsync(b->hs[i].num, 0, bytes, s));
+    BCK(cudaMemsetAsync(b->hs[i].den, 0, bytes, s));
+  }
+  for (int n = b->g.nt; n >= 0; --n)
+    if (!launch_rev_b(b, n, s)) return bfail(RBC_ECUDA, "batched reverse launch failed");
+  return RBC_OK;
+}
+
+int run_b(rbc_batch *b, int kind, cudaStream_t s, long long *launches) {
+  const long long per = kind == 0 ? b->g.nt : b->g.nt + 1;
+  if (!b->use_graph) {
+    *launches += per;
+    return kind == 0 ? enq_fwd(b, s) : enq_rev(b, s);
+  }
+  if (!b->gexec[kind]) {
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = kind == 0 ? enq_fwd(b, b->cap) : enq_rev(b, b->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return bfail(RBC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec[kind], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->gexec[kind] = nullptr;
+      return bfail(RBC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  BCK(cudaGraphLaunch(b->gexec[kind], s));
+  *launches += per;
+  return RBC_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int rbc_batch_create(const rbc_grid *g, int nshots, const int *nx_host, const float *const *a_dev,
+                     rbc_batch **out) {
+  if (!g || !nx_host || !a_dev || !out || nshots < 1) return bfail(RBC_EINVAL, "rbc_batch_create: bad arguments");
+  if (g->ndim != 2) return bfail(RBC_ENOTSUP, "rbc_batch_create: batches are 2-D");
+  if (g->nz < 1 || g->nb < 2 || g->nt < 1 || !(g->h > 0) || !(g->dt > 0) || g->free_surface)
+    return bfail(RBC_EINVAL, "rbc_batch_create: bad grid");
+  *out = nullptr;
+  rbc_batch *b = new rbc_batch();
+  b->g = *g;
+  b->nshots = nshots;
+  const char *env = getenv("RBC_GRAPH");
+  b->use_graph = !(env && env[0] == '0');
+  size_t total = 0;
+  for (int s = 0; s < nshots; ++s) {
+    if (nx_host[s] < 1 || !a_dev[s]) {
+      delete b;
+      return bfail(RBC_EINVAL, "rbc_batch_create: shot %d has no width or no coefficient", s);
+    }
+    b->nx.push_back(nx_host[s]);
+    Lay L;
+    L.ndim = 2;
+    L.NX = nx_host[s] + 2 * g->nb;
+    L.NY = 1;
+    L.NZ = g->nz + 2 * g->nb;
+    L.NX4 = (L.NX + 3) / 4 * 4;
+    L.pitch = cdiv(L.NX, kTileX) * kTileX + 2 * kHaloX;
+    L.rows = 1;
+    L.plane = L.pitch;
+    L.origin = kHaloR * L.plane + kHaloX;
+    L.total = (long long)(L.NZ + 2 * kHaloR) * L.plane;
+    b->L.push_back(L);
+    total += 7 * (size_t)L.total;
+  }
+  // stability of every shot, as rbc_create checks it
+  unsigned int *dmax = nullptr;
+  if (cudaMalloc(&dmax, sizeof(unsigned int) * nshots) != cudaSuccess) {
+    delete b;
+    return bfail(RBC_ENOMEM, "rbc_batch_create: allocation failed");
+  }
+  cudaMemset(dmax, 0, sizeof(unsigned int) * nshots);
+  for (int s = 0; s < nshots; ++s) launch_max(a_dev[s], (long long)b->L[s].NX * b->L[s].NZ, dmax + s, 0);
+  std::vector<unsigned int> bits(nshots);
+  cudaMemcpy(bits.data(), dmax, sizeof(unsigned int) * nshots, cudaMemcpyDeviceToHost);
+  cudaFree(dmax);
+  for (int s = 0; s < nshots; ++s) {
+    float am;
+    memcpy(&am, &bits[s], sizeof am);
+    if (!(am * 2 * kSymbolMax < 4.0)) {
+      delete b;
+      return bfail(RBC_ECFL, "rbc_batch_create: shot %d is unstable (max (v dt/h)^2 = %g)", s, am);
+    }
+  }
+  if (cudaMalloc(&b->arena, sizeof(float) * total) != cudaSuccess || cudaMemset(b->arena, 0, sizeof(float) * total) ||
+      cudaMalloc(&b->ds, sizeof(BShot) * nshots) != cudaSuccess ||
+      cudaMalloc(&b->d_ncols, sizeof(int) * nshots) != cudaSuccess ||
+      cudaMalloc(&b->d_wav, sizeof(float) * g->nt) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    rbc_batch_destroy(b);
+    return bfail(RBC_ENOMEM, "rbc_batch_create: allocation of %zu bytes failed", sizeof(float) * total);
+  }
+  cudaMemcpy(b->d_ncols, nx_host, sizeof(int) * nshots, cudaMemcpyHostToDevice);
+  float *p = b->arena;
+  b->hs.resize(nshots);
+  for (int s = 0; s < nshots; ++s) {
+    BShot &S = b->hs[s];
+    memset(&S, 0, sizeof S);
+    S.L = b->L[s];
+    const long long T = S.L.total;
+    S.a = p; S.p0 = p + T; S.p1 = p + 2 * T; S.q0 = p + 3 * T; S.q1 = p + 4 * T; S.num = p + 5 * T; S.den = p + 6 * T;
+    p += 7 * T;
+    S.ix0 = g->nb; S.ix1 = g->nb + b->nx[s]; S.iz0 = g->nb; S.iz1 = g->nb + g->nz;
+    launch_copy_in(S.L, a_dev[s], S.a, 0);
+  }
+  // tuning-time receiver tables: every tile of every shot with no receiver
+  int rc = RBC_OK;
+  {
+    size_t maxt = 0;
+    for (int s = 0; s < nshots; ++s) maxt = std::max(maxt, (size_t)cdiv(b->L[s].NX, kTileX) * cdiv(b->L[s].NZ, k2dWarps) + 1);
+    if (cudaMalloc(&b->d_tile_ptr, sizeof(int) * maxt) != cudaSuccess) {
+      rbc_batch_destroy(b);
+      return bfail(RBC_ENOMEM, "rbc_batch_create: allocation failed");
+    }
+    cudaMemset(b->d_tile_ptr, 0, sizeof(int) * maxt);
+    b->tile_cap = (int)maxt;
+    for (int s = 0; s < nshots; ++s) b->hs[s].tile_ptr = b->d_tile_ptr;
+  }
+  cudaMemset(b->d_wav, 0, sizeof(float) * g->nt);
+  rc = autotune(b);
+  if (rc) {
+    rbc_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return RBC_OK;
+}
+
+int rbc_batch_destroy(rbc_batch *b) {
+  if (!b) return RBC_OK;
+  cudaDeviceSynchronize();
+  drop_graphs(b);
+  cudaFree(b->arena);
+  cudaFree(b->ds);
+  cudaFree(b->d_ncols);
+  cudaFree(b->d_item_f);
+  cudaFree(b->d_item_r);
+  cudaFree(b->d_rec_off);
+  cudaFree(b->d_tile_ptr);
+  cudaFree(b->d_tile_rec);
+  cudaFree(b->d_seis_t);
+  cudaFree(b->d_wav);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  delete b;
+  return RBC_OK;
+}
+
+int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev, int flags, float eps_rel,
+                  float *image_dev, int survey_nx, void *stream) {
+  if (!b || !shots || !wavelet_dev || !image_dev) return bfail(RBC_EINVAL, "rbc_batch_rtm: NULL argument");
+  if (flags != RBC_REINJECT_SOURCE) return bfail(RBC_EINVAL, "rbc_batch_rtm: flags must be RBC_REINJECT_SOURCE");
+  if (!(eps_rel >= 0)) return bfail(RBC_EINVAL, "rbc_batch_rtm: eps_rel must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nt = b->g.nt;
+  // receiver tables of every shot (counting sort by reverse tile)
+  std::vector<int> off, ptr, order;
+  std::vector<int> rec_base(b->nshots), ptr_base(b->nshots);
+  long long seis_total = 0;
+  std::vector<long long> seis_base(b->nshots);
+  for (int i = 0; i < b->nshots; ++i) {
+    const rbc_shot &sh = shots[i];
+    const Lay &L = b->L[i];
+    if (sh.off_x < 0 || sh.off_x + b->nx[i] > survey_nx)
+      return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d window does not fit the survey", i);
+    if (sh.nrec < 0 || (sh.nrec > 0 && (!sh.rec_host || !sh.seis_dev)))
+      return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d has a bad receiver list", i);
+    auto inside = [&](const int *r) { return r[0] >= 0 && r[0] < L.NX && r[1] == 0 && r[2] >= 0 && r[2] < L.NZ; };
+    if (!inside(sh.src)) return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d source outside its grid", i);
+    const int gx = cdiv(L.NX, kTileX), gz = cdiv(L.NZ, k2dWarps * b->rzr);
+    rec_base[i] = (int)off.size();
+    ptr_base[i] = (int)ptr.size();
+    std::vector<int> cnt(gx * gz + 1, 0), tile(sh.nrec);
+    for (int r = 0; r < sh.nrec; ++r) {
+      const int *q = sh.rec_host + 3 * r;
+      if (!inside(q)) return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d receiver %d outside its grid", i, r);
+      off.push_back(lay_off(L, q[0], 0, q[2]));
+      tile[r] = (q[2] / (k2dWarps * b->rzr)) * gx + q[0] / kTileX;
+      cnt[tile[r] + 1]++;
+    }
+    for (int t = 0; t < gx * gz; ++t) cnt[t + 1] += cnt[t];
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1), ord(std::max(sh.nrec, 0));
+    for (int r = 0; r < sh.nrec; ++r) ord[fill[tile[r]]++] = r;
+    const int obase = (int)order.size();
+    for (int t = 0; t <= gx * gz; ++t) ptr.push_back(obase + cnt[t]);
+    order.insert(order.end(), ord.begin(), ord.end());
+    seis_base[i] = seis_total;
+    seis_total += (long long)(nt + 1) * sh.nrec;
+  }
+  // grow the capacity buffers (invalidates the graphs)
+  const int nr = std::max(1, (int)off.size()), np = std::max(1, (int)ptr.size());
+  if (nr > b->rec_cap || np > b->tile_cap || !b->d_seis_t || !b->d_rec_off) {
+    drop_graphs(b);
+    cudaFree(b->d_rec_off);
+    cudaFree(b->d_tile_rec);
+    cudaFree(b->d_tile_ptr);
+    cudaFree(b->d_seis_t);
+    b->d_rec_off = b->d_tile_rec = b->d_tile_ptr = nullptr;
+    b->d_seis_t = nullptr;
+    b->rec_cap = std::max(nr, b->rec_cap);
+    b->tile_cap = std::max(np, b->tile_cap);
+    BCK(cudaMalloc(&b->d_rec_off, sizeof(int) * b->rec_cap));
+    BCK(cudaMalloc(&b->d_tile_rec, sizeof(int) * b->rec_cap));
+    BCK(cudaMalloc(&b->d_tile_ptr, sizeof(int) * b->tile_cap));
+    BCK(cudaMalloc(&b->d_seis_t, sizeof(float) * (size_t)b->rec_cap * (nt + 1)));
+  }
+  for (int i = 0; i < b->nshots; ++i) {
+    BShot &S = b->hs[i];
+    S.src_off = lay_off(b->L[i], shots[i].src[0], 0, shots[i].src[2]);
+    S.nrec = shots[i].nrec;
+    S.rec_off = b->d_rec_off + rec_base[i];
+    S.tile_rec = b->d_tile_rec;  // the CSR holds positions in the whole list
+    S.tile_ptr = b->d_tile_ptr + ptr_base[i];
+    S.seis_t = b->d_seis_t + seis_base[i];
+    S.off_x = shots[i].off_x;
+    S.maxbits = 0;
+  }
+  // the CSR holds global positions into d_tile_rec, and d_tile_rec holds
+  // shot-local receiver indices
+  BCK(cudaMemcpyAsync(b->ds, b->hs.data(), sizeof(BShot) * b->nshots, cudaMemcpyHostToDevice, s));
+  if (!off.empty()) {
+    BCK(cudaMemcpyAsync(b->d_rec_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(b->d_tile_rec, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s));
+  }
+  BCK(cudaMemcpyAsync(b->d_tile_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_wav, wavelet_dev, sizeof(float) * nt, cudaMemcpyDeviceToDevice, s));
+  long long launches = 0;
+  for (int i = 0; i < b->nshots; ++i)
+    if (shots[i].nrec > 0) {
+      launch_transpose(shots[i].seis_dev, b->d_seis_t + seis_base[i], shots[i].nrec, nt + 1, s);
+      ++launches;
+    }
+  cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
+  if (b->timing)
+    for (int k = 0; k < 3; ++k) {
+      BCK(cudaEventCreate(&e3[k]));
+      b->ev.push_back(e3[k]);
+    }
+  if (b->timing) BCK(cudaEventRecord(e3[0], s));
+  int rc = run_b(b, 0, s, &launches);
+  if (rc) return rc;
+  if (b->timing) BCK(cudaEventRecord(e3[1], s));
+  rc = run_b(b, 1, s, &launches);
+  if (rc) return rc;
+  if (b->timing) BCK(cudaEventRecord(e3[2], s));
+  int maxnx = 0;
+  for (int x : b->nx) maxnx = std::max(maxnx, x);
+  const long long per = (long long)maxnx * b->g.nz;
+  const int gxb = (int)std::min<long long>(1024, std::max<long long>(1, (per + 255) / 256));
+  k_batch_max<<<dim3(gxb, b->nshots), 256, 0, s>>>(b->ds, b->d_ncols, b->g.nz);
+  k_batch_image<<<dim3(gxb, b->nshots), 256, 0, s>>>(b->ds, b->d_ncols, b->g.nz, eps_rel, image_dev, survey_nx);
+  launches += 2;
+  rbc::add_launches(launches);
+  BCK(cudaGetLastError());
+  return RBC_OK;
+}
+
+int rbc_batch_timing(rbc_batch *b, int enable, double *out) {
+  if (!b) return bfail(RBC_EINVAL, "rbc_batch_timing: NULL batch");
+  double f = 0, r = 0;
+  const size_t calls = b->ev.size() / 3;
+  if (!enable || b->timing) {
+    for (size_t k = 0; k < calls; ++k) {
+      float t1 = 0, t2 = 0;
+      BCK(cudaEventSynchronize(b->ev[3 * k + 2]));
+      BCK(cudaEventElapsedTime(&t1, b->ev[3 * k], b->ev[3 * k + 1]));
+      BCK(cudaEventElapsedTime(&t2, b->ev[3 * k + 1], b->ev[3 * k + 2]));
+      f += t1;
+      r += t2;
+    }
+  }
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  b->ev.clear();
+  b->timing = enable != 0;
+  if (!enable && out) {
+    out[0] = f;
+    out[1] = r;
+    out[2] = (double)calls * b->g.nt;
+    out[3] = (double)calls * (b->g.nt + 1);
+    out[4] = (double)calls;
+  }
+  return RBC_OK;
+}
+
+int rbc_batch_info(const rbc_batch *b, int *out) {
+  if (!b || !out) return bfail(RBC_EINVAL, "rbc_batch_info: NULL argument");
+  out[0] = b->rzf;
+  out[1] = b->rzr;
+  out[2] = b->nitems_f;
+  out[3] = b->nitems_r;
+  out[4] = b->grid_f;
+  out[5] = b->grid_r;
+  return RBC_OK;
+}
+
+} // extern "C"

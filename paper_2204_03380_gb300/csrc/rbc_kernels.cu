@@ -15,62 +15,9 @@
 // neighbours come from the adjacent lanes by warp shuffles (lanes 0/31 fetch
 // the 4-float halo) and the z neighbours from a register queue marching down
 // z.  The 3-D kernels (TMA-fed plane rings) are in rbc_kernels3d.cu.
-#include "rbc_internal.cuh"
-#include "rbc_stencil.cuh"
+#include "rbc_tile2d.cuh"
 
 namespace rbc {
-
-__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-__device__ __forceinline__ float cmp(const float4 &v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
-__device__ __forceinline__ float4 shfl_up4(float4 v) {
-  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
-  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
-  v.z = __shfl_up_sync(0xffffffffu, v.z, 1);
-  v.w = __shfl_up_sync(0xffffffffu, v.w, 1);
-  return v;
-}
-__device__ __forceinline__ float4 shfl_dn4(float4 v) {
-  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
-  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
-  v.z = __shfl_down_sync(0xffffffffu, v.z, 1);
-  v.w = __shfl_down_sync(0xffffffffu, v.w, 1);
-  return v;
-}
-
-// Leapfrog update of 4 consecutive nodes from the x window (lf, c, rt) and
-// the z window zq[0..8] (zq[4] == c); see rbc_stencil.cuh.
-__device__ __forceinline__ float4 leap4_2d(const float4 lf, const float4 c, const float4 rt, const float4 *zq,
-                                           const float4 po, const float4 av) {
-  const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w, rt.x, rt.y, rt.z, rt.w};
-  return leap4p<false>(w, zq, nullptr, nullptr, po, av);
-}
-
-// Subtract a point term from component (src - o) of v when the source node
-// falls in the float4 starting at offset o.
-__device__ __forceinline__ void point_sub(float4 &v, int d, float term) {
-  if (d == 0) v.x -= term;
-  else if (d == 1) v.y -= term;
-  else if (d == 2) v.z -= term;
-  else if (d == 3) v.w -= term;
-}
-
-__device__ __forceinline__ float4 masked_prod(const float4 u, const float4 v, int x0, int lo, int hi) {
-  float4 r;
-  r.x = (x0 + 0 >= lo && x0 + 0 < hi) ? u.x * v.x : 0.f;
-  r.y = (x0 + 1 >= lo && x0 + 1 < hi) ? u.y * v.y : 0.f;
-  r.z = (x0 + 2 >= lo && x0 + 2 < hi) ? u.z * v.z : 0.f;
-  r.w = (x0 + 3 >= lo && x0 + 3 < hi) ? u.w * v.w : 0.f;
-  return r;
-}
-
-__device__ __forceinline__ float4 add4(float4 a, float4 b) {
-  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
 
 // Record the current level at every receiver (Algorithm 1 "record
 // seismogram"): grid-strided so any block may sample any receiver.
@@ -109,91 +56,9 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d(const StepArgs A) {
   const int lane = threadIdx.x, w = threadIdx.y;
   const int x0 = blockIdx.x * kTileX + lane * 4;
   const int zb = (blockIdx.y * k2dWarps + w) * RZ;
-  const bool xok = x0 < L.NX4;
-  const int col = L.origin + x0;
   if (A.sample) sample_receivers(A, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
   if (zb >= L.NZ) return;  // warp-uniform; no block barrier in this kernel
-  float4 q[RZ + 8];
-#pragma unroll
-  for (int j = 0; j < RZ + 8; ++j) {
-    const int z = zb - kHaloR + j;
-    q[j] = (xok && z < L.NZ + kHaloR) ? ldg4(A.cur + col + z * L.pitch) : zero4();
-  }
-  const int src = A.info->src_off;
-  const float fsrc = A.wav[A.n] * A.info->src_fwd;
-#pragma unroll
-  for (int j = 0; j < RZ; ++j) {
-    const int z = zb + j;
-    if (z >= L.NZ) break;
-    const int o = col + z * L.pitch;
-    const float4 c = q[j + 4];
-    float4 lf = shfl_up4(c), rt = shfl_dn4(c);
-    if (lane == 0) lf = ldg4(A.cur + o - 4);
-    if (lane == 31) rt = ldg4(A.cur + o + 4);
-    if (xok) {
-      const float4 av = ldg4(A.a + o);
-      const float4 po = ld4(A.nxt + o);
-      float4 r = leap4_2d(lf, c, rt, &q[j], po, av);
-      const int d = src - o;
-      if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
-      st4(A.nxt + o, r);
-    }
-  }
-}
-
-// One field of the reverse pass: advance (cur, nxt) and return the centre
-// values of `cur` for the imaging condition.
-template <int RZ, bool kInc>
-__device__ __forceinline__ void rev_field2d(const Lay &L, const float *__restrict__ a,
-                                            const float *__restrict__ cur, float *__restrict__ nxt,
-                                            bool update, int lane, int x0, int zb, bool xok,
-                                            int src, float fsrc, float4 *cen, float4 *inc) {
-  const int col = L.origin + x0;
-  if (!update) {
-#pragma unroll
-    for (int j = 0; j < RZ; ++j) {
-      const int z = zb + j;
-      cen[j] = (xok && z < L.NZ) ? ldg4(cur + col + z * L.pitch) : zero4();
-    }
-    return;
-  }
-  float4 q[RZ + 8];
-#pragma unroll
-  for (int j = 0; j < RZ + 8; ++j) {
-    const int z = zb - kHaloR + j;
-    q[j] = (xok && z < L.NZ + kHaloR) ? ldg4(cur + col + z * L.pitch) : zero4();
-  }
-#pragma unroll
-  for (int j = 0; j < RZ; ++j) {
-    const int z = zb + j;
-    cen[j] = q[j + 4];
-    if (z >= L.NZ) break;
-    const int o = col + z * L.pitch;
-    const float4 c = q[j + 4];
-    float4 lf = shfl_up4(c), rt = shfl_dn4(c);
-    if (lane == 0) lf = ldg4(cur + o - 4);
-    if (lane == 31) rt = ldg4(cur + o + 4);
-    if (xok) {
-      const float4 av = ldg4(a + o);
-      const float4 po = ld4(nxt + o);
-      float4 r;
-      if (kInc) {
-        // the increment p^{n+1} - 2 p^n + p^{n-1} (point term included)
-        const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w, rt.x, rt.y, rt.z, rt.w};
-        r = leap4p_inc(w, &q[j], po, av, &inc[j]);
-        const int d = src - o;
-        if ((unsigned)d < 4u) {
-          point_sub(r, d, cmp(av, d) * fsrc);
-          point_sub(inc[j], d, cmp(av, d) * fsrc);
-        }
-      } else {
-        r = leap4_2d(lf, c, rt, &q[j], po, av);
-        const int d = src - o;
-        if ((unsigned)d < 4u) point_sub(r, d, cmp(av, d) * fsrc);
-      }
-      st4(nxt + o, r);
-    }
-  }
+  fwd2d_rows<RZ>(L, A.a, A.cur, A.nxt, lane, x0, zb, A.info->src_off, A.wav[A.n] * A.info->src_fwd);
 }
 
 template <int RZ, bool kGrad>

@@ -65,6 +65,11 @@ SHOT_3D = Workload("3d_500x500x300_nb40_3000steps", 3, 500, 500, 300, 40, 10.0, 
                    15.0, 1500.0, 4500.0, 4500.0, 3)
 
 
+# 64 shots of uneven aperture (400-1200 columns) over a 4000 x 600 model at 5 m
+BATCH_2D = Workload("2d_batch_64shots_w400-1200_600rows_nb50_3000steps", 2, 4000, 1, 600, 50, 5.0,
+                    0.5e-3, 3000, 25.0, 1500.0, 4000.0, 4000.0, 4, nshots=64)
+
+
 def scaled(w: Workload, nx=None, ny=None, nz=None, nb=None, nt=None, name=None) -> Workload:
     """A smaller copy of a preset (same spacing, velocities and source)."""
     return dataclasses.replace(
@@ -225,3 +230,27 @@ def shot_3d_inputs(w: Workload = SHOT_3D, model_seed: int = 11):
 def random_field(shape, seed: int, lo=-1.0, hi=1.0) -> np.ndarray:
     """Seeded uniform test field (for stencil-level parity cases)."""
     return np.random.default_rng(seed).uniform(lo, hi, shape)
+
+
+def batch_2d_inputs(w: Workload = BATCH_2D, model_seed: int = 9, width_seed: int = 4,
+                    wmin: int = 400, wmax: int = 1200, rec_step: int = 2):
+    """Uneven-aperture shots over one faulted layered model.
+
+    Shot s has an interior window of width U{wmin..wmax} (seeded) centred as
+    close as it fits to (s + 0.5) w.nx / nshots; its source is at the window
+    centre at depth 1 and its receivers every `rec_step` columns at depth 1.
+    Nodes are in the shot's own padded grid."""
+    v_true = faulted_layers(w.nx, w.nz, model_seed, w.v_lo, w.v_max, nlayers=10, nfaults=3)
+    v_mig = smooth_slowness(v_true, 10.0)
+    rng = np.random.default_rng(width_seed)
+    widths = rng.integers(wmin, wmax + 1, w.nshots)
+    shots = []
+    for s, width in enumerate(widths):
+        width = int(min(width, w.nx))
+        centre = (s + 0.5) * w.nx / w.nshots
+        off = int(min(max(round(centre - width / 2), 0), w.nx - width))
+        xs = np.arange(0, width, rec_step) + w.nb
+        rec = np.stack([xs, np.zeros_like(xs), np.full_like(xs, w.nb + 1)], 1).astype(np.int32)
+        src = np.array([width // 2 + w.nb, 0, w.nb + 1], np.int32)
+        shots.append(dict(width=width, off_x=off, src=src, rec=rec))
+    return dict(v_true=v_true, v_mig=v_mig, shots=shots, wavelet=ricker(w.nt, w.dt, w.f_peak))
