@@ -238,6 +238,46 @@ int rbc_batch_timing(rbc_batch *b, int enable, double *out);
  * autotuner, work items of both kernels, and their persistent grid sizes. */
 int rbc_batch_info(const rbc_batch *b, int *out);
 
+/* ------------------------------------------------------------------------
+ * Learned denoiser of random-boundary noise in RTM images (not in the paper:
+ * it stands in for stacking K boundary realizations).  Network: five 3x3
+ * convolutions 1 -> 32 -> 32 -> 32 -> 32 -> 1 channels, zero padding, ReLU
+ * after the first four, the input added to the output.  bf16 operands, fp32
+ * accumulation, tensor cores.  Parameters: one fp32 vector of
+ * rbc_cnn_param_count() values, [W1 b1 W2 b2 W3 b3 W4 b4 W5 b5], every W
+ * stored [tap][out][in] with tap = 3 (dy + 1) + (dx + 1) for the input offset
+ * (dy, dx) in {-1, 0, 1}^2.  Images: nimg x H x W fp32, row major.
+ * ------------------------------------------------------------------------ */
+long long rbc_cnn_param_count(void);
+
+/* Bytes of the caller-owned workspace of rbc_cnn_forward/backward for a
+ * batch of nimg H x W images (bf16 activations kept for the backward pass). */
+long long rbc_cnn_workspace_bytes(int nimg, int H, int W);
+
+/* y = CNN(x).  ws_dev: workspace of rbc_cnn_workspace_bytes (keeps the
+ * activations needed by rbc_cnn_backward).  Errors: RBC_EINVAL, RBC_ECUDA. */
+int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W,
+                    const float *x_dev, float *y_dev, void *ws_dev,
+                    void *stream);
+
+/* grad_dev (param_count fp32) += dL/dparams for the dL/dy in dy_dev, using
+ * the activations the preceding rbc_cnn_forward left in ws_dev (same batch,
+ * same parameters).  Errors: RBC_EINVAL, RBC_ECUDA. */
+int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W,
+                     const float *dy_dev, float *grad_dev, void *ws_dev,
+                     void *stream);
+
+/* loss_dev (one double) += mean((y - t)^2) over n values; dy_dev (may be
+ * NULL) = 2 (y - t) / n.  Errors: RBC_EINVAL, RBC_ECUDA. */
+int rbc_cnn_mse(const float *y_dev, const float *t_dev, long long n,
+                float *dy_dev, double *loss_dev, void *stream);
+
+/* One Adam step (Kingma & Ba 2015, bias-corrected; step >= 1) on the
+ * parameter vector with moment vectors m_dev, v_dev. */
+int rbc_cnn_adam(float *params_dev, const float *grad_dev, float *m_dev,
+                 float *v_dev, float lr, float b1, float b2, float eps,
+                 int step, void *stream);
+
 /*
  * rbc_set_snapshots -- ask the next rbc_model / rbc_rtm_shot on this context
  * to copy wavefields at chosen time levels (Figure 1's propagation and

@@ -82,6 +82,16 @@ def _load():
     lib.rbc_batch_timing.argtypes = [P, I, P]
     for name in ("rbc_batch_create", "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing"):
         getattr(lib, name).restype = I
+    lib.rbc_cnn_param_count.restype = C.c_longlong
+    lib.rbc_cnn_param_count.argtypes = []
+    lib.rbc_cnn_workspace_bytes.restype = C.c_longlong
+    lib.rbc_cnn_workspace_bytes.argtypes = [I, I, I]
+    lib.rbc_cnn_forward.argtypes = [P, I, I, I, P, P, P, P]
+    lib.rbc_cnn_backward.argtypes = [P, I, I, I, P, P, P, P]
+    lib.rbc_cnn_mse.argtypes = [P, P, C.c_longlong, P, P, P]
+    lib.rbc_cnn_adam.argtypes = [P, P, P, P, F, F, F, F, I, P]
+    for name in ("rbc_cnn_forward", "rbc_cnn_backward", "rbc_cnn_mse", "rbc_cnn_adam"):
+        getattr(lib, name).restype = I
     lib.rbc_model_static.argtypes = [G, P, P, P, I, P, P, P]
     lib.rbc_model_static.restype = I
     lib.rbc_last_error.restype = C.c_char_p
@@ -97,7 +107,9 @@ _lib = _load()
 EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc_rtm_shot",
             "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing",
             "rbc_model_static", "rbc_fwi_forward", "rbc_fwi_backward", "rbc_batch_create",
-            "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing", "rbc_last_error",
+            "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing",
+            "rbc_cnn_param_count", "rbc_cnn_workspace_bytes", "rbc_cnn_forward", "rbc_cnn_backward",
+            "rbc_cnn_mse", "rbc_cnn_adam", "rbc_last_error",
             "rbc_launch_count")
 
 
@@ -279,6 +291,44 @@ def rbc_batch_info(batch):
     _check(_lib.rbc_batch_info(C.c_void_p(batch), out))
     return dict(rows_fwd=out[0], rows_rev=out[1], items_fwd=out[2], items_rev=out[3], grid_fwd=out[4],
                 grid_rev=out[5])
+
+
+def rbc_cnn_param_count() -> int:
+    return int(_lib.rbc_cnn_param_count())
+
+
+def rbc_cnn_workspace_bytes(nimg, H, W) -> int:
+    return int(_lib.rbc_cnn_workspace_bytes(int(nimg), int(H), int(W)))
+
+
+def _u8(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def rbc_cnn_forward(params, x, y, ws, stream=None):
+    """x, y: (nimg, H, W) fp32; ws: uint8 workspace of rbc_cnn_workspace_bytes."""
+    n, H, W = x.shape
+    _check(_lib.rbc_cnn_forward(_dev(params, None, "params"), n, H, W, _dev(x, None, "x"), _dev(y, None, "y"),
+                                _u8(ws, "ws"), _stream(stream)))
+
+
+def rbc_cnn_backward(params, dy, grad, ws, stream=None):
+    n, H, W = dy.shape
+    _check(_lib.rbc_cnn_backward(_dev(params, None, "params"), n, H, W, _dev(dy, None, "dy"),
+                                 _dev(grad, None, "grad"), _u8(ws, "ws"), _stream(stream)))
+
+
+def rbc_cnn_mse(y, t, dy, loss, stream=None):
+    _check(_lib.rbc_cnn_mse(_dev(y, None, "y"), _dev(t, None, "t"), y.numel(),
+                            _dev(dy, None, "dy") if dy is not None else None, _u8(loss, "loss"), _stream(stream)))
+
+
+def rbc_cnn_adam(params, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _check(_lib.rbc_cnn_adam(_dev(params, None, "params"), _dev(grad, None, "grad"), _dev(m, None, "m"),
+                             _dev(v, None, "v"), float(lr), float(b1), float(b2), float(eps), int(step),
+                             _stream(stream)))
 
 
 def rbc_last_error() -> str:

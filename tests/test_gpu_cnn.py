@@ -1,0 +1,72 @@
+"""The denoiser's tensor-core kernels (rbc_cnn_*) against the FP64 oracle
+(oracle/cnn.py, pinned by finite differences).  The oracle gets the GPU's
+bf16-rounded parameters and inputs; hidden activations are bf16 on the GPU,
+so the bar is relative L2 <= 1e-2 (forward) and <= 3e-2 (gradient)."""
+import numpy as np
+import pytest
+
+from oracle import cnn
+from rtm_cases import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 37, 70)])
+def test_cnn_forward_and_gradient_match_oracle(shape):
+    import paper_2204_03380_gb300 as R
+    rng = np.random.default_rng(sum(shape))
+    p = cnn.init_params(4)
+    p[-(9 * 32 + 1):] = rng.normal(0, 0.05, 9 * 32 + 1)
+    p = bf16(p)
+    x = bf16(rng.standard_normal(shape))
+    t = rng.standard_normal(shape)
+    y_o, cache = cnn.forward(p, x)
+    g_o = cnn.backward(p, cache, 2 * (y_o - t) / y_o.size)
+    dev = "cuda"
+    P = torch.tensor(p, dtype=torch.float32, device=dev)
+    X = torch.tensor(x, dtype=torch.float32, device=dev)
+    T = torch.tensor(t, dtype=torch.float32, device=dev)
+    Y = torch.empty_like(X)
+    ws = torch.empty(R.rbc_cnn_workspace_bytes(*shape), dtype=torch.uint8, device=dev)
+    R.rbc_cnn_forward(P, X, Y, ws)
+    dY = torch.empty_like(X)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    R.rbc_cnn_mse(Y, T, dY, loss)
+    G = torch.zeros_like(P)
+    R.rbc_cnn_backward(P, dY, G, ws)
+    torch.cuda.synchronize()
+    assert R.rbc_cnn_param_count() == p.size
+    assert rel(Y.cpu().numpy(), y_o) <= 1e-2
+    assert float(loss) == pytest.approx(cnn.mse(y_o, t), rel=2e-2)
+    assert rel(G.cpu().numpy(), g_o) <= 3e-2, rel(G.cpu().numpy(), g_o)
+
+
+def test_cnn_adam_steps_reduce_the_loss():
+    import paper_2204_03380_gb300 as R
+    rng = np.random.default_rng(9)
+    dev = "cuda"
+    x = rng.standard_normal((4, 32, 64))
+    k = np.ones((3, 3)) / 9.0
+    from scipy.signal import correlate2d
+    t = np.stack([correlate2d(xi, k, mode="same") for xi in x])     # learn a smoothing
+    P = torch.tensor(cnn.init_params(5), dtype=torch.float32, device=dev)
+    X = torch.tensor(x, dtype=torch.float32, device=dev)
+    T = torch.tensor(t, dtype=torch.float32, device=dev)
+    Y, dY = torch.empty_like(X), torch.empty_like(X)
+    M, V = torch.zeros_like(P), torch.zeros_like(P)
+    ws = torch.empty(R.rbc_cnn_workspace_bytes(*x.shape), dtype=torch.uint8, device=dev)
+    losses = []
+    for step in range(1, 61):
+        G = torch.zeros_like(P)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        R.rbc_cnn_forward(P, X, Y, ws)
+        R.rbc_cnn_mse(Y, T, dY, loss)
+        R.rbc_cnn_backward(P, dY, G, ws)
+        R.rbc_cnn_adam(P, G, M, V, 2e-3, step)
+        losses.append(float(loss))
+    assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
