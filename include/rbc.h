@@ -340,6 +340,18 @@ int rbc_model_static(const rbc_grid *g, const float *a_dev,
                      const int *src_host, const float *wavelet_dev, int nrec,
                      const int *rec_host, float *seis_dev, void *stream);
 
+/*
+ * rbc_inject_fault -- failure-detection test hook.  mode 1 (3-D contexts):
+ * in the next rbc_model / rbc_rtm_shot call, block 0 of the first forward
+ * launch never issues one of its TMA plane copies, so that block's bounded
+ * mbarrier wait runs out after about a second; the block records the
+ * timeout in the context's error word, drains its other copies and leaves,
+ * and the next call on the context returns RBC_ETIMEOUT (the results of the
+ * faulted call are invalid).  Nothing faults, traps or hangs.  mode 0
+ * clears a pending request.  Errors: RBC_EINVAL, RBC_ENOTSUP (2-D).
+ */
+int rbc_inject_fault(rbc_ctx *ctx, int mode);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char *rbc_last_error(void);
 

@@ -71,6 +71,8 @@ def _load():
     lib.rbc_set_snapshots.argtypes = [P, I, P, P, P, P]
     lib.rbc_get_panels.argtypes = [P, P, P, P]
     lib.rbc_phase_timing.argtypes = [P, I, P]
+    lib.rbc_inject_fault.argtypes = [P, I]
+    lib.rbc_inject_fault.restype = I
     lib.rbc_fwi_forward.argtypes = [P, P, P, I, P, P, P, P, P, P]
     lib.rbc_fwi_backward.argtypes = [P, P, P, I, P, P, P, P, P]
     lib.rbc_fwi_forward.restype = I
@@ -109,7 +111,7 @@ EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc
             "rbc_model_static", "rbc_fwi_forward", "rbc_fwi_backward", "rbc_batch_create",
             "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing",
             "rbc_cnn_param_count", "rbc_cnn_workspace_bytes", "rbc_cnn_forward", "rbc_cnn_backward",
-            "rbc_cnn_mse", "rbc_cnn_adam", "rbc_last_error",
+            "rbc_cnn_mse", "rbc_cnn_adam", "rbc_inject_fault", "rbc_last_error",
             "rbc_launch_count")
 
 
@@ -329,6 +331,12 @@ def rbc_cnn_adam(params, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-8, strea
     _check(_lib.rbc_cnn_adam(_dev(params, None, "params"), _dev(grad, None, "grad"), _dev(m, None, "m"),
                              _dev(v, None, "v"), float(lr), float(b1), float(b2), float(eps), int(step),
                              _stream(stream)))
+
+
+def rbc_inject_fault(ctx, mode=1):
+    """Test hook: make the next call's first 3-D forward launch run a bounded
+    wait out (see include/rbc.h); the call after it reports RBC_ETIMEOUT."""
+    _check(_lib.rbc_inject_fault(C.c_void_p(ctx), int(mode)))
 
 
 def rbc_last_error() -> str:

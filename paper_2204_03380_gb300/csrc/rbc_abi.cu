@@ -127,6 +127,7 @@ struct rbc_ctx {
   // error word of the kernels' bounded waits (mapped host memory)
   int *err_host = nullptr;
   int *err_dev = nullptr;
+  int fault = 0;  // rbc_inject_fault: applies to the next call only
 };
 
 namespace {
@@ -195,6 +196,8 @@ int upload_shot(rbc_ctx *c, const int *src, int nrec, const int *rec, int reinje
   info.src_fwd = (float)ps;
   info.src_rev = reinject ? (float)ps : 0.f;
   info.rec_scale = (float)ps;
+  info.fault = c->fault;
+  c->fault = 0;
   int gx, gy, gz, t;
   rev_tiling(L, c->zc, &gx, &gy, &gz, &t);
   std::vector<int> off(std::max(nrec, 1)), tile(std::max(nrec, 1)), ptr(c->ntiles + 1, 0),
@@ -738,6 +741,14 @@ int rbc_phase_timing(rbc_ctx *c, int enable, double *out) {
     out[3] = (double)shots * (c->g.nt + 1);
     out[4] = (double)shots;
   }
+  return RBC_OK;
+}
+
+int rbc_inject_fault(rbc_ctx *c, int mode) {
+  if (!c) return fail(RBC_EINVAL, "ctx is NULL");
+  if (mode != 0 && mode != 1) return fail(RBC_EINVAL, "unknown fault mode %d", mode);
+  if (mode == 1 && c->L.ndim != 3) return fail(RBC_ENOTSUP, "fault mode 1 needs a 3-D context");
+  c->fault = mode;
   return RBC_OK;
 }
 

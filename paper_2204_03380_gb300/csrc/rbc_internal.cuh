@@ -54,7 +54,8 @@ struct ShotInfo {
   float src_fwd;   // h^(2-d): forward injection scale
   float src_rev;   // h^(2-d) or 0: reconstruction re-subtraction scale
   float rec_scale; // +h^(2-d): receiver injection scale (Eq. 2)
-  int pad[3];
+  int fault;       // test hook: 1 = the first 3-D forward launch withholds one plane
+  int pad[2];
 };
 
 struct StepArgs {

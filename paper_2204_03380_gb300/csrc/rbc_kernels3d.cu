@@ -218,7 +218,14 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_fwd3d_tma(const __grid_consta
       const uint32_t pbytes = sizeof(float) * kPStage, tbytes = sizeof(float) * 2 * kTTile;
       int gp = 0, gt = 0;  // sequence numbers
       bool ok = true;
+      // failure-detection test hook: block 0 of the first step never issues
+      // P plane 8, so its consumers' bounded wait runs out
+      const int withhold = (A.info->fault == 1 && A.n == 0 && blockIdx.x == 0) ? 8 : -1;
       auto issueP = [&](int plane, int hx, int hy) {
+        if (gp == withhold) {
+          ++gp;
+          return;
+        }
         const int s = gp % kRP, f = gp / kRP;
         if (f > 0) ok = mbar_wait_ab(&emptyP[s], (f - 1) & 1, abort_blk);
         if (!ok) return;
@@ -248,7 +255,8 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_fwd3d_tma(const __grid_consta
       if (*abort_blk) {
         flag_error(A.err, 1);
         // let every issued copy land before the block's shared memory is released
-        for (int k = max(0, gp - kRP); k < gp; ++k) mbar_wait(&fullP[k % kRP], (k / kRP) & 1);
+        for (int k = max(0, gp - kRP); k < gp; ++k)
+          if (k != withhold) mbar_wait(&fullP[k % kRP], (k / kRP) & 1);
         for (int k = max(0, gt - kRT); k < gt; ++k) mbar_wait(&fullT[k % kRT], (k / kRT) & 1);
       }
     }
