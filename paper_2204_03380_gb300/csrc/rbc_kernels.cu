@@ -19,6 +19,29 @@
 
 namespace rbc {
 
+// Programmatic dependent launch: the kernels of consecutive time steps are
+// launched with programmatic stream serialisation, so the next step's grid
+// can be scheduled while this one drains; each kernel waits for its
+// predecessor's completion (and memory) before touching the fields and lets
+// its dependents launch after its own stores.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Record the current level at every receiver (Algorithm 1 "record
 // seismogram"): grid-strided so any block may sample any receiver.
 __device__ __forceinline__ void sample_receivers(const StepArgs &A, int nblocks, int bid) {
@@ -56,9 +79,11 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d(const StepArgs A) {
   const int lane = threadIdx.x, w = threadIdx.y;
   const int x0 = blockIdx.x * kTileX + lane * 4;
   const int zb = (blockIdx.y * k2dWarps + w) * RZ;
+  griddep_wait();
   if (A.sample) sample_receivers(A, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
-  if (zb >= L.NZ) return;  // warp-uniform; no block barrier in this kernel
-  fwd2d_rows<RZ>(L, A.a, A.cur, A.nxt, lane, x0, zb, A.info->src_off, A.wav[A.n] * A.info->src_fwd);
+  if (zb < L.NZ)  // warp-uniform; no block barrier in this kernel
+    fwd2d_rows<RZ>(L, A.a, A.cur, A.nxt, lane, x0, zb, A.info->src_off, A.wav[A.n] * A.info->src_fwd);
+  griddep_launch();
 }
 
 template <int RZ, bool kGrad>
@@ -69,6 +94,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
   const int zb = (blockIdx.y * k2dWarps + w) * RZ;
   const bool xok = x0 < L.NX4;
   const bool active = zb < L.NZ;  // warp-uniform
+  griddep_wait();
   if (active) {
     float4 cr[RZ], cb[RZ], inc[RZ];
     const int src = A.info->src_off;
@@ -103,6 +129,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
     }
   }
   if (A.do_b) inject_receivers(A, blockIdx.y * gridDim.x + blockIdx.x);
+  griddep_launch();
 }
 
 // ------------------------------------------------------------ launchers ----
@@ -112,7 +139,7 @@ bool launch_fwd(const StepArgs &A, cudaStream_t s) {
   const Lay &L = A.L;
   if (L.ndim == 3) return launch_fwd3d(A, s);
   dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarps * k2dRowsF));
-  k_fwd2d<k2dRowsF><<<grid, dim3(32, k2dWarps), 0, s>>>(A);
+  launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarps), 0, s, A);
   return true;
 }
 
@@ -135,9 +162,9 @@ bool launch_rev(const RevArgs &A, cudaStream_t s) {
   int gx, gy, gz, t;
   rev_tiling(A.L, A.zc, &gx, &gy, &gz, &t);
   if (A.mode == 1)
-    k_rev2d<k2dRowsR, true><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
+    launch_pdl(k_rev2d<k2dRowsR, true>, dim3(gx, gy), dim3(32, k2dWarps), 0, s, A);
   else
-    k_rev2d<k2dRowsR, false><<<dim3(gx, gy), dim3(32, k2dWarps), 0, s>>>(A);
+    launch_pdl(k_rev2d<k2dRowsR, false>, dim3(gx, gy), dim3(32, k2dWarps), 0, s, A);
   return true;
 }
 
