@@ -54,6 +54,11 @@ def _L():
             lib.orc_rtm_shot.argtypes = [i, i, i, i, P, d, i, P, P, i, P, P, i, d,
                                          i, i, i, i, P, P, i, P, P, P]
             lib.orc_rtm_shot.restype = i
+            lib.orc_rtm_storage.argtypes = [i, i, i, i, P, d, i, P, P, i, P, P, d, i,
+                                            i, i, i, i, P, P, P]
+            lib.orc_rtm_storage.restype = i
+            lib.orc_nyquist_stride.argtypes = [d, d, d]
+            lib.orc_nyquist_stride.restype = i
             lib.orc_image.argtypes = [C.c_long, P, P, d, P]
             lib.orc_stack.argtypes = [i, i, i, P, i, i, i, i, P]
             lib.orc_energy.argtypes = [i, i, i, i, P, P, P]
@@ -169,6 +174,40 @@ def rtm_shot(a, h, nt, src, wavelet, rec, seis, nb, interior, reinject=True,
     if rc:
         raise ValueError("orc_rtm_shot: bad argument")
     return dict(num=num, den=den, pr=prs, pb=pbs)
+
+
+def nyquist_stride(dt, f_max, f_min=0.0) -> int:
+    """Eq. 7: k = floor(dt_nyq / dt) with dt_nyq = 1 / (2 (f_max - f_min)); 0 on a bad argument."""
+    return int(_L().orc_nyquist_stride(float(dt), float(f_max), float(f_min)))
+
+
+def rtm_storage(a, h, nt, src, wavelet, rec, seis, nb, interior, stride, rec_sign=REC_SIGN,
+                keep_store=False):
+    """Algorithm 2 (RTM with wavefield storage) for one shot: the source
+    wavefield is stored at levels 0, k, 2k, ... (k = stride) and the imaging
+    integrals of Eq. 3 are accumulated at those levels only.
+
+    Returns dict(num, den) on the interior and, with keep_store, the stored
+    interior fields store[j] = p^{j k}."""
+    a = _f64(a)
+    nd, NX, NY, NZ = _dims(a.shape)
+    nx, ny, nz = interior
+    ishape = (nz, nx) if nd == 2 else (nz, ny, nx)
+    num, den = np.zeros(ishape), np.zeros(ishape)
+    rec = _i32(np.asarray(rec).reshape(-1, 3))
+    seis = _f64(seis)
+    assert seis.shape == (rec.shape[0], nt + 1)
+    store = np.zeros((nt // stride + 1,) + ishape) if keep_store else None
+    rc = _L().orc_rtm_storage(nd, NX, NY, NZ, _p(a), float(h), int(nt), _p(_i32(src)),
+                              _p(_f64(wavelet)), rec.shape[0], _p(rec), _p(seis), float(rec_sign),
+                              int(stride), int(nb), int(nx), int(ny if nd == 3 else 1), int(nz),
+                              _p(num), _p(den), _p(store) if keep_store else None)
+    if rc:
+        raise ValueError("orc_rtm_storage: bad argument")
+    out = dict(num=num, den=den)
+    if keep_store:
+        out["store"] = store
+    return out
 
 
 def image(num, den, eps_rel=1e-6):

@@ -21,6 +21,9 @@
  *     the seismogram as source in reversed time) and Eq. 3 (source-normalised
  *     cross-correlation imaging condition), combined as Algorithm 3 (RTM with
  *     wavefield reconstruction); shot stacking as Algorithm 3's last step.
+ *   - Algorithm 2 (RTM with wavefield storage): the forward wavefield kept
+ *     every k steps, k from the Nyquist step of Eq. 7, and the Eq. 3
+ *     integrals accumulated at the kept levels.
  *
  * Readings where the paper is silent (each listed in the design notes):
  *   - Stencil weights are the standard 8th-order central second-derivative
@@ -270,6 +273,109 @@ int orc_rtm_shot(int ndim, int NX, int NY, int NZ, const double *a, double h,
 done:
   free(A); free(B); free(C);
   free(pb_prev); free(pb_cur); free(pb_next);
+  return rc;
+}
+
+/*
+ * Eq. 7: the Nyquist time step of a source band [f_min, f_max] is
+ * dt_nyq = 1 / (2 (f_max - f_min)); the source wavefield is kept every
+ * k = floor(dt_nyq / dt) finite-difference steps (at least 1).  The small
+ * guard absorbs a ratio such as 9.999999999 that is an integer in exact
+ * arithmetic.  Returns 0 on a bad argument.
+ */
+int orc_nyquist_stride(double dt, double f_max, double f_min) {
+  if (!(dt > 0.0) || !(f_max > f_min) || !(f_min >= 0.0)) return 0;
+  double dt_nyq = 1.0 / (2.0 * (f_max - f_min));
+  double k = floor(dt_nyq / dt + 1e-9);
+  return k < 1.0 ? 1 : (int)k;
+}
+
+/*
+ * Algorithm 2 (RTM with wavefield storage) for one shot, with the source
+ * wavefield stored only at the levels n = 0, k, 2k, ... <= N (k = stride,
+ * from Eq. 7 in the paper's experiments).
+ * Forward: Algorithm 1 (no recording); at every kept level the interior box
+ *   of p^n is written to store[n / k] ([nz][ny][nx], the box at padded node
+ *   (nb, nb, nb)).
+ * Reverse, n = N .. 0:
+ *   image at kept levels only:  num += p^n pbar_n,  den += (p^n)^2  (Eq. 3
+ *     integrals sampled every k steps);
+ *   Eq. 2:  pbar_{n-1} = 2 pbar_n - pbar_{n+1} + a L8 pbar_n
+ *                        + rec_sign * sum_r a_r s[r][n] h^(2-d) delta_r,
+ *   with pbar_{N+1} = pbar_N = 0.
+ * store: NULL or (N / k + 1) interior boxes (written).  num, den accumulated.
+ * Returns 0, or -1 on a bad argument.
+ */
+int orc_rtm_storage(int ndim, int NX, int NY, int NZ, const double *a, double h,
+                    int nt, const int *src, const double *wavelet, int nrec,
+                    const int *rec, const double *seis, double rec_sign,
+                    int stride, int nb, int nx, int ny, int nz, double *num,
+                    double *den, double *store) {
+  dims_t g = mkdims(ndim, NX, NY, NZ);
+  long N = npts(&g);
+  if (ndim == 2) ny = 1;
+  long yoff = (ndim == 3) ? nb : 0;
+  if (stride < 1 || nt < 1) return -1;
+  if (nb + nx > NX || nb + nz > NZ || (ndim == 3 && nb + ny > NY)) return -1;
+  if (!inside(&g, src)) return -1;
+  for (int r = 0; r < nrec; ++r)
+    if (!inside(&g, rec + 3 * r)) return -1;
+  long nbox = (long)nx * ny * nz;
+  long nkeep = nt / stride + 1;
+  double *S = store ? store : malloc(nkeep * nbox * sizeof(double));
+  double *pm = calloc(N, sizeof(double)); /* p^{n-1} */
+  double *pc = calloc(N, sizeof(double)); /* p^n     */
+  double *pn = calloc(N, sizeof(double)); /* p^{n+1} */
+  int rc = -1;
+  if (!S || !pm || !pc || !pn) goto done;
+  /* forward (Algorithm 2, first loop): solve Eq. 1, keep every k-th level */
+  {
+    long s = ridx(&g, src);
+    double ps = point_scale(ndim, h);
+    for (int n = 0; n <= nt; ++n) {
+      if (n % stride == 0) {
+        double *box = S + (long)(n / stride) * nbox;
+        for (long z = 0; z < nz; ++z)
+          for (long y = 0; y < ny; ++y)
+            for (long x = 0; x < nx; ++x)
+              box[(z * ny + y) * nx + x] = pc[idx(&g, x + nb, y + yoff, z + nb)];
+      }
+      if (n == nt) break;
+      leapfrog(&g, a, pm, pc, pn);
+      pn[s] -= a[s] * wavelet[n] * ps;
+      double *t = pm; pm = pc; pc = pn; pn = t;
+    }
+  }
+  /* reverse (second loop): receiver wavefield, imaging at the kept levels */
+  memset(pm, 0, N * sizeof(double)); /* pbar_{n+1} */
+  memset(pc, 0, N * sizeof(double)); /* pbar_n     */
+  {
+    double ps = point_scale(ndim, h);
+    for (int n = nt; n >= 0; --n) {
+      if (n % stride == 0) {
+        const double *box = S + (long)(n / stride) * nbox;
+        for (long z = 0; z < nz; ++z)
+          for (long y = 0; y < ny; ++y)
+            for (long x = 0; x < nx; ++x) {
+              long o = (z * ny + y) * nx + x;
+              double p = box[o];
+              num[o] += p * pc[idx(&g, x + nb, y + yoff, z + nb)];
+              den[o] += p * p;
+            }
+      }
+      if (n == 0) break;
+      leapfrog(&g, a, pm, pc, pn);
+      for (int r = 0; r < nrec; ++r) {
+        long j = ridx(&g, rec + 3 * r);
+        pn[j] += rec_sign * a[j] * seis[(long)r * (nt + 1) + n] * ps;
+      }
+      double *t = pm; pm = pc; pc = pn; pn = t;
+    }
+  }
+  rc = 0;
+done:
+  if (!store) free(S);
+  free(pm); free(pc); free(pn);
   return rc;
 }
 
