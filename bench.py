@@ -60,15 +60,21 @@ def parse():
                         "small profiler captures")
     p.add_argument("--interior", type=int, nargs="+", default=None,
                    help="interior size override (nx nz | nx ny nz); only for small profiler captures")
+    p.add_argument("--method", choices=["rbc", "storage"], default="rbc",
+                   help="survey2d / shot3d: rbc = Algorithm 3 (reconstruction through the random boundary, "
+                        "default); storage = Algorithm 2 with the source wavefield kept in device memory every "
+                        "k steps, k from Eq. 7 with f_max = 2.5 x the peak frequency")
     p.add_argument("--denoise-models", type=int, default=96, help="denoise: training models")
     p.add_argument("--denoise-size", type=int, default=128, help="denoise: training image size")
-    p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d", "denoise"], default="survey2d",
+    p.add_argument("--cnn-batch", type=int, nargs=3, default=[32, 512, 512],
+                   help="cnn: images, height, width of one training / inference batch")
+    p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d", "denoise", "cnn"], default="survey2d",
                    help="survey2d: the 240-shot 2-D survey (default); shot3d: one 3-D shot on "
                         "500 x 500 x 300 + 40 (one step = one RTM shot); batch2d: 64 shots of "
                         "400-1200 columns x 600 rows in one launch per time step (one step = the batch)")
     a = p.parse_args()
     if a.steps is None:
-        a.steps = {"survey2d": 30, "shot3d": 3, "batch2d": 5, "denoise": 3}[a.workload]
+        a.steps = {"survey2d": 30, "shot3d": 3, "batch2d": 5, "denoise": 3, "cnn": 20}[a.workload]
     if a.shots_per_step is None:
         a.shots_per_step = 8 if a.workload == "survey2d" else 1
     return a
@@ -152,6 +158,16 @@ def shot_plan(nshots_total: int, steps: int, warmup: int, per_step: int, rank: i
 def updates_per_shot(w) -> int:
     # forward nt, reconstruction nt - 1, receiver wavefield nt updates per node
     return w.npad * (3 * w.nt - 1)
+
+
+def storage_phase_bytes(w, stride):
+    """Algorithmic bytes of Algorithm 2's two phases: nt leapfrog steps each
+    (16 B per padded node) plus, at the kept levels, the interior store
+    (read 4 + write 4) in the forward phase and the imaging read of the store,
+    of pbar and the num/den read-modify-write (4 + 4 + 16) in the reverse."""
+    nint = w.nx * (w.ny if w.ndim == 3 else 1) * w.nz
+    kept = w.nt // stride + 1
+    return 16 * w.npad * w.nt + 8 * nint * kept, 16 * w.npad * w.nt + 24 * nint * kept
 
 
 def rev_bytes_per_launch(w) -> int:
@@ -457,6 +473,58 @@ def run_denoise(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_cnn(args, rank, world):
+    """cnn: the denoiser's kernels on their own.  One step = one training step
+    (forward, MSE, backward, Adam) on a batch of seeded random images; the
+    inference forward of the same batch is timed separately and gives the
+    tensor-core roofline line (56 448 flop per pixel over the 5 layers)."""
+    import torch
+    from paper_2204_03380_gb300 import denoise as D
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    n, H, Wd = args.cnn_batch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((n, H, Wd), generator=g, device="cuda")
+    t = torch.randn((n, H, Wd), generator=g, device="cuda")
+    net = D.Denoiser(seed=1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        net.train_step(x, t, 1e-5)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        net.train_step(x, t, 1e-5)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_train = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    for _ in range(args.warmup):
+        y = net(x)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        y = net(x)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_inf = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    assert torch.isfinite(y).all()
+    px = n * H * Wd
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    achieved = 56448.0 * px / t_inf / 1e12
+    out = {"metric": METRIC, "value": px / t_train / 1e9, "unit": "Gpx/s (training: forward + backward + Adam)",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_train * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+           "data": "synthetic", "config": {"workload": f"cnn: batch of {n} images of {H}x{Wd}",
+                                           "train_step_ms": t_train * 1e3, "inference_ms": t_inf * 1e3,
+                                           "training_tflops": 3 * 56448.0 * px / t_train / 1e12},
+           "roofline": {"bound": "tensor", "kernel": "k_conv3x3 (5 layers, mma.sync bf16)", "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
+           "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -498,6 +566,9 @@ def main():
         return
     if args.workload == "denoise":
         run_denoise(args, rank, world)
+        return
+    if args.workload == "cnn":
+        run_cnn(args, rank, world)
         return
     import torch
     import paper_2204_03380_gb300 as R
@@ -548,8 +619,16 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     flags = R.RBC_REINJECT_SOURCE | R.RBC_ZERO_FIRST
 
+    storage = args.method == "storage"
+    if storage:
+        stride = R.rbc_nyquist_stride(w.dt, 2.5 * w.f_peak)
+        store = torch.empty(R.rbc_storage_bytes(g, stride) // 4, dtype=torch.float32, device=dev)
+
     def migrate(shot, d):
-        R.rbc_rtm_shot(ctx, srcs[shot], wav, rec, d, flags, num, den)
+        if storage:
+            R.rbc_rtm_storage(ctx, srcs[shot], wav, rec, d, stride, store, R.RBC_ZERO_FIRST, num, den)
+        else:
+            R.rbc_rtm_shot(ctx, srcs[shot], wav, rec, d, flags, num, den)
         R.rbc_image_stack(g, num, den, EPS_REL, 0, 0, g, image)
 
     for s in range(args.warmup):
@@ -580,7 +659,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el = float(t.item())
     shots_total = args.steps * B * world
-    upd = updates_per_shot(w) * shots_total
+    # Algorithm 3 solves three wave equations per step, Algorithm 2 two
+    upd = (2 * w.npad * w.nt if storage else updates_per_shot(w)) * shots_total
     value = upd / el / 1e9
 
     # end to end: records from pinned host memory, image read back every step
@@ -630,12 +710,22 @@ def main():
                          "so achieved can exceed the HBM copy bandwidth") if w.ndim == 2 else
                         "working set of 4 GB: DRAM-bound"}
 
+    if storage:
+        nshots_ph = max(phases["shots"], 1)
+        fb, rb = storage_phase_bytes(w, stride)
+        fwd_s, rev_s = phases["fwd_ms"] / 1e3 / nshots_ph, phases["rev_ms"] / 1e3 / nshots_ph
+        achieved = (fb + rb) / (fwd_s + rev_s) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_fwd2d/k_fwd3d_tma steps + store/image kernels (whole phases)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": roofline["peak_source"], "traffic": None,
+                    "forward_phase": {"bytes": fb, "s": fwd_s, "GB/s": fb / fwd_s / 1e9},
+                    "reverse_phase": {"bytes": rb, "s": rev_s, "GB/s": rb / rev_s / 1e9}}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and not storage:
         ns = ORACLE_SAMPLE_STEPS if w.ndim == 2 else 8
         v, dt = oracle_rtm_sample(w, inp, ns)
         cpu = {"value": v, "unit": "Gpts/s", "cores": cores_used(), "kind": "oracle",
@@ -650,7 +740,11 @@ def main():
                       "survey_s": el / (args.steps * B) * w.nshots,
                       "updates_per_shot": updates_per_shot(w),
                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                      "parallelism": f"shots sharded over {world} GPU(s)"},
+                      "parallelism": f"shots sharded over {world} GPU(s)",
+                      "method": (f"storage: Algorithm 2, source wavefield kept every {stride} steps "
+                                 f"(Eq. 7, f_max = {2.5 * w.f_peak:g} Hz), store {store.numel() * 4 / 2**30:.2f} GiB "
+                                 "in device memory") if storage else
+                                "rbc: Algorithm 3, reconstruction through the random boundary"},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": clocks}
     print(json.dumps(out), flush=True)

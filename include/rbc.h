@@ -141,6 +141,48 @@ int rbc_rtm_shot(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
                  int flags, float *num_dev, float *den_dev, void *stream);
 
 /*
+ * rbc_nyquist_stride -- Eq. 7: the source wavefield of RTM with wavefield
+ * storage is kept every k = floor(dt_nyq / dt) steps (at least 1), where
+ * dt_nyq = 1 / (2 (f_max - f_min)) for the source band [f_min, f_max] in Hz.
+ * Returns k >= 1, or 0 when dt <= 0 or not 0 <= f_min < f_max (message in
+ * rbc_last_error).  Host only.
+ */
+int rbc_nyquist_stride(double dt, double f_max, double f_min);
+
+/*
+ * rbc_storage_bytes -- size of the store that rbc_rtm_storage needs: the
+ * interior box (nz, ny, nx) fp32 of every kept level n = 0, k, 2k, ... <= nt,
+ * i.e. 4 nx ny nz (nt / k + 1) bytes.  Returns -1 on a bad grid or k < 1.
+ * Host only.
+ */
+long long rbc_storage_bytes(const rbc_grid *g, int stride);
+
+/*
+ * rbc_rtm_storage -- Algorithm 2 (RTM with wavefield storage) for one shot,
+ * the baseline that reconstruction (rbc_rtm_shot) replaces; the paper runs
+ * it with the Nyquist stride of Eq. 7 and keeps the wavefield on disk, here
+ * it stays in device memory.
+ *   Forward: Algorithm 1 without recording; level n = j k (j = 0 .. nt / k)
+ *   is written to store_dev + j nx ny nz as a dense interior (nz, ny, nx)
+ *   fp32 box (the store is an output the caller may read afterwards).
+ *   Reverse, n = nt .. 0: at the kept levels num += p^n pbar_n and
+ *   den += (p^n)^2 (Eq. 3 integrals sampled every k steps); pbar_{n-1} from
+ *   Eq. 2 with the record injected as + a_r s[r][n] h^(2-d).
+ *   stride: k >= 1 (rbc_nyquist_stride gives Eq. 7's).
+ *   store_dev, store_bytes: caller-owned device memory of at least
+ *   rbc_storage_bytes(grid, stride) bytes.
+ *   flags: 0 or RBC_ZERO_FIRST; num_dev, den_dev as in rbc_rtm_shot.
+ * The context keeps a graph per (store_dev, stride) pair: a call with another
+ * pair captures anew.  Afterwards the context holds p^{nt-1}, p^{nt}.
+ * Errors: as rbc_rtm_shot; store smaller than needed, stride < 1 or other
+ * flags -> RBC_EINVAL.
+ */
+int rbc_rtm_storage(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
+                    int nrec, const int *rec_host, const float *seis_dev,
+                    int stride, float *store_dev, long long store_bytes,
+                    int flags, float *num_dev, float *den_dev, void *stream);
+
+/*
  * rbc_image_stack -- Eq. 3 ratio and Algorithm 3 stacking:
  *   I = num / (den + eps_rel * max(den)) over the shot interior (nz, ny, nx),
  *   image[z][y + off_y][x + off_x] += I[z][y][x]   (survey grid interior),

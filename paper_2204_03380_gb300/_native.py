@@ -68,6 +68,11 @@ def _load():
     lib.rbc_model.argtypes = [P, P, P, I, P, P, P]
     lib.rbc_rtm_shot.argtypes = [P, P, P, I, P, P, I, P, P, P]
     lib.rbc_image_stack.argtypes = [G, P, P, F, I, I, G, P, P]
+    lib.rbc_nyquist_stride.argtypes = [C.c_double, C.c_double, C.c_double]
+    lib.rbc_nyquist_stride.restype = I
+    lib.rbc_storage_bytes.argtypes = [G, I]
+    lib.rbc_storage_bytes.restype = C.c_longlong
+    lib.rbc_rtm_storage.argtypes = [P, P, P, I, P, P, I, P, C.c_longlong, I, P, P, P]
     lib.rbc_set_snapshots.argtypes = [P, I, P, P, P, P]
     lib.rbc_get_panels.argtypes = [P, P, P, P]
     lib.rbc_phase_timing.argtypes = [P, I, P]
@@ -112,7 +117,7 @@ EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc
             "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing",
             "rbc_cnn_param_count", "rbc_cnn_workspace_bytes", "rbc_cnn_forward", "rbc_cnn_backward",
             "rbc_cnn_mse", "rbc_cnn_adam", "rbc_inject_fault", "rbc_last_error",
-            "rbc_launch_count")
+            "rbc_launch_count", "rbc_nyquist_stride", "rbc_storage_bytes", "rbc_rtm_storage")
 
 
 def _check(code):
@@ -176,6 +181,34 @@ def rbc_rtm_shot(ctx, src, wavelet, rec, seis, flags, num, den, stream=None):
                              r.shape[0], r.ctypes.data_as(C.c_void_p) if r.size else None,
                              _dev(seis, None, "seis") if r.shape[0] else None, int(flags),
                              _dev(num, None, "num"), _dev(den, None, "den"), _stream(stream)))
+
+
+def rbc_nyquist_stride(dt, f_max, f_min=0.0) -> int:
+    k = int(_lib.rbc_nyquist_stride(float(dt), float(f_max), float(f_min)))
+    if k < 1:
+        raise RBCError(RBC_EINVAL, _lib.rbc_last_error().decode())
+    return k
+
+
+def rbc_storage_bytes(grid, stride) -> int:
+    n = int(_lib.rbc_storage_bytes(C.byref(grid), int(stride)))
+    if n < 0:
+        raise RBCError(RBC_EINVAL, _lib.rbc_last_error().decode())
+    return n
+
+
+def rbc_rtm_storage(ctx, src, wavelet, rec, seis, stride, store, flags, num, den, stream=None):
+    """store: contiguous fp32 CUDA tensor of at least rbc_storage_bytes(grid, stride) bytes."""
+    s = _nodes(src, 1)
+    r = _nodes(rec)
+    if not (isinstance(store, torch.Tensor) and store.is_cuda and store.dtype == torch.float32
+            and store.is_contiguous()):
+        raise TypeError("store must be a contiguous float32 CUDA tensor")
+    _check(_lib.rbc_rtm_storage(C.c_void_p(ctx), s.ctypes.data_as(C.c_void_p), _dev(wavelet, None, "wavelet"),
+                                r.shape[0], r.ctypes.data_as(C.c_void_p) if r.size else None,
+                                _dev(seis, None, "seis") if r.shape[0] else None, int(stride),
+                                C.c_void_p(store.data_ptr()), store.numel() * 4, int(flags),
+                                _dev(num, None, "num"), _dev(den, None, "den"), _stream(stream)))
 
 
 def rbc_image_stack(shot_grid, num, den, eps_rel, off_x, off_y, survey_grid, image, stream=None):

@@ -99,7 +99,7 @@ struct rbc_ctx {
   float *buf = nullptr;  // one allocation: a, p0, p1, q0, q1, num, den
   float *a = nullptr, *p[2] = {nullptr, nullptr}, *q[2] = {nullptr, nullptr};
   float *num = nullptr, *den = nullptr;
-  ShotInfo *info = nullptr;
+  ShotInfo *info = nullptr;  // [0]: this shot; [1]: no source, no receivers (Algorithm 2's pbar steps)
   float *wav = nullptr;
   int rec_cap = 0;
   int *rec_off = nullptr;
@@ -109,9 +109,12 @@ struct rbc_ctx {
   float *seis_t = nullptr;
   cudaStream_t cap = nullptr;
   // cached graphs: 0 = modeling loop, 1 = RTM forward phase, 2 = RTM reverse phase,
-  // 3 = FWI adjoint phase
-  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
-  long long gnodes[4] = {0, 0, 0, 0};
+  // 3 = FWI adjoint phase, 4/5 = storage-RTM forward/reverse phase (for store, stride)
+  static constexpr int kGraphs = 6;
+  cudaGraphExec_t gexec[kGraphs] = {};
+  long long gnodes[kGraphs] = {};
+  float *store = nullptr;  // Algorithm 2: the kept levels of the graphs 4/5
+  int stride = 0;
   double *misfit_tmp = nullptr;
   // phase timing (rbc_phase_timing)
   bool timing = false;
@@ -133,7 +136,7 @@ struct rbc_ctx {
 namespace {
 
 void drop_graphs(rbc_ctx *c) {
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < rbc_ctx::kGraphs; ++k) {
     if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
     c->gexec[k] = nullptr;
   }
@@ -390,6 +393,82 @@ int enq_fwi_adj(rbc_ctx *c, cudaStream_t s, int) {
   return RBC_OK;
 }
 
+// Algorithm 2, first loop: Algorithm 1 without recording; the interior of
+// every k-th level p^n (n = 0, k, ..., <= nt) goes to slot n / k of the store.
+int enq_store_fwd(rbc_ctx *c, cudaStream_t s, int) {
+  const Lay &L = c->L;
+  const size_t bytes = sizeof(float) * (size_t)L.total;
+  CK(cudaMemsetAsync(c->p[0], 0, bytes, s));
+  CK(cudaMemsetAsync(c->p[1], 0, bytes, s));
+  const rbc_grid &g = c->g;
+  const long long nint = (long long)g.nx * g.ny * g.nz;
+  StepArgs A{};
+  A.L = L;
+  A.a = c->a;
+  A.info = c->info;
+  A.wav = c->wav;
+  A.rec_off = c->rec_off;
+  A.seis_t = c->seis_t;
+  A.sample = 0;
+  A.zc = c->zc;
+  A.err = c->err_dev;
+  for (int n = 0; n <= g.nt; ++n) {
+    if (n % c->stride == 0) {
+      launch_store_level(L, c->p[n & 1], c->store + (n / c->stride) * nint, g.nb, g.nx, g.ny, g.nz, s);
+      ++g_launches;
+    }
+    if (n == g.nt) break;
+    A.cur = c->p[n & 1];
+    A.nxt = c->p[(n + 1) & 1];
+    A.n = n;
+    if (!launch_fwd(A, s)) return fail(RBC_ECUDA, "tensor map encoding failed");
+    ++g_launches;
+  }
+  CKL();
+  return RBC_OK;
+}
+
+// Algorithm 2, second loop, n = nt .. 0: Eq. 3 integrals at the kept levels
+// (p^n read from the store), then pbar_{n-1} by the leapfrog step (the step
+// is symmetric in time, so the forward kernel runs it with the silent shot
+// record info[1]) and the record row n injected at the receivers.
+int enq_store_rev(rbc_ctx *c, cudaStream_t s, int) {
+  const Lay &L = c->L;
+  const size_t bytes = sizeof(float) * (size_t)L.total;
+  CK(cudaMemsetAsync(c->q[0], 0, bytes, s));
+  CK(cudaMemsetAsync(c->q[1], 0, bytes, s));
+  CK(cudaMemsetAsync(c->num, 0, bytes, s));
+  CK(cudaMemsetAsync(c->den, 0, bytes, s));
+  const rbc_grid &g = c->g;
+  const long long nint = (long long)g.nx * g.ny * g.nz;
+  StepArgs B{};
+  B.L = L;
+  B.a = c->a;
+  B.info = c->info + 1;
+  B.wav = c->wav;
+  B.rec_off = c->rec_off;
+  B.seis_t = c->seis_t;
+  B.sample = 0;
+  B.n = 0;  // the silent info scales f[0] by 0
+  B.zc = c->zc;
+  B.err = c->err_dev;
+  for (int n = g.nt; n >= 0; --n) {
+    if (n % c->stride == 0) {
+      launch_store_image(L, c->store + (n / c->stride) * nint, c->q[n & 1], c->num, c->den, g.nb, g.nx, g.ny,
+                         g.nz, s);
+      ++g_launches;
+    }
+    if (n == 0) break;
+    B.cur = c->q[n & 1];
+    B.nxt = c->q[(n + 1) & 1];
+    if (!launch_fwd(B, s)) return fail(RBC_ECUDA, "tensor map encoding failed");
+    launch_rec_inject(c->a, c->q[(n + 1) & 1], c->rec_off, c->info, c->seis_t, n, c->rec_cap, s);
+    g_launches += 2;
+  }
+  CKL();
+  return RBC_OK;
+}
+
 int record_event(rbc_ctx *c, cudaStream_t s) {
   cudaEvent_t e;
   if (!c->ev_free.empty()) {
@@ -512,13 +591,16 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   }
   *c->err_host = 0;
   if (cudaMalloc(&c->tile_ptr, sizeof(int) * (c->ntiles + 1)) != cudaSuccess ||
-      cudaMalloc(&c->info, sizeof(ShotInfo)) != cudaSuccess ||
+      cudaMalloc(&c->info, 2 * sizeof(ShotInfo)) != cudaSuccess ||
       cudaMalloc(&c->wav, sizeof(float) * g->nt) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     rbc_destroy(c);
     return fail(RBC_ENOMEM, "context allocation failed");
   }
-  if (cudaMemset(c->buf, 0, 7 * fb) != cudaSuccess) {
+  ShotInfo silent{};
+  silent.src_off = -1;  // no node: the kernels' point test never matches
+  if (cudaMemset(c->buf, 0, 7 * fb) != cudaSuccess ||
+      cudaMemcpy(c->info + 1, &silent, sizeof silent, cudaMemcpyHostToDevice) != cudaSuccess) {
     rbc_destroy(c);
     return fail(RBC_ECUDA, "memset failed");
   }
@@ -608,6 +690,71 @@ int rbc_rtm_shot(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int 
   g_launches += 2;
   CKL();
   c->have_panels = 0;  // the reverse pass consumed the panels
+  return RBC_OK;
+}
+
+int rbc_nyquist_stride(double dt, double f_max, double f_min) {
+  if (!(dt > 0) || !(f_min >= 0) || !(f_max > f_min)) {
+    fail(RBC_EINVAL, "need dt > 0 and 0 <= f_min < f_max");
+    return 0;
+  }
+  const double dt_nyq = 1.0 / (2.0 * (f_max - f_min));  // Eq. 7
+  const double k = std::floor(dt_nyq / dt + 1e-9);
+  return k < 1.0 ? 1 : (int)std::min(k, 1e9);
+}
+
+long long rbc_storage_bytes(const rbc_grid *g, int stride) {
+  if (check_grid(g)) return -1;
+  if (stride < 1) {
+    fail(RBC_EINVAL, "stride must be >= 1");
+    return -1;
+  }
+  const long long nint = (long long)g->nx * (g->ndim == 3 ? g->ny : 1) * g->nz;
+  return (long long)sizeof(float) * nint * (g->nt / stride + 1);
+}
+
+int rbc_rtm_storage(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nrec, const int *rec_host,
+                    const float *seis_dev, int stride, float *store_dev, long long store_bytes, int flags,
+                    float *num_dev, float *den_dev, void *stream) {
+  if (!c) return fail(RBC_EINVAL, "ctx is NULL");
+  if (!wavelet_dev || !num_dev || !den_dev || !store_dev || (nrec > 0 && !seis_dev))
+    return fail(RBC_EINVAL, "NULL device pointer");
+  if (flags & ~RBC_ZERO_FIRST) return fail(RBC_EINVAL, "unknown flags 0x%x", flags);
+  if (stride < 1) return fail(RBC_EINVAL, "stride must be >= 1 (got %d)", stride);
+  const long long need = rbc_storage_bytes(&c->g, stride);
+  if (store_bytes < need)
+    return fail(RBC_EINVAL, "store of %lld bytes is smaller than the %lld the stride needs", store_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  rc = upload_shot(c, src_host, nrec, rec_host, 0, s);
+  if (rc) return rc;
+  if (c->store != store_dev || c->stride != stride) {  // the storage graphs bake both in
+    for (int k = 4; k < 6; ++k) {
+      if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+      c->gexec[k] = nullptr;
+    }
+    c->store = store_dev;
+    c->stride = stride;
+  }
+  CK(cudaMemcpyAsync(c->wav, wavelet_dev, sizeof(float) * c->g.nt, cudaMemcpyDeviceToDevice, s));
+  if (nrec > 0) {
+    launch_transpose(seis_dev, c->seis_t, nrec, c->g.nt + 1, s);
+    ++g_launches;
+  }
+  if (c->timing && (rc = record_event(c, s))) return rc;
+  rc = run_loop(c, 4, enq_store_fwd, s);
+  if (rc) return rc;
+  if (c->timing && (rc = record_event(c, s))) return rc;
+  rc = run_loop(c, 5, enq_store_rev, s);
+  if (rc) return rc;
+  if (c->timing && (rc = record_event(c, s))) return rc;
+  const int ow = (flags & RBC_ZERO_FIRST) ? 1 : 0;
+  launch_accum_interior(c->L, c->num, num_dev, c->g.nb, c->g.nx, c->g.ny, c->g.nz, ow, s);
+  launch_accum_interior(c->L, c->den, den_dev, c->g.nb, c->g.nx, c->g.ny, c->g.nz, ow, s);
+  g_launches += 2;
+  CKL();
+  c->have_panels = 1;  // the forward loop leaves p^{nt-1}, p^{nt} in place
   return RBC_OK;
 }
 

@@ -130,6 +130,12 @@ void launch_fwi_adjoint_source(const float *resid, float *seis_t, int nrec, int 
                                cudaStream_t s);
 void launch_fwi_finalize(const Lay &L, const float *num, const float *a, float *grad, int nb, int nx,
                          int nz, double dt, double h, cudaStream_t s);
+// RTM with wavefield storage (Algorithm 2, Eq. 7 stride)
+void launch_store_level(const Lay &L, const float *p, float *slot, int nb, int nx, int ny, int nz, cudaStream_t s);
+void launch_store_image(const Lay &L, const float *slot, const float *pb, float *num, float *den, int nb, int nx,
+                        int ny, int nz, cudaStream_t s);
+void launch_rec_inject(const float *a, float *bn, const int *rec_off, const ShotInfo *info, const float *seis_t,
+                       int n, int nrec_cap, cudaStream_t s);
 void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_int, double v_lo,
                       double v_hi, double v_max, uint64_t seed, int mode, double dt, double h,
                       float *v_pad, float *a, cudaStream_t s);

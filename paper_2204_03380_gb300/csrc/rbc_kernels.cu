@@ -424,4 +424,71 @@ void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_i
                                                mode, dt, h, v_pad, a);
 }
 
+// -------------------------------------- RTM with wavefield storage ----
+// Algorithm 2 keeps the source wavefield every k steps (Eq. 7); the kept
+// level is the interior box as a dense [nz][ny][nx] slot.  Threads run along
+// x of one interior row (coalesced on both sides), blocks stride over rows.
+__global__ void k_store_level(const Lay L, const float *__restrict__ p, float *__restrict__ slot, int nb, int nx,
+                              int ny, int nz) {
+  griddep_wait();
+  const int yo = (L.ndim == 3) ? nb : 0;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < nx)
+    for (int r = blockIdx.y; r < ny * nz; r += gridDim.y) {
+      const int y = r % ny, z = r / ny;
+      slot[(long long)r * nx + x] = p[lay_off(L, x + nb, y + yo, z + nb)];
+    }
+  griddep_launch();
+}
+
+// Eq. 3 integrals at a kept level n: num += p^n pbar_n, den += (p^n)^2, with
+// p^n read back from its slot (num/den in the pitched layout).
+__global__ void k_store_image(const Lay L, const float *__restrict__ slot, const float *__restrict__ pb,
+                              float *__restrict__ num, float *__restrict__ den, int nb, int nx, int ny, int nz) {
+  griddep_wait();
+  const int yo = (L.ndim == 3) ? nb : 0;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < nx)
+    for (int r = blockIdx.y; r < ny * nz; r += gridDim.y) {
+      const int y = r % ny, z = r / ny;
+      const int o = lay_off(L, x + nb, y + yo, z + nb);
+      const float v = slot[(long long)r * nx + x];
+      num[o] += v * pb[o];
+      den[o] += v * v;
+    }
+  griddep_launch();
+}
+
+// Eq. 2 source term after a receiver-wavefield step: pbar_{n-1} at the
+// receivers += a_r s[r][n] h^(2-d) (atomics: receivers may share a node).
+__global__ void k_rec_inject(const float *__restrict__ a, float *__restrict__ bn, const int *__restrict__ rec_off,
+                             const ShotInfo *info, const float *__restrict__ seis_t, int n) {
+  griddep_wait();
+  const int nrec = info->nrec;
+  const float sc = info->rec_scale;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
+    const int o = rec_off[r];
+    atomicAdd(bn + o, sc * a[o] * seis_t[(long long)n * nrec + r]);
+  }
+  griddep_launch();
+}
+
+static dim3 interior_grid(int nx, int rows) {
+  return dim3(cdiv(nx, 128), (unsigned)min(rows, 4 * 152 * 16 / max(1, cdiv(nx, 128))));
+}
+
+void launch_store_level(const Lay &L, const float *p, float *slot, int nb, int nx, int ny, int nz, cudaStream_t s) {
+  launch_pdl(k_store_level, interior_grid(nx, ny * nz), dim3(128), 0, s, L, p, slot, nb, nx, ny, nz);
+}
+
+void launch_store_image(const Lay &L, const float *slot, const float *pb, float *num, float *den, int nb, int nx,
+                        int ny, int nz, cudaStream_t s) {
+  launch_pdl(k_store_image, interior_grid(nx, ny * nz), dim3(128), 0, s, L, slot, pb, num, den, nb, nx, ny, nz);
+}
+
+void launch_rec_inject(const float *a, float *bn, const int *rec_off, const ShotInfo *info, const float *seis_t,
+                       int n, int nrec_cap, cudaStream_t s) {
+  launch_pdl(k_rec_inject, dim3(cdiv(max(nrec_cap, 1), 256)), dim3(256), 0, s, a, bn, rec_off, info, seis_t, n);
+}
+
 } // namespace rbc

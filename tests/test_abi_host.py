@@ -64,3 +64,24 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert lib.rbc_image_stack(C.byref(shot), p, p, 1e-6, 0, 0, C.byref(other), p, None) == 1
     assert lib.rbc_model(None, None, None, 0, None, None, None) == 1
     assert lib.rbc_set_snapshots(None, 0, None, None, None, None) == 1
+
+
+def test_nyquist_stride_and_storage_size_on_the_host():
+    # host-only entry points: Eq. 7 against the oracle's independent version
+    # and the paper's 5 ms step, and the store size formula
+    import json
+    import oracle
+    import paper_2204_03380_gb300 as R
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    n = g["nyquist_step_2d"]
+    assert R.rbc_nyquist_stride(n["dt"], n["f_max"], n["f_min"]) == n["stride"]
+    for dt, fmax, fmin in [(0.001, 37.5, 0.0), (0.0004, 62.5, 0.0), (0.001, 40.0, 10.0), (0.004, 1000.0, 0.0)]:
+        assert R.rbc_nyquist_stride(dt, fmax, fmin) == oracle.nyquist_stride(dt, fmax, fmin)
+    with pytest.raises(R.RBCError):
+        R.rbc_nyquist_stride(0.001, 10.0, 20.0)
+    grid = R.make_grid(3, 10, 7, 5, 4, 10.0, 1e-3, 23)
+    assert R.rbc_storage_bytes(grid, 4) == 4 * 10 * 7 * 5 * (23 // 4 + 1)
+    grid = R.make_grid(2, 10, 1, 5, 4, 10.0, 1e-3, 24)
+    assert R.rbc_storage_bytes(grid, 4) == 4 * 10 * 5 * 7
+    with pytest.raises(R.RBCError):
+        R.rbc_storage_bytes(grid, 0)
