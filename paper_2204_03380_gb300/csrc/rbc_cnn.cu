@@ -5,17 +5,21 @@
 // boundary realizations of an RTM image (Section 4.3's noise is incoherent
 // between realizations).
 //
-// Activations are NHWC bf16 ([image][row][col][channel]); weights are stored
+// The 32-channel activations are bf16 and channel-group planar:
+// [image][channel / 8][row][col][channel % 8] (16 bytes per pixel and group,
+// so a row of one group is contiguous for the TMA copies and the tensor-core
+// operands); one-channel images are [image][row][col].  Weights are stored
 // [tap][out][in] (tap = 3 * dy + dx, dy, dx in 0..2 for offsets -1..1).
-// Convolutions run as implicit GEMMs on the tensor cores (mma.sync
-// m16n8k16, bf16 in, fp32 accumulate): a block computes an 8 x 32 pixel tile
-// for all output channels, one warp per tile row (two 16-pixel m tiles),
-// with the input halo tile and the weights staged in shared memory.  The
-// backward pass of the input is the same kernel with the taps mirrored and
-// the channel roles swapped, its epilogue applying the ReLU mask of the
-// layer below.  Weight gradients are per-tap GEMMs over the pixels, also on
-// the tensor cores, reduced by persistent blocks and added to the fp32
-// gradient once per block.
+// The 32 -> 32 convolutions (three hidden layers, and their backward-data
+// passes: the same kernel with the taps mirrored and the channel roles
+// swapped, its epilogue applying the ReLU mask of the layer below) run as
+// implicit GEMMs on the 5th-generation tensor cores (tcgen05.mma, operands
+// in shared memory, fp32 accumulators in tensor memory).  The one-channel
+// first and last layers run on the CUDA cores.  Weight gradients are per-tap
+// GEMMs over the pixels on the warp-level tensor cores (mma.sync m16n8k16),
+// reduced by persistent blocks and added to the fp32 gradient once per block.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -50,146 +54,394 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
 
 enum { kHidden = 0, kLast = 1, kBackData = 2 };
 
-// Implicit-GEMM 3x3 convolution with zero padding.
-//   CIN in {1, 32}, COUT in {1, 32}.  in: NHWC bf16 with CIN channels.
-//   wt: bf16 weights [9][COUT][CIN] (already mirrored / transposed for the
-//   backward-data pass).
-//   MODE kHidden:   out_bf = relu(conv + bias)                (bf16, COUT ch)
-//   MODE kLast:     out_f  = resid + conv + bias              (fp32, COUT = 1)
-//   MODE kBackData: out_bf = conv * (mask > 0)                (bf16, COUT ch)
-template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wt,
-                                                 const float *__restrict__ bias, const float *__restrict__ resid,
-                                                 const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ out_bf,
-                                                 float *__restrict__ out_f, int H, int W) {
-  constexpr int CP = (CIN == 32) ? 40 : 2;      // padded channel stride in shared memory (bank spread)
-  constexpr int NT = (COUT == 32) ? 4 : 1;      // n tiles of 8 output channels
-  constexpr int NW = NT * 8;                    // padded output channels
-  constexpr int KP = (CIN == 32) ? 40 : 16;     // padded K per tap (CIN = 1: K is the 9 taps, padded to 16)
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16 *s_in = reinterpret_cast<__nv_bfloat16 *>(smem_raw);                  // [(TH+2)(TW+2)][CP]
-  __nv_bfloat16 *s_w = s_in + (TH + 2) * (TW + 2) * CP;                                // [taps][NW][KP]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, tig = lane & 3;
-  const int img = blockIdx.z;
-  const int y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
+// The one-channel ends of the network carry 32x fewer flops than the hidden
+// layers and are bound by their 64-byte-per-pixel activations, so they run on
+// the CUDA cores: one thread per pixel of an 8 x 32 tile, the halo and the
+// fp32 weights in shared memory.
+// 1 -> 32 channels (first layer forward; last layer's backward-data pass):
+//   wt [tap][32] (bf16);  MODE kHidden: relu(conv + bias);  kBackData: conv * (mask > 0)
+template <int MODE>
+__global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restrict__ in,
+                                                    const __nv_bfloat16 *__restrict__ wt,
+                                                    const float *__restrict__ bias,
+                                                    const __nv_bfloat16 *__restrict__ mask,
+                                                    __nv_bfloat16 *__restrict__ out, int H, int W) {
+  __shared__ float s_w[9 * 32];
+  __shared__ float s_b[32];
+  __shared__ float s_in[(TH + 2) * (TW + 2)];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int img = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
   const long long ibase = (long long)img * H * W;
-  // weights -> shared (zero padding for the n / k tails)
-  if (CIN == 32) {
-    for (int i = threadIdx.x; i < 9 * NW * KP; i += blockDim.x) {
-      const int k = i % KP, n = (i / KP) % NW, t = i / (KP * NW);
-      s_w[i] = (k < CIN && n < COUT) ? wt[(t * COUT + n) * CIN + k] : __float2bfloat16(0.f);
-    }
-  } else {
-    for (int i = threadIdx.x; i < NW * KP; i += blockDim.x) {
-      const int k = i % KP, n = i / KP;  // k = tap
-      s_w[i] = (k < 9 && n < COUT) ? wt[k * COUT + n] : __float2bfloat16(0.f);
-    }
-  }
-  // input halo tile -> shared (zero outside the image)
-  for (int i = threadIdx.x; i < (TH + 2) * (TW + 2) * CIN; i += blockDim.x) {
-    const int c = i % CIN, px = (i / CIN) % (TW + 2), py = i / (CIN * (TW + 2));
-    const int yy = y0 + py - 1, xx = x0 + px - 1;
-    s_in[(py * (TW + 2) + px) * CP + c] =
-        (yy >= 0 && yy < H && xx >= 0 && xx < W) ? in[(ibase + (long long)yy * W + xx) * CIN + c] : __float2bfloat16(0.f);
+  for (int i = tid; i < 9 * 32; i += 256) s_w[i] = __bfloat162float(wt[i]);
+  if (MODE == kHidden && tid < 32) s_b[tid] = bias[tid];
+  for (int i = tid; i < (TH + 2) * (TW + 2); i += 256) {
+    const int yy = y0 + i / (TW + 2) - 1, xx = x0 + i % (TW + 2) - 1;
+    s_in[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __bfloat162float(in[ibase + (long long)yy * W + xx]) : 0.f;
   }
   __syncthreads();
-  float acc[2][NT][4];
+  const int yy = y0 + ty, xx = x0 + tx;
+  if (yy >= H || xx >= W) return;
+  float acc[32];
 #pragma unroll
-  for (int m = 0; m < 2; ++m)
+  for (int c = 0; c < 32; ++c) acc[c] = 0.f;
 #pragma unroll
-    for (int n = 0; n < NT; ++n)
+  for (int t = 0; t < 9; ++t) {
+    const float v = s_in[(ty + t / 3) * (TW + 2) + tx + t % 3];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[m][n][r] = 0.f;
-  if (CIN == 32) {
-#pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-      const int dy = t / 3, dx = t % 3;
+    for (int c = 0; c < 32; ++c) acc[c] = fmaf(v, s_w[t * 32 + c], acc[c]);
+  }
+  const long long HWp = (long long)H * W, pix = (long long)yy * W + xx;
+  if (MODE == kHidden) {
 #pragma unroll
-      for (int kk = 0; kk < 32; kk += 16) {
-        uint32_t b[NT][2];
+    for (int c = 0; c < 32; ++c) acc[c] = fmaxf(acc[c] + s_b[c], 0.f);
+  } else {
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-          const __nv_bfloat16 *wp = s_w + (t * NW + n * 8 + g) * KP + kk + tig * 2;
-          b[n][0] = *reinterpret_cast<const uint32_t *>(wp);
-          b[n][1] = *reinterpret_cast<const uint32_t *>(wp + 8);
+    for (int q = 0; q < 4; ++q) {
+      const uint4 m4 = reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp + pix];
+      const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 mf = __bfloat1622float2(m2[e]);
+        if (!(mf.x > 0.f)) acc[q * 8 + 2 * e] = 0.f;
+        if (!(mf.y > 0.f)) acc[q * 8 + 2 * e + 1] = 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 pk;
+    __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(acc[q * 8 + 2 * e], acc[q * 8 + 2 * e + 1]);
+    reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
+  }
+}
+
+// 32 -> 1 channel, the last layer: y = x + conv(in) + bias (fp32 out).
+//   wt [tap][32] (bf16, the single output channel's weights)
+__global__ void __launch_bounds__(256) k_conv_32to1(const __nv_bfloat16 *__restrict__ in,
+                                                    const __nv_bfloat16 *__restrict__ wt,
+                                                    const float *__restrict__ bias,
+                                                    const float *__restrict__ resid, float *__restrict__ out,
+                                                    int H, int W) {
+  __shared__ float s_w[9 * 32];
+  __shared__ __align__(16) __nv_bfloat16 s_h[(TH + 2) * (TW + 2) * 32];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int img = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
+  const long long ibase = (long long)img * H * W, HWp = (long long)H * W;
+  for (int i = tid; i < 9 * 32; i += 256) s_w[i] = __bfloat162float(wt[i]);
+  // halo as four channel-group planes [group][pixel] of 16-byte chunks
+  constexpr int HP = (TH + 2) * (TW + 2);
+  for (int i = tid; i < HP * 4; i += 256) {
+    const int q = i / HP, hp = i % HP;
+    const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+      v = reinterpret_cast<const uint4 *>(in)[((long long)img * 4 + q) * HWp + (long long)yy * W + xx];
+    reinterpret_cast<uint4 *>(s_h)[i] = v;
+  }
+  __syncthreads();
+  const int yy = y0 + ty, xx = x0 + tx;
+  if (yy >= H || xx >= W) return;
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int hp = (ty + t / 3) * (TW + 2) + tx + t % 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 v4 = reinterpret_cast<const uint4 *>(s_h)[q * HP + hp];
+      const __nv_bfloat162 *v2 = reinterpret_cast<const __nv_bfloat162 *>(&v4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(v2[e]);
+        acc = fmaf(f.x, s_w[t * 32 + q * 8 + 2 * e], acc);
+        acc = fmaf(f.y, s_w[t * 32 + q * 8 + 2 * e + 1], acc);
+      }
+    }
+  }
+  const long long p = ibase + (long long)yy * W + xx;
+  out[p] = resid[p] + acc + bias[0];
+}
+
+// ---------------------------------------------------------------------------
+// 32 -> 32 channel layers on the 5th-generation tensor cores (tcgen05).
+//
+// A tile is kTcRows output rows x 128 columns of one image.  The accumulator
+// of output row rr is a 128 (pixels) x 32 (channels) fp32 matrix in tensor
+// memory, built by 18 MMAs of M = 128, N = 32, K = 16: for each tap (dy, dx)
+// and each half of the 32 input channels
+//   D[px][co] += sum_ci halo[row + dy][px + dx][ci] * w[tap][co][ci].
+// Both operands sit in shared memory in the no-swizzle K-major layout: a
+// "core matrix" is 8 rows of 16 bytes (8 channels) stored contiguously.  The
+// activations are kept channel-group planar in memory ([image][group of 8
+// channels][row][column][8]), so one 5-D TMA copy lands a tile's halo as four
+// planes (one per channel group) of halo pixels in row-major order at 16
+// bytes each: 8 consecutive pixels of any halo row are one core matrix, and
+// the operand of a shifted tap is the same planes with the start address
+// moved by (dy * 130 + dx) * 16 bytes (stride between 8-pixel groups 128
+// bytes, between channel groups one plane).  Weights: [tap][group][co][8].
+//
+// Per block (one per SM, persistent over tiles), three roles: warp 4 streams
+// each tile's halo (zero-filled outside the image) into a 4-stage shared-
+// memory ring; warp 5 issues the 72 MMAs of a tile into one of two
+// tensor-memory accumulators and commits them to the ring's "empty" and the
+// accumulator's "full" barrier; warps 0-3 (tensor-memory lanes 0-127, one
+// pixel each) drain the other accumulator with tcgen05.ld, apply the epilogue
+// (the backward-data pass reads its ReLU mask from global memory, issued
+// before the accumulator wait) and store.  Copies of tiles k+1 .. k+3, MMAs
+// of tile k and the epilogue of tile k-1 overlap.  Every wait is bounded; a
+// block that gives up flags the error word and stops.
+constexpr int kTcRows = 4;                                   // output rows per tile
+constexpr int kTcW = 128;                                    // output columns per tile (M)
+constexpr int kTcHW = kTcW + 2;                              // halo row width (pixels)
+constexpr int kTcPlane = (kTcRows + 2) * kTcHW * 16;         // 12480 B per channel-group plane
+constexpr int kTcStage = 4 * kTcPlane;                       // halo stage (one TMA box)
+constexpr int kTcStages = 4;                                 // halo ring depth
+constexpr int kTcWBytes = 9 * 4 * 32 * 16;                   // weights, 18432 B
+constexpr long long kTcWaitCycles = 4000000000LL;            // about two seconds
+constexpr int kTcSmem = kTcWBytes + kTcStages * kTcStage + 256;
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // no swizzle; start, leading (K) and stride (M/N) byte offsets in 16-byte
+  // units; bits 46-47 = 1 (descriptor version of this architecture)
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: fp32 accumulator, bf16 A and B, both
+// K-major, N = 32, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tc_mbar_init(uint32_t b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tc_arrive(uint32_t b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ bool tc_try(uint32_t b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(b), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait that gives up when another role of the block has flagged an
+// abort, and flags one itself when its time runs out.
+__device__ __forceinline__ bool tc_wait(uint32_t b, uint32_t parity, volatile int *abort_blk) {
+  if (tc_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!tc_try(b, parity)) {
+    if (*abort_blk) return false;
+    if (clock64() - t0 > kTcWaitCycles) {
+      *abort_blk = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tc_tma5(uint32_t dst, const CUtensorMap *tm, int c1, int c2, int c4, uint32_t bar) {
+  // coordinates (channel 0, x, y, group 0, image)
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(c1), "r"(c2), "r"(0), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+//   MODE kHidden:   out = relu(conv(in) + bias)
+//   MODE kBackData: out = conv(in) * (mask > 0)   (weights mirrored and transposed)
+template <int MODE>
+__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
+                                                    const __nv_bfloat16 *__restrict__ wt,
+                                                    const float *__restrict__ bias,
+                                                    const __nv_bfloat16 *__restrict__ mask,
+                                                    __nv_bfloat16 *__restrict__ out, int nimg, int H, int W, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t s_w = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t s_h = s_w + kTcWBytes;  // halo ring
+  unsigned char *tail = smem + kTcWBytes + kTcStages * kTcStage;
+  float *s_bias = reinterpret_cast<float *>(tail);
+  // barriers: full[kTcStages], empty[kTcStages], tfull[2], tempty[2]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(tail + 128);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kTcStages + 4);
+  volatile int *abort_blk = reinterpret_cast<volatile int *>(tslot + 1);
+  const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(bars);
+  auto full = [&](int i) { return b0 + 8u * i; };
+  auto empty = [&](int i) { return b0 + 8u * (kTcStages + i); };
+  auto tfull = [&](int i) { return b0 + 8u * (2 * kTcStages + i); };
+  auto tempty = [&](int i) { return b0 + 8u * (2 * kTcStages + 2 + i); };
+  // weights [tap][co][ci] -> [tap][ci / 8][co][8]
+  for (int i = tid; i < 9 * 32 * 4; i += blockDim.x) {
+    const int j = i & 3, co = (i >> 2) & 31, t = i >> 7;
+    cp_async16(s_w + t * 2048 + j * 512 + co * 16, wt + (t * 32 + co) * 32 + j * 8, true);
+  }
+  if (MODE == kHidden && tid < 32) s_bias[tid] = bias[tid];
+  if (tid == 0) {
+    *abort_blk = 0;
+    for (int i = 0; i < kTcStages; ++i) {
+      tc_mbar_init(full(i), 1);
+      tc_mbar_init(empty(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc_mbar_init(tfull(i), 1);
+      tc_mbar_init(tempty(i), 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        (uint32_t)__cvta_generic_to_shared(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int ntx = (W + kTcW - 1) / kTcW, nty = (H + kTcRows - 1) / kTcRows;
+  const long long ntiles = (long long)ntx * nty * nimg;
+  auto tile_xy = [&](long long t, int &img, int &y0, int &x0) {
+    img = (int)(t / ((long long)ntx * nty));
+    const int rem = (int)(t % ((long long)ntx * nty));
+    y0 = (rem / ntx) * kTcRows;
+    x0 = (rem % ntx) * kTcW;
+  };
+  if (warp == 4) {
+    // ---- producer: one TMA copy of the halo per tile ----
+    if (lane == 0) {
+      int issued = 0;
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
+        const int s = issued % kTcStages, u = issued / kTcStages;
+        if (u > 0 && !tc_wait(empty(s), (u - 1) & 1, abort_blk)) break;
+        int img, y0, x0;
+        tile_xy(t, img, y0, x0);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTcStage) : "memory");
+        tc_tma5(s_h + s * kTcStage, &tm_in, x0 - 1, y0 - 1, img, full(s));
+      }
+      if (*abort_blk) {  // let the copies in flight land before the block exits
+        for (int k = (issued > kTcStages ? issued - kTcStages : 0); k < issued; ++k) {
+          const long long t0 = clock64();
+          while (!tc_try(full(k % kTcStages), (k / kTcStages) & 1) && clock64() - t0 < kTcWaitCycles) {
+          }
         }
+      }
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int k = 0;
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k % kTcStages, u = k / kTcStages, b = k & 1, ub = k >> 1;
+        if (!tc_wait(full(s), u & 1, abort_blk)) break;
+        if (ub > 0 && !tc_wait(tempty(b), (ub - 1) & 1, abort_blk)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // descriptors differ only in their start-address field: one add per MMA
+        // (fully unrolled, the offsets are constants; a single thread issues
+        // all 72, so per-MMA arithmetic would bound the tile)
+        const uint64_t a0 = umma_desc(s_h + s * kTcStage, kTcPlane, 128), b0d = umma_desc(s_w, 512, 128);
+        const uint32_t d0 = tmem + b * 128;
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          const int px = m * 16 + g + dx;
-          const __nv_bfloat16 *r0 = s_in + ((warp + dy) * (TW + 2) + px) * CP + kk + tig * 2;
-          const __nv_bfloat16 *r1 = r0 + 8 * CP;
-          uint32_t a[4];
-          a[0] = *reinterpret_cast<const uint32_t *>(r0);
-          a[1] = *reinterpret_cast<const uint32_t *>(r1);
-          a[2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-          a[3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+        for (int rr = 0; rr < kTcRows; ++rr)
 #pragma unroll
-          for (int n = 0; n < NT; ++n) mma16816(acc[m][n], a, b[n]);
-        }
+          for (int tp = 0; tp < 9; ++tp)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint64_t ad = a0 + (uint64_t)((2 * ks * kTcPlane + ((rr + tp / 3) * kTcHW + tp % 3) * 16) >> 4);
+              const uint64_t bd = b0d + (uint64_t)((tp * 2048 + 2 * ks * 512) >> 4);
+              asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d0 + rr * 32), "l"(ad),
+                           "l"(bd), "r"(kTcIdesc), "r"((tp | ks) ? 1u : 0u));
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty(s))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tfull(b))
+                     : "memory");
       }
     }
   } else {
-    // CIN = 1: the K dimension is the tap index (9, padded to 16)
-    uint32_t b[NT][2];
+    // ---- epilogue: warps 0-3, one accumulator row (pixel) per thread ----
+    const long long HWp = (long long)H * W;
+    int k = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int b = k & 1, ub = k >> 1;
+      int img, y0, x0;
+      tile_xy(t, img, y0, x0);
+      const int px = warp * 32 + lane, xx = x0 + px;
+      uint4 mk[kTcRows][4];  // backward-data: this pixel's masks, loaded while the MMAs run
+      if (MODE == kBackData) {
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      const __nv_bfloat16 *wp = s_w + (n * 8 + g) * KP + tig * 2;
-      b[n][0] = *reinterpret_cast<const uint32_t *>(wp);
-      b[n][1] = *reinterpret_cast<const uint32_t *>(wp + 8);
-    }
-    auto tapv = [&](int px, int k) -> __nv_bfloat16 {
-      if (k >= 9) return __float2bfloat16(0.f);
-      return s_in[((warp + k / 3) * (TW + 2) + px + k % 3) * CP];
-    };
+        for (int rr = 0; rr < kTcRows; ++rr)
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int px = m * 16 + g;
-      const int k0 = tig * 2;
-      uint32_t a[4];
-      a[0] = pack2(tapv(px, k0), tapv(px, k0 + 1));
-      a[1] = pack2(tapv(px + 8, k0), tapv(px + 8, k0 + 1));
-      a[2] = pack2(tapv(px, k0 + 8), tapv(px, k0 + 9));
-      a[3] = pack2(tapv(px + 8, k0 + 8), tapv(px + 8, k0 + 9));
-#pragma unroll
-      for (int n = 0; n < NT; ++n) mma16816(acc[m][n], a, b[n]);
-    }
-  }
-  // epilogue: C fragment rows g / g + 8 (pixels), columns tig*2, +1 (channels)
-  const int yy = y0 + warp;
-  if (yy >= H) return;
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int xx = x0 + m * 16 + g + half * 8;
-      if (xx >= W) continue;
-      const long long p = ibase + (long long)yy * W + xx;
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const int co = n * 8 + tig * 2;
-        float v0 = acc[m][n][half * 2], v1 = acc[m][n][half * 2 + 1];
-        if (MODE == kLast) {
-          if (co == 0) out_f[p] = resid[p] + v0 + bias[0];
-        } else if (co < COUT) {
+          for (int q = 0; q < 4; ++q)
+            mk[rr][q] = (y0 + rr < H && xx < W)
+                            ? reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp +
+                                                                   (long long)(y0 + rr) * W + xx]
+                            : make_uint4(0u, 0u, 0u, 0u);
+      }
+      const bool ok = tc_wait(tfull(b), ub & 1, abort_blk);
+      if (__any_sync(0xffffffffu, !ok)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int rr = 0; rr < kTcRows; ++rr) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + b * 128 + rr * 32, v);
+        const int yy = y0 + rr;
+        if (yy < H && xx < W) {
+          const long long pix = (long long)yy * W + xx;
           if (MODE == kHidden) {
-            v0 = fmaxf(v0 + bias[co], 0.f);
-            v1 = fmaxf(v1 + bias[co + 1], 0.f);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + s_bias[c], 0.f);
           } else {
-            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + p * COUT + co);
-            v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
-            v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint4 m4 = mk[rr][q];
+              const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 mf = __bfloat1622float2(m2[e]);
+                v[q * 8 + 2 * e] = mf.x > 0.f ? v[q * 8 + 2 * e] : 0.f;
+                v[q * 8 + 2 * e + 1] = mf.y > 0.f ? v[q * 8 + 2 * e + 1] : 0.f;
+              }
+            }
           }
-          *reinterpret_cast<__nv_bfloat162 *>(out_bf + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint4 pk;
+            __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
+            reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
+          }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      tc_arrive(tempty(b));
     }
-}
-
-template <int CIN, int COUT>
-constexpr size_t conv_smem() {
-  return sizeof(__nv_bfloat16) * ((TH + 2) * (TW + 2) * ((CIN == 32) ? 40 : 2) +
-                                  (CIN == 32 ? 9 : 1) * ((COUT == 32) ? 32 : 8) * ((CIN == 32) ? 40 : 16));
+  }
+  __syncthreads();
+  if (tid == 0 && *abort_blk) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
 // Weight and bias gradients of one layer, on the tensor cores:
@@ -229,21 +481,44 @@ __global__ void __launch_bounds__(288) k_conv_wgrad(const __nv_bfloat16 *__restr
     const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
     const long long ibase = (long long)img * H * W;
     __syncthreads();
-    for (int i = threadIdx.x; i < HP * CN; i += blockDim.x) {
-      const int c = i % CN, hp = i / CN;
-      const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
-      s_x[c * HP + hp] = (c < CIN && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                             ? x[(ibase + (long long)yy * W + xx) * CIN + c] : zero;
-    }
-    for (int i = threadIdx.x; i < TH * TW * CM; i += blockDim.x) {
-      const int c = i % CM, q = i / CM;
-      const int yy = y0 + q / TW, xx = x0 + q % TW;
-      __nv_bfloat16 v = zero;
-      if (c < COUT && yy < H && xx < W) {
-        const long long p = ibase + (long long)yy * W + xx;
-        v = dzf ? __float2bfloat16(dzf[p]) : dz[p * COUT + c];
+    const long long HWp = (long long)H * W;
+    if (CIN == 32) {
+      // 16-byte chunks (8 channels of one pixel) of the channel-group planes
+      for (int i = threadIdx.x; i < HP * 4; i += blockDim.x) {
+        const int hp = i % HP, cg = i / HP;
+        const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+          v = reinterpret_cast<const uint4 *>(x)[((long long)img * 4 + cg) * HWp + (long long)yy * W + xx];
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s_x[(cg * 8 + k) * HP + hp] = e[k];
       }
-      s_dz[c * TH * TW + q] = v;
+    } else {
+      for (int i = threadIdx.x; i < HP * CN; i += blockDim.x) {
+        const int c = i / HP, hp = i % HP;
+        const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
+        s_x[c * HP + hp] = (c < CIN && yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[ibase + (long long)yy * W + xx] : zero;
+      }
+    }
+    if (COUT == 32) {
+      for (int i = threadIdx.x; i < TH * TW * 4; i += blockDim.x) {
+        const int q = i % (TH * TW), cg = i / (TH * TW);
+        const int yy = y0 + q / TW, xx = x0 + q % TW;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (yy < H && xx < W) v = reinterpret_cast<const uint4 *>(dz)[((long long)img * 4 + cg) * HWp + (long long)yy * W + xx];
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s_dz[(cg * 8 + k) * TH * TW + q] = e[k];
+      }
+    } else {
+      for (int i = threadIdx.x; i < TH * TW * CM; i += blockDim.x) {
+        const int c = i / (TH * TW), q = i % (TH * TW);
+        const int yy = y0 + q / TW, xx = x0 + q % TW;
+        __nv_bfloat16 v = zero;
+        if (c < COUT && yy < H && xx < W) v = __float2bfloat16(dzf[ibase + (long long)yy * W + xx]);
+        s_dz[c * TH * TW + q] = v;
+      }
     }
     __syncthreads();
     if (warp < 9) {
@@ -345,9 +620,8 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 void set_attrs() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_conv3x3<C, C, kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<C, C>());
-  cudaFuncSetAttribute(k_conv3x3<C, C, kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<C, C>());
-  cudaFuncSetAttribute(k_conv3x3<C, 1, kLast>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<C, 1>());
+  cudaFuncSetAttribute(k_conv_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   done = true;
 }
 
@@ -380,6 +654,54 @@ Ws carve(void *ws, long long npx) {
   return w;
 }
 
+// Error word of the tensor-core kernels' bounded waits (mapped host memory,
+// read at the next call).
+int *tc_err_host = nullptr, *tc_err_dev = nullptr;
+
+int tc_err() {
+  if (!tc_err_host) {
+    if (cudaHostAlloc((void **)&tc_err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&tc_err_dev, tc_err_host, 0) != cudaSuccess) {
+      tc_err_host = nullptr;
+      return rbc::set_error(RBC_ENOMEM, "error word allocation failed");
+    }
+    *tc_err_host = 0;
+  }
+  if (*(volatile int *)tc_err_host) {
+    *(volatile int *)tc_err_host = 0;
+    return rbc::set_error(RBC_ETIMEOUT, "a tensor-core convolution gave up waiting for its MMAs; results of the "
+                                        "calls since the last check are invalid");
+  }
+  return RBC_OK;
+}
+
+// 5-D tensor map over a channel-group planar bf16 activation buffer (32
+// channels): dims (channel in group, x, y, group, image); box (8, bx, by, 4, 1).
+bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, int bx, int by) {
+  auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(rbc::tmap_encode_fn());
+  if (!fn) return false;
+  cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)nimg};
+  cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)W * H * 64};
+  cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, 4, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(buf), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE>
+bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, const __nv_bfloat16 *mask,
+                    __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcRows - 1) / kTcRows) * nimg;
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  CUtensorMap tin;
+  if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcRows + 2)) return false;
+  k_conv_tc<MODE><<<grid, 192, kTcSmem, s>>>(tin, wt, bias, mask, out, nimg, H, W, tc_err_dev);
+  return true;
+}
+
 } // namespace
 
 extern "C" {
@@ -392,6 +714,7 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
                     void *stream) {
   if (!params_dev || !x_dev || !y_dev || !ws_dev || nimg < 1 || H < 1 || W < 1)
     return rbc::set_error(RBC_EINVAL, "rbc_cnn_forward: bad arguments");
+  if (int rc = tc_err()) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const long long npx = (long long)nimg * H * W;
   Ws w = carve(ws_dev, npx);
@@ -399,16 +722,13 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
   const dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, nimg);
-  k_conv3x3<1, C, kHidden><<<grid, 256, conv_smem<1, C>(), s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr, nullptr,
-                                                                w.act[0], nullptr, H, W);
-  k_conv3x3<C, C, kHidden><<<grid, 256, conv_smem<C, C>(), s>>>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, nullptr,
-                                                                w.act[1], nullptr, H, W);
-  k_conv3x3<C, C, kHidden><<<grid, 256, conv_smem<C, C>(), s>>>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, nullptr,
-                                                                w.act[2], nullptr, H, W);
-  k_conv3x3<C, C, kHidden><<<grid, 256, conv_smem<C, C>(), s>>>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, nullptr,
-                                                                w.act[3], nullptr, H, W);
-  k_conv3x3<C, 1, kLast><<<grid, 256, conv_smem<C, 1>(), s>>>(w.act[3], w.wf + kW5, params_dev + kB5, x_dev, nullptr,
-                                                              nullptr, y_dev, H, W);
+  k_conv_1to32<kHidden><<<grid, 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], H, W);
+  bool ok_tc = true;
+  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
+  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
+  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
+  k_conv_32to1<<<grid, 256, 0, s>>>(w.act[3], w.wf + kW5, params_dev + kB5, x_dev, y_dev, H, W);
+  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: tensor map encoding failed");
   rbc::add_launches(7);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
@@ -419,6 +739,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
                      void *stream) {
   if (!params_dev || !dy_dev || !grad_dev || !ws_dev || nimg < 1 || H < 1 || W < 1)
     return rbc::set_error(RBC_EINVAL, "rbc_cnn_backward: bad arguments");
+  if (int rc = tc_err()) return rc;
+  set_attrs();
   cudaStream_t s = (cudaStream_t)stream;
   const long long npx = (long long)nimg * H * W;
   Ws w = carve(ws_dev, npx);  // activations from the preceding rbc_cnn_forward
@@ -430,21 +752,21 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   k_conv_wgrad<C, 1><<<pg, 288, 0, s>>>(w.act[3], nullptr, dy_dev, grad_dev + kW5, grad_dev + kB5, nimg, H, W);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
-  k_conv3x3<1, C, kBackData><<<grid, 256, conv_smem<1, C>(), s>>>(w.dy1, w.wb + kW5, nullptr, nullptr, w.act[3], w.dz[0],
-                                                                  nullptr, H, W);
+  k_conv_1to32<kBackData><<<grid, 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3], w.dz[0], H, W);
   // layers 4, 3, 2: dW from dz; dz below = conv^T(dz) masked
   int cur = 0;
+  bool ok_tc = true;
   const int woff[3] = {kW4, kW3, kW2}, boff[3] = {kB4, kB3, kB2};
   for (int l = 0; l < 3; ++l) {
     const int layer_in = 2 - l;  // act index of this layer's input: act3 (l=0) ... act1
     k_conv_wgrad<C, C><<<pg, 288, 0, s>>>(w.act[layer_in], w.dz[cur], nullptr, grad_dev + woff[l], grad_dev + boff[l],
                                            nimg, H, W);
-    k_conv3x3<C, C, kBackData><<<grid, 256, conv_smem<C, C>(), s>>>(w.dz[cur], w.wb + woff[l], nullptr, nullptr,
-                                                                     w.act[layer_in], w.dz[1 - cur], nullptr, H, W);
+    ok_tc = ok_tc && launch_conv_tc<kBackData>(w.dz[cur], w.wb + woff[l], nullptr, w.act[layer_in], w.dz[1 - cur], nimg, H, W, s);
     cur = 1 - cur;
   }
   // layer 1
   k_conv_wgrad<1, C><<<pg, 288, 0, s>>>(w.x0, w.dz[cur], nullptr, grad_dev + kW1, grad_dev + kB1, nimg, H, W);
+  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_backward: tensor map encoding failed");
   rbc::add_launches(10);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));

@@ -537,6 +537,8 @@ int persistent_grid(const Lay &L, int zc, int ty, const void *fn, int threads, s
 
 } // namespace
 
+void *tmap_encode_fn() { return reinterpret_cast<void *>(encode_fn()); }
+
 int tile_rows_3d() { return kTY; }
 
 // The pitched buffers start at their allocation; tensor coordinates are the

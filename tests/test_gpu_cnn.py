@@ -16,7 +16,7 @@ def bf16(a):
     return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 37, 70)])
+@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 37, 70), (2, 45, 300)])
 def test_cnn_forward_and_gradient_match_oracle(shape):
     import paper_2204_03380_gb300 as R
     rng = np.random.default_rng(sum(shape))
