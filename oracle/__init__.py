@@ -52,10 +52,10 @@ def _L():
             lib.orc_model.argtypes = [i, i, i, i, P, d, i, P, P, i, P, P, P, P, i, P, P]
             lib.orc_model.restype = i
             lib.orc_rtm_shot.argtypes = [i, i, i, i, P, d, i, P, P, i, P, P, i, d,
-                                         i, i, i, i, P, P, i, P, P, P]
+                                         i, i, i, i, i, P, P, i, P, P, P]
             lib.orc_rtm_shot.restype = i
             lib.orc_rtm_storage.argtypes = [i, i, i, i, P, d, i, P, P, i, P, P, d, i,
-                                            i, i, i, i, P, P, P]
+                                            i, i, i, i, i, P, P, P]
             lib.orc_rtm_storage.restype = i
             lib.orc_nyquist_stride.argtypes = [d, d, d]
             lib.orc_nyquist_stride.restype = i
@@ -69,7 +69,7 @@ def _L():
             lib.orc_taper_g.restype = d
             lib.orc_taper_h.argtypes = [d, i]
             lib.orc_taper_h.restype = d
-            lib.orc_rbc_velocity.argtypes = [i, i, i, i, i, P, d, d, d, u64, i, P, P, P]
+            lib.orc_rbc_velocity.argtypes = [i, i, i, i, i, i, P, d, d, d, u64, i, P, P, P]
             lib.orc_rbc_velocity.restype = i
             lib.orc_coef.argtypes = [C.c_long, P, d, d, P, P]
             lib.orc_stencil_weights.argtypes = [P]
@@ -148,10 +148,11 @@ def model(a, h, nt, src, wavelet, rec, snaps=()):
 
 
 def rtm_shot(a, h, nt, src, wavelet, rec, seis, nb, interior, reinject=True,
-             rec_sign=REC_SIGN, snaps=()):
+             rec_sign=REC_SIGN, snaps=(), top=None):
     """Algorithm 3 (RTM with wavefield reconstruction) for one shot.
 
-    interior: (nx, ny, nz) box starting at padded node nb on every axis.
+    interior: (nx, ny, nz) box starting at padded node nb in x and y and at
+    row top in z (default nb; 4 with a free surface).
     Returns dict(num, den) on the interior (shape (nz, nx) or (nz, ny, nx)) and
     optional snapshots pr/pb of p^R_n and pbar_n on the padded grid.
     """
@@ -168,7 +169,7 @@ def rtm_shot(a, h, nt, src, wavelet, rec, seis, nb, interior, reinject=True,
     pbs = np.zeros((len(sn),) + a.shape)
     rc = _L().orc_rtm_shot(nd, NX, NY, NZ, _p(a), float(h), int(nt), _p(_i32(src)),
                            _p(_f64(wavelet)), rec.shape[0], _p(rec), _p(seis),
-                           int(bool(reinject)), float(rec_sign), int(nb), int(nx),
+                           int(bool(reinject)), float(rec_sign), int(nb), int(nb if top is None else top), int(nx),
                            int(ny if nd == 3 else 1), int(nz), _p(num), _p(den),
                            len(sn), _p(sn), _p(prs), _p(pbs))
     if rc:
@@ -182,7 +183,7 @@ def nyquist_stride(dt, f_max, f_min=0.0) -> int:
 
 
 def rtm_storage(a, h, nt, src, wavelet, rec, seis, nb, interior, stride, rec_sign=REC_SIGN,
-                keep_store=False):
+                keep_store=False, top=None):
     """Algorithm 2 (RTM with wavefield storage) for one shot: the source
     wavefield is stored at levels 0, k, 2k, ... (k = stride) and the imaging
     integrals of Eq. 3 are accumulated at those levels only.
@@ -200,7 +201,8 @@ def rtm_storage(a, h, nt, src, wavelet, rec, seis, nb, interior, stride, rec_sig
     store = np.zeros((nt // stride + 1,) + ishape) if keep_store else None
     rc = _L().orc_rtm_storage(nd, NX, NY, NZ, _p(a), float(h), int(nt), _p(_i32(src)),
                               _p(_f64(wavelet)), rec.shape[0], _p(rec), _p(seis), float(rec_sign),
-                              int(stride), int(nb), int(nx), int(ny if nd == 3 else 1), int(nz),
+                              int(stride), int(nb), int(nb if top is None else top), int(nx),
+                              int(ny if nd == 3 else 1), int(nz),
                               _p(num), _p(den), _p(store) if keep_store else None)
     if rc:
         raise ValueError("orc_rtm_storage: bad argument")
@@ -254,23 +256,26 @@ def taper_h(x, na):
     return _L().orc_taper_h(float(x), int(na))
 
 
-def rbc_velocity(v_int, nb, v_lo, v_hi, v_max, seed, mode=0, draws=False):
+def rbc_velocity(v_int, nb, v_lo, v_hi, v_max, seed, mode=0, draws=False, free_surface=False):
     """Random-boundary padding of an interior velocity (Section 4.3, Eqs. 4-5).
 
     v_int: (nz, nx) or (nz, ny, nx).  Returns the padded velocity (and, with
     draws=True, the per-cell coefficient c and random velocity, NaN inside).
+    free_surface: 4 zero-velocity rows on top instead of the random pad
+    (Section 5's pressure-release surface); the interior then starts at row 4.
     """
     v = _f64(v_int)
+    top = 4 if free_surface else nb
     if v.ndim == 2:
         nd, nz, ny, nx = 2, v.shape[0], 1, v.shape[1]
-        shp = (nz + 2 * nb, nx + 2 * nb)
+        shp = (nz + nb + top, nx + 2 * nb)
     else:
         nd, (nz, ny, nx) = 3, v.shape
-        shp = (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
+        shp = (nz + nb + top, ny + 2 * nb, nx + 2 * nb)
     out = np.zeros(shp)
     c = np.zeros(shp) if draws else None
     vr = np.zeros(shp) if draws else None
-    rc = _L().orc_rbc_velocity(nd, nx, ny, nz, int(nb), _p(v), float(v_lo), float(v_hi),
+    rc = _L().orc_rbc_velocity(nd, nx, ny, nz, int(nb), int(bool(free_surface)), _p(v), float(v_lo), float(v_hi),
                                float(v_max), C.c_uint64(seed), int(mode), _p(out), _p(c), _p(vr))
     if rc:
         raise ValueError("orc_rbc_velocity: bad argument")

@@ -202,21 +202,22 @@ int orc_model(int ndim, int NX, int NY, int NZ, const double *a, double h,
  *   Eq. 2:   pbar_{n-1} = 2 pbar_n - pbar_{n+1} + a L8 pbar_n
  *                        + rec_sign * sum_r a_r s[r][n] h^(2-d) delta_r
  *            with pbar_{N+1} = pbar_N = 0.
- * num, den: interior boxes [nz][ny][nx] starting at padded node (nb,nb,nb)
- * (y ignored in 2-D), accumulated (+=).  Snapshots (each may be NULL):
+ * num, den: interior boxes [nz][ny][nx] starting at padded node
+ * (x, y, z) = (nb, nb, top) (y ignored in 2-D; top = nb, or 4 with a free
+ * surface), accumulated (+=).  Snapshots (each may be NULL):
  * pr_snaps/pb_snaps [nsnap][N] = p^R_n, pbar_n for n = snap_n[k].
  */
 int orc_rtm_shot(int ndim, int NX, int NY, int NZ, const double *a, double h,
                  int nt, const int *src, const double *wavelet, int nrec,
                  const int *rec, const double *seis, int reinject,
-                 double rec_sign, int nb, int nx, int ny, int nz, double *num,
+                 double rec_sign, int nb, int top, int nx, int ny, int nz, double *num,
                  double *den, int nsnap, const int *snap_n, double *pr_snaps,
                  double *pb_snaps) {
   dims_t g = mkdims(ndim, NX, NY, NZ);
   long N = npts(&g);
   if (ndim == 2) ny = 1;
   long yoff = (ndim == 3) ? nb : 0;
-  if (nb + nx > NX || nb + nz > NZ || (ndim == 3 && nb + ny > NY)) return -1;
+  if (nb + nx > NX || top + nz > NZ || (ndim == 3 && nb + ny > NY)) return -1;
   if (!inside(&g, src)) return -1;
   for (int r = 0; r < nrec; ++r)
     if (!inside(&g, rec + 3 * r)) return -1;
@@ -243,7 +244,7 @@ int orc_rtm_shot(int ndim, int NX, int NY, int NZ, const double *a, double h,
       for (long z = 0; z < nz; ++z)
         for (long y = 0; y < ny; ++y)
           for (long x = 0; x < nx; ++x) {
-            long i = idx(&g, x + nb, y + yoff, z + nb);
+            long i = idx(&g, x + nb, y + yoff, z + top);
             long o = (z * ny + y) * nx + x;
             num[o] += pr_cur[i] * pb_cur[i];
             den[o] += pr_cur[i] * pr_cur[i];
@@ -296,7 +297,7 @@ int orc_nyquist_stride(double dt, double f_max, double f_min) {
  * from Eq. 7 in the paper's experiments).
  * Forward: Algorithm 1 (no recording); at every kept level the interior box
  *   of p^n is written to store[n / k] ([nz][ny][nx], the box at padded node
- *   (nb, nb, nb)).
+ *   (nb, nb, top)).
  * Reverse, n = N .. 0:
  *   image at kept levels only:  num += p^n pbar_n,  den += (p^n)^2  (Eq. 3
  *     integrals sampled every k steps);
@@ -309,14 +310,14 @@ int orc_nyquist_stride(double dt, double f_max, double f_min) {
 int orc_rtm_storage(int ndim, int NX, int NY, int NZ, const double *a, double h,
                     int nt, const int *src, const double *wavelet, int nrec,
                     const int *rec, const double *seis, double rec_sign,
-                    int stride, int nb, int nx, int ny, int nz, double *num,
+                    int stride, int nb, int top, int nx, int ny, int nz, double *num,
                     double *den, double *store) {
   dims_t g = mkdims(ndim, NX, NY, NZ);
   long N = npts(&g);
   if (ndim == 2) ny = 1;
   long yoff = (ndim == 3) ? nb : 0;
   if (stride < 1 || nt < 1) return -1;
-  if (nb + nx > NX || nb + nz > NZ || (ndim == 3 && nb + ny > NY)) return -1;
+  if (nb + nx > NX || top + nz > NZ || (ndim == 3 && nb + ny > NY)) return -1;
   if (!inside(&g, src)) return -1;
   for (int r = 0; r < nrec; ++r)
     if (!inside(&g, rec + 3 * r)) return -1;
@@ -338,7 +339,7 @@ int orc_rtm_storage(int ndim, int NX, int NY, int NZ, const double *a, double h,
         for (long z = 0; z < nz; ++z)
           for (long y = 0; y < ny; ++y)
             for (long x = 0; x < nx; ++x)
-              box[(z * ny + y) * nx + x] = pc[idx(&g, x + nb, y + yoff, z + nb)];
+              box[(z * ny + y) * nx + x] = pc[idx(&g, x + nb, y + yoff, z + top)];
       }
       if (n == nt) break;
       leapfrog(&g, a, pm, pc, pn);
@@ -359,7 +360,7 @@ int orc_rtm_storage(int ndim, int NX, int NY, int NZ, const double *a, double h,
             for (long x = 0; x < nx; ++x) {
               long o = (z * ny + y) * nx + x;
               double p = box[o];
-              num[o] += p * pc[idx(&g, x + nb, y + yoff, z + nb)];
+              num[o] += p * pc[idx(&g, x + nb, y + yoff, z + top)];
               den[o] += p * p;
             }
       }
@@ -457,30 +458,42 @@ static long pad_dist(long q, int nb, int n) {
 
 /*
  * Pad the interior velocity v_int [nz][ny][nx] with an nb-cell random
- * boundary on every side (Section 4.3).  For a pad cell with max-norm
- * distance i (1..nb) into the pad and linear index L in the padded grid:
+ * boundary on every side (Section 4.3) or, with free_surface, on every side
+ * but the top, which gets 4 rows (half the stencil length) of v = 0: there
+ * a = 0 and p stays 0, the pressure-release surface of Section 5.  The
+ * padded grid then has nz + nb + 4 rows and the interior starts at row 4.
+ * For a pad cell with max-norm distance i (1..nb) into the pad (measured
+ * from the sides and the bottom only when free_surface) and linear index L
+ * in the padded grid:
  *   c  = h_i + (g_i - h_i) U_{2L+1},   v_rand = v_lo + (v_hi - v_lo) U_{2L+2}
  *   mode 0: v = min(c v_edge + (1 - c) v_rand, v_max)
  *   mode 1: v = min(max(c v_rand, v_lo), v_max)
  * Optional outputs c_out, vr_out (NaN in the interior) expose the draws.
  */
-int orc_rbc_velocity(int ndim, int nx, int ny, int nz, int nb,
+int orc_rbc_velocity(int ndim, int nx, int ny, int nz, int nb, int free_surface,
                      const double *v_int, double v_lo, double v_hi,
                      double v_max, uint64_t seed, int mode, double *v_pad,
                      double *c_out, double *vr_out) {
   if (nb < 2 || nx < 1 || nz < 1 || (ndim == 3 && ny < 1)) return -1;
   if (ndim == 2) ny = 1;
-  long NX = nx + 2L * nb, NZ = nz + 2L * nb;
+  long top = free_surface ? 4 : nb;
+  long NX = nx + 2L * nb, NZ = nz + nb + top;
   long NY = (ndim == 3) ? ny + 2L * nb : 1;
   for (long z = 0; z < NZ; ++z)
     for (long y = 0; y < NY; ++y)
       for (long x = 0; x < NX; ++x) {
         long L = (z * NY + y) * NX + x;
-        long dx = pad_dist(x, nb, nx), dz = pad_dist(z, nb, nz);
+        if (free_surface && z < top) { /* the zero-pressure rows */
+          v_pad[L] = 0.0;
+          if (c_out) c_out[L] = NAN;
+          if (vr_out) vr_out[L] = NAN;
+          continue;
+        }
+        long dx = pad_dist(x, nb, nx), dz = pad_dist(z, (int)top, nz);
         long dy = (ndim == 3) ? pad_dist(y, nb, ny) : 0;
         long i = dx > dz ? dx : dz;
         i = dy > i ? dy : i;
-        long ex = clampl(x - nb, 0, nx - 1), ez = clampl(z - nb, 0, nz - 1);
+        long ex = clampl(x - nb, 0, nx - 1), ez = clampl(z - top, 0, nz - 1);
         long ey = (ndim == 3) ? clampl(y - nb, 0, ny - 1) : 0;
         double v_edge = v_int[(ez * ny + ey) * (long)nx + ex];
         if (i == 0) {
