@@ -55,11 +55,21 @@ enum {
 #define RBC_REINJECT_SOURCE 1 /* reconstruction re-subtracts the source term  */
 #define RBC_ZERO_FIRST 2      /* overwrite num/den instead of accumulating    */
 
+/* Padded extents: NX = nx + 2 nb, NY = ny + 2 nb (3-D; 1 in 2-D),
+ * NZ = nz + nb + top with top = nb, or 4 with free_surface = 1.  Nodes passed
+ * to the calls (sources, receivers) are in this padded frame; interior arrays
+ * (num, den, images, stores) cover x in [nb, nb + nx), y in [nb, nb + ny),
+ * z in [top, top + nz). */
+
 typedef struct {
   int ndim;         /* 2 or 3                                                 */
   int nx, ny, nz;   /* interior nodes; ny is ignored (taken as 1) for 2-D     */
   int nb;           /* random-boundary cells on each side, >= 2              */
-  int free_surface; /* must be 0: random boundary on every side              */
+  int free_surface; /* 0: random boundary on every side (padded grid         */
+                    /*    nz + 2 nb rows, interior from row nb);             */
+                    /* 1: a pressure-release top (Section 5): 4 rows (half   */
+                    /*    the stencil length) of zero velocity, a = 0, so    */
+                    /*    p = 0 there; nz + nb + 4 rows, interior from row 4 */
   double h;         /* grid spacing dx = dy = dz (m)                          */
   double dt;        /* time step (s)                                          */
   int nt;           /* number of time steps N_t (>= 1)                        */
@@ -70,7 +80,8 @@ typedef struct rbc_ctx rbc_ctx;
 /*
  * rbc_build_velocity -- pad an interior velocity with a random boundary and
  * form the leapfrog coefficient (Section 4.3, Eqs. 4-5; Algorithm 3 "create
- * a RBC").
+ * a RBC").  With g->free_surface the top 4 rows get v = 0 and a = 0 and the
+ * pad distance i is measured from the sides and the bottom only.
  *   v_int_dev: interior velocity (m/s), dense (nz, ny, nx) fp32.
  *   For a pad cell with max-norm distance i (1..nb) into the pad and padded
  *   linear index L, two splitmix64 counter draws U1 = draw(2L+1),
@@ -203,7 +214,7 @@ int rbc_image_stack(const rbc_grid *shot, const float *num_dev,
  *   fields, p^{nt-1} then p^{nt} -- the only state the gradient needs, since
  *   the random boundary lets rbc_fwi_backward rebuild the wavefield backwards
  *   instead of storing or checkpointing it.
- * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D), RBC_ECUDA.
+ * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D or free_surface), RBC_ECUDA.
  */
 int rbc_fwi_forward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
                     int nrec, const int *rec_host, const float *dobs_dev,
@@ -221,7 +232,7 @@ int rbc_fwi_forward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
  * re-subtracted).  resid_dev: from rbc_fwi_forward; panels_dev: the panels
  * it exported, or NULL to use those the context still holds from that call.
  * grad_dev: interior (nz, nx) fp32, ACCUMULATED (+=).
- * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D), RBC_ECUDA.
+ * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D or free_surface), RBC_ECUDA.
  */
 int rbc_fwi_backward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
                      int nrec, const int *rec_host, const float *resid_dev,
@@ -249,7 +260,8 @@ typedef struct {
  * stability, lays all fields out in one allocation, and times the candidate
  * tile shapes (rows per warp of the forward and reverse kernels) on the batch
  * to keep the fastest.  Synchronous.
- * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D), RBC_ECFL, RBC_ENOMEM, RBC_ECUDA.
+ * Errors: RBC_EINVAL (also for free_surface = 1), RBC_ENOTSUP (3-D), RBC_ECFL,
+ * RBC_ENOMEM, RBC_ECUDA.
  */
 int rbc_batch_create(const rbc_grid *g, int nshots, const int *nx_host,
                      const float *const *a_dev, rbc_batch **out);

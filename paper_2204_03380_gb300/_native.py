@@ -34,11 +34,16 @@ class rbc_grid(C.Structure):
                 ("dt", C.c_double), ("nt", C.c_int)]
 
     @property
+    def top(self):
+        """Rows above the interior: the random pad, or 4 zero-pressure rows with a free surface."""
+        return 4 if self.free_surface else self.nb
+
+    @property
     def padded(self):
         n = 2 * self.nb
         if self.ndim == 2:
-            return (self.nz + n, self.nx + n)
-        return (self.nz + n, self.ny + n, self.nx + n)
+            return (self.nz + self.nb + self.top, self.nx + n)
+        return (self.nz + self.nb + self.top, self.ny + n, self.nx + n)
 
     @property
     def interior(self):

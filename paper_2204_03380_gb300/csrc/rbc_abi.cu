@@ -51,7 +51,7 @@ int check_grid(const rbc_grid *g) {
   if (g->nx < 1 || g->nz < 1 || (g->ndim == 3 && g->ny < 1))
     return fail(RBC_EINVAL, "interior sizes must be >= 1");
   if (g->nb < 2) return fail(RBC_EINVAL, "nb must be >= 2 (got %d)", g->nb);
-  if (g->free_surface != 0) return fail(RBC_ENOTSUP, "free_surface != 0 is not supported");
+  if (g->free_surface != 0 && g->free_surface != 1) return fail(RBC_EINVAL, "free_surface must be 0 or 1");
   if (!(g->h > 0) || !(g->dt > 0)) return fail(RBC_EINVAL, "h and dt must be > 0");
   if (g->nt < 1) return fail(RBC_EINVAL, "nt must be >= 1");
   return RBC_OK;
@@ -59,12 +59,16 @@ int check_grid(const rbc_grid *g) {
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// Rows above the interior: the random pad, or with a free surface (Section 5)
+// half the stencil length (4) of zero-pressure rows.
+inline int top_rows(const rbc_grid *g) { return g->free_surface ? kHaloR : g->nb; }
+
 Lay make_layout(const rbc_grid *g) {
   Lay L;
   L.ndim = g->ndim;
   L.NX = g->nx + 2 * g->nb;
   L.NY = (g->ndim == 3) ? g->ny + 2 * g->nb : 1;
-  L.NZ = g->nz + 2 * g->nb;
+  L.NZ = g->nz + g->nb + top_rows(g);
   L.NX4 = (L.NX + 3) / 4 * 4;
   L.pitch = cdiv(L.NX, kTileX) * kTileX + 2 * kHaloX;
   if (g->ndim == 2) {
@@ -299,11 +303,11 @@ int enqueue_reverse(rbc_ctx *c, cudaStream_t s) {
   A.tile_ptr = c->tile_ptr;
   A.tile_rec = c->tile_rec;
   A.seis_t = c->seis_t;
-  const int nb = c->g.nb;
+  const int nb = c->g.nb, top = top_rows(&c->g);
   A.ix0 = nb;
   A.ix1 = nb + c->g.nx;
-  A.iz0 = nb;
-  A.iz1 = nb + c->g.nz;
+  A.iz0 = top;
+  A.iz1 = top + c->g.nz;
   A.iy0 = (L.ndim == 3) ? nb : 0;
   A.iy1 = (L.ndim == 3) ? nb + c->g.ny : 1;
   A.zc = c->zc;
@@ -414,7 +418,8 @@ int enq_store_fwd(rbc_ctx *c, cudaStream_t s, int) {
   A.err = c->err_dev;
   for (int n = 0; n <= g.nt; ++n) {
     if (n % c->stride == 0) {
-      launch_store_level(L, c->p[n & 1], c->store + (n / c->stride) * nint, g.nb, g.nx, g.ny, g.nz, s);
+      launch_store_level(L, c->p[n & 1], c->store + (n / c->stride) * nint, g.nb, top_rows(&g), g.nx, g.ny, g.nz,
+                         s);
       ++g_launches;
     }
     if (n == g.nt) break;
@@ -454,7 +459,8 @@ int enq_store_rev(rbc_ctx *c, cudaStream_t s, int) {
   B.err = c->err_dev;
   for (int n = g.nt; n >= 0; --n) {
     if (n % c->stride == 0) {
-      launch_store_image(L, c->store + (n / c->stride) * nint, c->q[n & 1], c->num, c->den, g.nb, g.nx, g.ny,
+      launch_store_image(L, c->store + (n / c->stride) * nint, c->q[n & 1], c->num, c->den, g.nb, top_rows(&g),
+                         g.nx, g.ny,
                          g.nz, s);
       ++g_launches;
     }
@@ -530,7 +536,8 @@ int rbc_build_velocity(const rbc_grid *g, const float *v_int_dev, float v_lo, fl
   if (!v_int_dev || !a_dev) return fail(RBC_EINVAL, "v_int_dev and a_dev must not be NULL");
   if (!(v_lo <= v_hi) || !(v_lo > 0) || !(v_max > 0)) return fail(RBC_EINVAL, "need 0 < v_lo <= v_hi, v_max > 0");
   if (mode != 0 && mode != 1) return fail(RBC_EINVAL, "mode must be 0 (blend) or 1 (literal)");
-  launch_rbc_build(g->ndim, g->nx, g->ny, g->nz, g->nb, v_int_dev, v_lo, v_hi, v_max, seed, mode, g->dt, g->h,
+  launch_rbc_build(g->ndim, g->nx, g->ny, g->nz, g->nb, top_rows(g), v_int_dev, v_lo, v_hi, v_max, seed, mode,
+                   g->dt, g->h,
                    v_pad_dev, a_dev, (cudaStream_t)stream);
   ++g_launches;
   CKL();
@@ -685,8 +692,8 @@ int rbc_rtm_shot(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int 
   if (rc) return rc;
   if (c->timing && (rc = record_event(c, s))) return rc;
   const int ow = (flags & RBC_ZERO_FIRST) ? 1 : 0;
-  launch_accum_interior(c->L, c->num, num_dev, c->g.nb, c->g.nx, c->g.ny, c->g.nz, ow, s);
-  launch_accum_interior(c->L, c->den, den_dev, c->g.nb, c->g.nx, c->g.ny, c->g.nz, ow, s);
+  launch_accum_interior(c->L, c->num, num_dev, c->g.nb, top_rows(&c->g), c->g.nx, c->g.ny, c->g.nz, ow, s);
+  launch_accum_interior(c->L, c->den, den_dev, c->g.nb, top_rows(&c->g), c->g.nx, c->g.ny, c->g.nz, ow, s);
   g_launches += 2;
   CKL();
   c->have_panels = 0;  // the reverse pass consumed the panels
@@ -750,8 +757,8 @@ int rbc_rtm_storage(rbc_ctx *c, const int *src_host, const float *wavelet_dev, i
   if (rc) return rc;
   if (c->timing && (rc = record_event(c, s))) return rc;
   const int ow = (flags & RBC_ZERO_FIRST) ? 1 : 0;
-  launch_accum_interior(c->L, c->num, num_dev, c->g.nb, c->g.nx, c->g.ny, c->g.nz, ow, s);
-  launch_accum_interior(c->L, c->den, den_dev, c->g.nb, c->g.nx, c->g.ny, c->g.nz, ow, s);
+  launch_accum_interior(c->L, c->num, num_dev, c->g.nb, top_rows(&c->g), c->g.nx, c->g.ny, c->g.nz, ow, s);
+  launch_accum_interior(c->L, c->den, den_dev, c->g.nb, top_rows(&c->g), c->g.nx, c->g.ny, c->g.nz, ow, s);
   g_launches += 2;
   CKL();
   c->have_panels = 1;  // the forward loop leaves p^{nt-1}, p^{nt} in place
@@ -788,7 +795,8 @@ int rbc_image_stack(const rbc_grid *shot, const float *num_dev, const float *den
 int rbc_fwi_forward(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nrec, const int *rec_host,
                     const float *dobs_dev, float *resid_dev, double *misfit_dev, float *panels_dev, void *stream) {
   if (!c) return fail(RBC_EINVAL, "ctx is NULL");
-  if (c->L.ndim != 2) return fail(RBC_ENOTSUP, "the FWI gradient is built for 2-D grids");
+  if (c->L.ndim != 2 || c->g.free_surface)
+    return fail(RBC_ENOTSUP, "the FWI gradient is built for 2-D grids with the random boundary on every side");
   if (!wavelet_dev || nrec < 1 || !dobs_dev || !resid_dev || !misfit_dev)
     return fail(RBC_EINVAL, "NULL pointer or no receivers");
   cudaStream_t s = (cudaStream_t)stream;
@@ -816,7 +824,8 @@ int rbc_fwi_forward(rbc_ctx *c, const int *src_host, const float *wavelet_dev, i
 int rbc_fwi_backward(rbc_ctx *c, const int *src_host, const float *wavelet_dev, int nrec, const int *rec_host,
                      const float *resid_dev, const float *panels_dev, float *grad_dev, void *stream) {
   if (!c) return fail(RBC_EINVAL, "ctx is NULL");
-  if (c->L.ndim != 2) return fail(RBC_ENOTSUP, "the FWI gradient is built for 2-D grids");
+  if (c->L.ndim != 2 || c->g.free_surface)
+    return fail(RBC_ENOTSUP, "the FWI gradient is built for 2-D grids with the random boundary on every side");
   if (!wavelet_dev || nrec < 1 || !resid_dev || !grad_dev) return fail(RBC_EINVAL, "NULL pointer or no receivers");
   if (!panels_dev && !c->have_panels) return fail(RBC_EINVAL, "no panels: pass panels_dev or run rbc_fwi_forward");
   cudaStream_t s = (cudaStream_t)stream;

@@ -119,7 +119,7 @@ void rev_tiling(const Lay &L, int zc, int *gx, int *gy, int *gz, int *tz_or_by);
 void launch_copy_in(const Lay &L, const float *dense, float *pitched, cudaStream_t s);
 void launch_copy_out(const Lay &L, const float *pitched, float *dense, cudaStream_t s);
 void launch_transpose(const float *in, float *out, int rows, int cols, cudaStream_t s);
-void launch_accum_interior(const Lay &L, const float *pitched, float *dense, int nb, int nx,
+void launch_accum_interior(const Lay &L, const float *pitched, float *dense, int nb, int top, int nx,
                            int ny, int nz, int overwrite, cudaStream_t s);
 void launch_max(const float *x, long long n, unsigned int *out_bits, cudaStream_t s);
 void launch_image_stack(const float *num, const float *den, const unsigned int *maxbits,
@@ -132,12 +132,13 @@ void launch_fwi_adjoint_source(const float *resid, float *seis_t, int nrec, int 
 void launch_fwi_finalize(const Lay &L, const float *num, const float *a, float *grad, int nb, int nx,
                          int nz, double dt, double h, cudaStream_t s);
 // RTM with wavefield storage (Algorithm 2, Eq. 7 stride)
-void launch_store_level(const Lay &L, const float *p, float *slot, int nb, int nx, int ny, int nz, cudaStream_t s);
-void launch_store_image(const Lay &L, const float *slot, const float *pb, float *num, float *den, int nb, int nx,
-                        int ny, int nz, cudaStream_t s);
+void launch_store_level(const Lay &L, const float *p, float *slot, int nb, int top, int nx, int ny, int nz,
+                        cudaStream_t s);
+void launch_store_image(const Lay &L, const float *slot, const float *pb, float *num, float *den, int nb, int top,
+                        int nx, int ny, int nz, cudaStream_t s);
 void launch_rec_inject(const float *a, float *bn, const int *rec_off, const ShotInfo *info, const float *seis_t,
                        int n, int nrec_cap, cudaStream_t s);
-void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_int, double v_lo,
+void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, int top, const float *v_int, double v_lo,
                       double v_hi, double v_max, uint64_t seed, int mode, double dt, double h,
                       float *v_pad, float *a, cudaStream_t s);
 } // namespace rbc

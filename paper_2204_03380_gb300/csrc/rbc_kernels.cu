@@ -231,7 +231,7 @@ void launch_transpose(const float *in, float *out, int rows, int cols, cudaStrea
 }
 
 __global__ void k_accum_interior(const Lay L, const float *__restrict__ pitched, float *__restrict__ dense,
-                                 int nb, int nx, int ny, int nz, int overwrite) {
+                                 int nb, int top, int nx, int ny, int nz, int overwrite) {
   const long long n = (long long)nx * ny * nz;
   const int yo = (L.ndim == 3) ? nb : 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -240,15 +240,15 @@ __global__ void k_accum_interior(const Lay L, const float *__restrict__ pitched,
     const long long r = i / nx;
     const int y = (int)(r % ny);
     const int z = (int)(r / ny);
-    const float v = pitched[lay_off(L, x + nb, y + yo, z + nb)];
+    const float v = pitched[lay_off(L, x + nb, y + yo, z + top)];
     dense[i] = overwrite ? v : dense[i] + v;
   }
 }
 
-void launch_accum_interior(const Lay &L, const float *pitched, float *dense, int nb, int nx, int ny,
+void launch_accum_interior(const Lay &L, const float *pitched, float *dense, int nb, int top, int nx, int ny,
                            int nz, int overwrite, cudaStream_t s) {
   const long long n = (long long)nx * ny * nz;
-  k_accum_interior<<<grid_for(n, 256), 256, 0, s>>>(L, pitched, dense, nb, nx, ny, nz, overwrite);
+  k_accum_interior<<<grid_for(n, 256), 256, 0, s>>>(L, pitched, dense, nb, top, nx, ny, nz, overwrite);
 }
 
 // Maximum of non-negative values as ordered uint bits (atomicMax).
@@ -377,10 +377,10 @@ __device__ __forceinline__ int pad_distance(int q, int nb, int n) {
 // Section 4.3: random velocities in an nb-cell pad, blended towards the
 // nearest interior value with a coefficient between the Gaussian (Eq. 5) and
 // linear (Eq. 4) tapers; a = (v dt / h)^2.
-__global__ void k_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *__restrict__ v_int,
+__global__ void k_rbc_build(int ndim, int nx, int ny, int nz, int nb, int top, const float *__restrict__ v_int,
                             double v_lo, double v_hi, double v_max, uint64_t seed, int mode, double dt,
                             double h, float *__restrict__ v_pad, float *__restrict__ a) {
-  const int NX = nx + 2 * nb, NZ = nz + 2 * nb;
+  const int NX = nx + 2 * nb, NZ = nz + nb + top;
   const int NY = (ndim == 3) ? ny + 2 * nb : 1;
   const int nyi = (ndim == 3) ? ny : 1;
   const long long n = (long long)NX * NY * NZ;
@@ -390,9 +390,14 @@ __global__ void k_rbc_build(int ndim, int nx, int ny, int nz, int nb, const floa
     const long long r = L / NX;
     const int y = (int)(r % NY);
     const int z = (int)(r / NY);
-    int i = max(pad_distance(x, nb, nx), pad_distance(z, nb, nz));
+    if (top != nb && z < top) {  // free surface: the zero-pressure rows (a = 0 keeps p = 0)
+      if (v_pad) v_pad[L] = 0.f;
+      a[L] = 0.f;
+      continue;
+    }
+    int i = max(pad_distance(x, nb, nx), pad_distance(z, top, nz));
     if (ndim == 3) i = max(i, pad_distance(y, nb, ny));
-    const int ex = min(max(x - nb, 0), nx - 1), ez = min(max(z - nb, 0), nz - 1);
+    const int ex = min(max(x - nb, 0), nx - 1), ez = min(max(z - top, 0), nz - 1);
     const int ey = (ndim == 3) ? min(max(y - nb, 0), ny - 1) : 0;
     double v = (double)v_int[((long long)ez * nyi + ey) * nx + ex];
     if (i > 0) {
@@ -416,11 +421,11 @@ __global__ void k_rbc_build(int ndim, int nx, int ny, int nz, int nb, const floa
   }
 }
 
-void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_int, double v_lo,
+void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, int top, const float *v_int, double v_lo,
                       double v_hi, double v_max, uint64_t seed, int mode, double dt, double h,
                       float *v_pad, float *a, cudaStream_t s) {
-  const long long n = (long long)(nx + 2 * nb) * (ndim == 3 ? ny + 2 * nb : 1) * (nz + 2 * nb);
-  k_rbc_build<<<grid_for(n, 256), 256, 0, s>>>(ndim, nx, ny, nz, nb, v_int, v_lo, v_hi, v_max, seed,
+  const long long n = (long long)(nx + 2 * nb) * (ndim == 3 ? ny + 2 * nb : 1) * (nz + nb + top);
+  k_rbc_build<<<grid_for(n, 256), 256, 0, s>>>(ndim, nx, ny, nz, nb, top, v_int, v_lo, v_hi, v_max, seed,
                                                mode, dt, h, v_pad, a);
 }
 
@@ -428,15 +433,15 @@ void launch_rbc_build(int ndim, int nx, int ny, int nz, int nb, const float *v_i
 // Algorithm 2 keeps the source wavefield every k steps (Eq. 7); the kept
 // level is the interior box as a dense [nz][ny][nx] slot.  Threads run along
 // x of one interior row (coalesced on both sides), blocks stride over rows.
-__global__ void k_store_level(const Lay L, const float *__restrict__ p, float *__restrict__ slot, int nb, int nx,
-                              int ny, int nz) {
+__global__ void k_store_level(const Lay L, const float *__restrict__ p, float *__restrict__ slot, int nb, int top,
+                              int nx, int ny, int nz) {
   griddep_wait();
   const int yo = (L.ndim == 3) ? nb : 0;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x < nx)
     for (int r = blockIdx.y; r < ny * nz; r += gridDim.y) {
       const int y = r % ny, z = r / ny;
-      slot[(long long)r * nx + x] = p[lay_off(L, x + nb, y + yo, z + nb)];
+      slot[(long long)r * nx + x] = p[lay_off(L, x + nb, y + yo, z + top)];
     }
   griddep_launch();
 }
@@ -444,14 +449,15 @@ __global__ void k_store_level(const Lay L, const float *__restrict__ p, float *_
 // Eq. 3 integrals at a kept level n: num += p^n pbar_n, den += (p^n)^2, with
 // p^n read back from its slot (num/den in the pitched layout).
 __global__ void k_store_image(const Lay L, const float *__restrict__ slot, const float *__restrict__ pb,
-                              float *__restrict__ num, float *__restrict__ den, int nb, int nx, int ny, int nz) {
+                              float *__restrict__ num, float *__restrict__ den, int nb, int top, int nx, int ny,
+                              int nz) {
   griddep_wait();
   const int yo = (L.ndim == 3) ? nb : 0;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x < nx)
     for (int r = blockIdx.y; r < ny * nz; r += gridDim.y) {
       const int y = r % ny, z = r / ny;
-      const int o = lay_off(L, x + nb, y + yo, z + nb);
+      const int o = lay_off(L, x + nb, y + yo, z + top);
       const float v = slot[(long long)r * nx + x];
       num[o] += v * pb[o];
       den[o] += v * v;
@@ -477,13 +483,15 @@ static dim3 interior_grid(int nx, int rows) {
   return dim3(cdiv(nx, 128), (unsigned)min(rows, 4 * 152 * 16 / max(1, cdiv(nx, 128))));
 }
 
-void launch_store_level(const Lay &L, const float *p, float *slot, int nb, int nx, int ny, int nz, cudaStream_t s) {
-  launch_pdl(k_store_level, interior_grid(nx, ny * nz), dim3(128), 0, s, L, p, slot, nb, nx, ny, nz);
+void launch_store_level(const Lay &L, const float *p, float *slot, int nb, int top, int nx, int ny, int nz,
+                        cudaStream_t s) {
+  launch_pdl(k_store_level, interior_grid(nx, ny * nz), dim3(128), 0, s, L, p, slot, nb, top, nx, ny, nz);
 }
 
-void launch_store_image(const Lay &L, const float *slot, const float *pb, float *num, float *den, int nb, int nx,
-                        int ny, int nz, cudaStream_t s) {
-  launch_pdl(k_store_image, interior_grid(nx, ny * nz), dim3(128), 0, s, L, slot, pb, num, den, nb, nx, ny, nz);
+void launch_store_image(const Lay &L, const float *slot, const float *pb, float *num, float *den, int nb, int top,
+                        int nx, int ny, int nz, cudaStream_t s) {
+  launch_pdl(k_store_image, interior_grid(nx, ny * nz), dim3(128), 0, s, L, slot, pb, num, den, nb, top, nx, ny,
+             nz);
 }
 
 void launch_rec_inject(const float *a, float *bn, const int *rec_off, const ShotInfo *info, const float *seis_t,

@@ -45,8 +45,9 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert "NULL" in R.rbc_last_error()
     bad = R.make_grid(4, 10, 1, 10, 5, 10.0, 1e-3, 10)
     assert lib.rbc_create(C.byref(bad), C.c_void_p(16), C.byref(out)) == 1
-    fs = R.make_grid(2, 10, 1, 10, 5, 10.0, 1e-3, 10, free_surface=1)
-    assert lib.rbc_create(C.byref(fs), C.c_void_p(16), C.byref(out)) == 6
+    fs = R.make_grid(2, 10, 1, 10, 5, 10.0, 1e-3, 10, free_surface=2)
+    assert lib.rbc_create(C.byref(fs), C.c_void_p(16), C.byref(out)) == 1
+    assert R.make_grid(2, 10, 1, 10, 5, 10.0, 1e-3, 10, free_surface=1).padded == (10 + 5 + 4, 20)
     nb1 = R.make_grid(2, 10, 1, 10, 1, 10.0, 1e-3, 10)
     assert lib.rbc_build_velocity(C.byref(nb1), C.c_void_p(16), 1.0, 2.0, 2.0, 0, 0, None,
                                   C.c_void_p(16), None) == 1
@@ -85,3 +86,21 @@ def test_nyquist_stride_and_storage_size_on_the_host():
     assert R.rbc_storage_bytes(grid, 4) == 4 * 10 * 5 * 7
     with pytest.raises(R.RBCError):
         R.rbc_storage_bytes(grid, 0)
+
+
+def test_paper_receiver_grid_of_eqs_8_9():
+    # host geometry: the 320 x 320 receivers of Eqs. 8-9 on the 25 m grid of
+    # the 10 km model land on consecutive nodes 40 .. 359 (1012.5 m rounds to
+    # node 41 with halves rounded up) in both axes
+    import json
+    import numpy as np
+    import workloads as W
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))["receivers_3d"]
+    n = int(g["extent_m"] / g["h"]) + 1
+    w = W.scaled(W.SHOT_3D, nx=n, ny=n, nz=20, nb=5, name="hpc4e")
+    w = W.dataclasses.replace(w, h=g["h"])
+    rec = W.receiver_grid_m(w, g["start_m"], g["spacing_m"], g["count"], top=4)
+    assert rec.shape == (g["count"] ** 2, 3)
+    xs = np.unique(rec[:, 0]) - w.nb
+    assert xs[0] == 41 and xs[-1] == 360 and np.all(np.diff(xs) == 1)
+    assert np.all(rec[:, 2] == 5)

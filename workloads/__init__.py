@@ -174,26 +174,47 @@ def dipping_salt_3d(nx: int, ny: int, nz: int, seed: int, v_min=1500.0, v_max=45
 # --------------------------------------------------------------------------
 # geometry (padded-frame nodes)
 # --------------------------------------------------------------------------
+# `top` is the first interior row of the padded frame: nb (random boundary on
+# every side, the default) or 4 (free-surface grids).
 def surface_line(w: Workload, depth: int = 1, step: int = 1, x_from: int = 0,
-                 x_to: int | None = None) -> np.ndarray:
+                 x_to: int | None = None, top: int | None = None) -> np.ndarray:
     """Receivers every `step` interior columns at interior depth `depth` (2-D)."""
     x_to = w.nx if x_to is None else x_to
+    top = w.nb if top is None else top
     xs = np.arange(x_from, x_to, step) + w.nb
-    return np.stack([xs, np.zeros_like(xs), np.full_like(xs, w.nb + depth)], 1).astype(np.int32)
+    return np.stack([xs, np.zeros_like(xs), np.full_like(xs, top + depth)], 1).astype(np.int32)
 
 
-def surface_grid(w: Workload, depth: int = 1, step: int = 2) -> np.ndarray:
+def surface_grid(w: Workload, depth: int = 1, step: int = 2, top: int | None = None) -> np.ndarray:
     """Receivers on a square surface grid every `step` nodes (3-D)."""
+    top = w.nb if top is None else top
     xs = np.arange(0, w.nx, step) + w.nb
     ys = np.arange(0, w.ny, step) + w.nb
     X, Y = np.meshgrid(xs, ys, indexing="xy")
-    Z = np.full_like(X, w.nb + depth)
+    Z = np.full_like(X, top + depth)
     return np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1).astype(np.int32)
 
 
-def source_at(w: Workload, ix: int, iy: int = 0, depth: int = 1) -> np.ndarray:
+def receiver_grid_m(w: Workload, start_m: float, spacing_m: float, count: int, depth: int = 1,
+                    top: int | None = None) -> np.ndarray:
+    """Receivers at r = start + spacing (i - 1), i = 1..count, metres from the
+    model origin on both surface axes (the form of the paper's 3-D acquisition,
+    Eqs. 8-9), each at the nearest interior node (a position half-way between
+    nodes goes to the next node); nodes outside the model are dropped (3-D)."""
+    top = w.nb if top is None else top
+    r = start_m + spacing_m * np.arange(count)
+    idx = np.floor(r / w.h + 0.5).astype(np.int64)  # nearest node, halves up (the paper's sit on half nodes)
+    ix = idx[(idx >= 0) & (idx < w.nx)]
+    iy = idx[(idx >= 0) & (idx < w.ny)]
+    X, Y = np.meshgrid(ix + w.nb, iy + w.nb, indexing="xy")
+    Z = np.full_like(X, top + depth)
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1).astype(np.int32)
+
+
+def source_at(w: Workload, ix: int, iy: int = 0, depth: int = 1, top: int | None = None) -> np.ndarray:
     """Source node at interior (ix, iy, depth) in the padded frame."""
-    return np.array([ix + w.nb, (iy + w.nb) if w.ndim == 3 else 0, depth + w.nb], np.int32)
+    top = w.nb if top is None else top
+    return np.array([ix + w.nb, (iy + w.nb) if w.ndim == 3 else 0, depth + top], np.int32)
 
 
 def shot_columns(w: Workload, nshots: int) -> np.ndarray:
