@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_fwd3d_tma(const __grid_consta
     ok = __all_sync(0xffffffffu, ok);  // keep the warp's decision uniform
     if (lane == 0)
       for (int j = 0; j < 4; ++j) mbar_arrive(&emptyP[(gp + j) % kRP]);
+#pragma unroll 4  // the z queue's shifts become register renames within an unrolled group
     for (int r = 0; ok && r < nplanes; ++r) {
       const int z = T.zb + r;
       const int top = gp + r + 8, cen = gp + r + 4, tk = gt + r;
