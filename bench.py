@@ -64,8 +64,9 @@ def parse():
                    help="survey2d / shot3d: rbc = Algorithm 3 (reconstruction through the random boundary, "
                         "default); storage = Algorithm 2 with the source wavefield kept in device memory every "
                         "k steps, k from Eq. 7 with f_max = 2.5 x the peak frequency")
-    p.add_argument("--denoise-models", type=int, default=96, help="denoise: training models")
-    p.add_argument("--denoise-size", type=int, default=128, help="denoise: training image size")
+    p.add_argument("--denoise-models", type=int, default=512, help="denoise: training models")
+    p.add_argument("--denoise-size", type=int, default=96, help="denoise: training image size")
+    p.add_argument("--denoise-steps", type=int, default=20000, help="denoise: Adam steps (batch 32)")
     p.add_argument("--cnn-batch", type=int, nargs=3, default=[32, 512, 512],
                    help="cnn: images, height, width of one training / inference batch")
     p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d", "denoise", "cnn"], default="survey2d",
@@ -399,8 +400,9 @@ def run_denoise(args, rank, world):
     x, t = torch.cat([x, x.flip(-1)]), torch.cat([t, t.flip(-1)])
     net = D.Denoiser(seed=1)
     t0 = time.perf_counter()
-    for lr, st, sd in ((2e-3, 1600, 0), (5e-4, 800, 1), (1e-4, 800, 2)):
-        net.fit(x, t, steps=st, batch=16, lr=lr, seed=sd)
+    ns = args.denoise_steps
+    for lr, st, sd in ((2e-3, ns // 2, 0), (5e-4, ns // 4, 1), (1e-4, ns // 4, 2)):
+        net.fit(x, t, steps=st, batch=32, lr=lr, seed=sd)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     xs, ts, _ = D.normalized_pairs(held)

@@ -159,11 +159,12 @@ def rtm_realizations(R, grid, v_true, v_mig, K, shots, rec, wavelet, rbc, obs_se
 
 
 def normalized_pairs(iset: ImageSet):
-    """(input, target) pairs scaled by the target's RMS so that every model
-    weighs the same in the loss."""
-    t = iset.stack
-    scale = t.pow(2).mean(dim=(1, 2), keepdim=True).sqrt().clamp_min(1e-30)
-    return iset.single / scale, t / scale, scale
+    """(input, target) pairs scaled by the input's RMS, so that every model
+    weighs the same in the loss; the scale is the one available at inference,
+    where only the single-realization image exists."""
+    x = iset.single
+    scale = x.pow(2).mean(dim=(1, 2), keepdim=True).sqrt().clamp_min(1e-30)
+    return x / scale, iset.stack / scale, scale
 
 
 def rel_l2(a, b) -> float:
