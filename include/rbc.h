@@ -288,8 +288,11 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
  * reverse ms, forward launches, reverse launches, calls). */
 int rbc_batch_timing(rbc_batch *b, int enable, double *out);
 
-/* rbc_batch_info -- out[0..5]: forward and reverse rows per warp chosen by the
- * autotuner, work items of both kernels, and their persistent grid sizes. */
+/* rbc_batch_info -- out[0..12]: forward and reverse rows per warp chosen by
+ * the autotuner (0 = the streaming kernels), work items of both kernels,
+ * their grids, then the measured per-launch time in microseconds of every
+ * candidate: forward streaming / 1 / 2 / 4 rows, reverse 1 / 2 rows /
+ * streaming (0 where a candidate was not timed).  Host only. */
 int rbc_batch_info(const rbc_batch *b, int *out);
 
 /* ------------------------------------------------------------------------

@@ -120,6 +120,306 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
   }
 }
 
+// Streaming form of the forward step for DRAM-bound batches: every warp owns
+// a 128-column strip of kSZ rows of one shot and keeps its own rings in
+// shared memory -- kSR rows of p^n (with the 4-column halo, 544 bytes each)
+// and kSA rows of a and p^{n-1} -- filled by bulk asynchronous copies
+// (cp.async.bulk, completion counted on one mbarrier per ring slot) up to
+// kSR rows ahead of the row being computed.  Loads are in flight while the
+// warp computes, where the register-queue kernels wait on them; the x and z
+// neighbours come from the ring.  Every wait is bounded.
+constexpr int kSZ = 64, kSR = 12, kSA = 4;
+constexpr int kSRow = kTileX + 8;                             // 136 floats: x0-4 .. x0+131
+constexpr int kSWarp = kSR * kSRow + 2 * kSA * kTileX;        // floats per warp
+constexpr size_t kStreamSmem = sizeof(float) * kSWarp * k2dWarps + sizeof(uint64_t) * (kSR + kSA) * k2dWarps;
+constexpr long long kSWait = 2000000000LL;                    // about a second
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool s_try(uint64_t *b, uint32_t par) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(s_addr(b)), "r"(par) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool s_wait(uint64_t *b, uint32_t par) {
+  if (s_try(b, par)) return true;
+  const long long t0 = clock64();
+  while (!s_try(b, par))
+    if (clock64() - t0 > kSWait) return false;
+  return true;
+}
+__device__ __forceinline__ void s_copy(float *dst, const float *src, uint32_t bytes, uint64_t *b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   s_addr(dst)), "l"(src), "r"(bytes), "r"(s_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ void s_expect(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d_stream(const BShot *__restrict__ shots,
+                                                                 const int *__restrict__ item_shot, int nitems,
+                                                                 int n, const float *__restrict__ wav,
+                                                                 float src_scale, int *err) {
+  extern __shared__ __align__(128) float sm_s[];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  float *rc = sm_s + w * kSWarp;       // [kSR][kSRow]  p^n
+  float *ra = rc + kSR * kSRow;        // [kSA][128]    a
+  float *rp = ra + kSA * kTileX;       // [kSA][128]    p^{n-1}
+  uint64_t *bc = reinterpret_cast<uint64_t *>(sm_s + k2dWarps * kSWarp) + w * (kSR + kSA);
+  uint64_t *ba = bc + kSR;
+  if (lane == 0) {
+    for (int i = 0; i < kSR + kSA; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bc + i)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const float f = wav[n] * src_scale;
+  int gc = 0, ga = 0;  // copies issued so far into the p^n / (a, p^{n-1}) rings
+  bool ok = true;
+  for (int t = blockIdx.x * k2dWarps + w; ok && t < nitems; t += gridDim.x * k2dWarps) {
+    const BShot &S = shots[item_shot[t]];
+    const Lay &L = S.L;
+    const int loc = t - S.tbase_f;
+    const int x0 = (loc % S.gx) * kTileX, zb = (loc / S.gx) * kSZ;
+    const int nrow = min(kSZ, L.NZ - zb);
+    const float *cur = (n & 1) ? S.p1 : S.p0;
+    float *nxt = (n & 1) ? S.p0 : S.p1;
+    const int c0 = gc, a0 = ga;
+    // p^n rows zb-4 .. zb+nrow+3 (task index i = row - zb + 4); a, p^{n-1} rows zb .. zb+nrow-1
+    auto issue_c = [&](int i) {
+      const int q = c0 + i;
+      uint64_t *b = bc + q % kSR;
+      s_expect(b, kSRow * 4);
+      s_copy(rc + (q % kSR) * kSRow, cur + L.origin + (zb - 4 + i) * L.pitch + x0 - 4, kSRow * 4, b);
+    };
+    auto issue_a = [&](int i) {
+      const int q = a0 + i;
+      uint64_t *b = ba + q % kSA;
+      const int o = L.origin + (zb + i) * L.pitch + x0;
+      s_expect(b, 2 * kTileX * 4);
+      s_copy(ra + (q % kSA) * kTileX, S.a + o, kTileX * 4, b);
+      s_copy(rp + (q % kSA) * kTileX, nxt + o, kTileX * 4, b);
+    };
+    if (lane == 0) {
+      for (int i = 0; i < min(kSR, nrow + 8); ++i) issue_c(i);
+      for (int i = 0; i < min(kSA, nrow); ++i) issue_a(i);
+    }
+    int waited_c = 0, waited_a = 0;  // rows of this task already seen complete
+    const int xl = x0 + lane * 4;
+    int r = 0;
+    for (; r < nrow; ++r) {
+      while (ok && waited_c <= r + 8) {
+        const int q = c0 + waited_c;
+        ok = s_wait(bc + q % kSR, (uint32_t)(q / kSR) & 1u);
+        if (ok) ++waited_c;
+      }
+      if (ok) {
+        const int q = a0 + r;
+        ok = s_wait(ba + q % kSA, (uint32_t)(q / kSA) & 1u);
+        if (ok) waited_a = r + 1;
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      const int z = zb + r;
+      const float *crow = rc + ((c0 + r + 4) % kSR) * kSRow + lane * 4;
+      const float4 lf = *reinterpret_cast<const float4 *>(crow), c = *reinterpret_cast<const float4 *>(crow + 4),
+                   rt = *reinterpret_cast<const float4 *>(crow + 8);
+      float4 zq[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        zq[k] = *reinterpret_cast<const float4 *>(rc + ((c0 + r + k) % kSR) * kSRow + lane * 4 + 4);
+      const int qa = (a0 + r) % kSA;
+      const float4 av = *reinterpret_cast<const float4 *>(ra + qa * kTileX + lane * 4);
+      const float4 po = *reinterpret_cast<const float4 *>(rp + qa * kTileX + lane * 4);
+      if (xl < L.NX4) {
+        const int o = L.origin + z * L.pitch + xl;
+        float4 v = leap4_2d(lf, c, rt, zq, po, av);
+        const int d = S.src_off - o;
+        if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * f);
+        st4(nxt + o, v);
+      }
+      __syncwarp();  // every lane is done with p^n row r and (a, p^{n-1}) row r: their slots refill
+      if (lane == 0) {
+        if (r + kSR < nrow + 8) issue_c(r + kSR);
+        if (r + kSA < nrow) issue_a(r + kSA);
+      }
+    }
+    if (!ok) {
+      // let this task's copies in flight land before the block's shared memory goes away:
+      // rows below min(r + ring, end) were issued, rows below waited_* were seen complete
+      if (lane == 0) {
+        atomicOr(err, 1);
+        for (int i = waited_c; i < min(r + kSR, nrow + 8); ++i) {
+          const int q = c0 + i;
+          s_wait(bc + q % kSR, (uint32_t)(q / kSR) & 1u);
+        }
+        for (int i = waited_a; i < min(r + kSA, nrow); ++i) {
+          const int q = a0 + i;
+          s_wait(ba + q % kSA, (uint32_t)(q / kSA) & 1u);
+        }
+      }
+      break;
+    }
+    gc = c0 + nrow + 8;
+    ga = a0 + nrow;
+  }
+}
+
+// Streaming form of the fused reverse step (Eqs. 6, 2 and 3): the same
+// per-warp task and rings as k_fwd2d_stream, with two window rings (p^R_n,
+// pbar_n) and one ring of the rows read once (a, p^R_{n+1}, pbar_{n+1}, and
+// num / den where the row meets the image).  The task's receivers are added
+// to pbar_{n-1} after its last row is stored.
+constexpr int kSRr = 12, kSAr = 3;
+constexpr int kSWarpR = 2 * kSRr * kSRow + kSAr * 5 * kTileX;
+constexpr size_t kStreamSmemR =
+    sizeof(float) * kSWarpR * k2dWarps + sizeof(uint64_t) * (2 * kSRr + kSAr) * k2dWarps;
+
+__global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_stream(const BShot *__restrict__ shots,
+                                                                 const int *__restrict__ item_shot, int nitems,
+                                                                 int n, int nt, const float *__restrict__ wav,
+                                                                 float src_scale, float rec_scale, int *err) {
+  extern __shared__ __align__(128) float sm_r[];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  float *wr = sm_r + w * kSWarpR;          // [kSRr][kSRow] p^R_n
+  float *wb = wr + kSRr * kSRow;           // [kSRr][kSRow] pbar_n
+  float *rr = wb + kSRr * kSRow;           // [kSAr][5][128] a, p^R_{n+1}, pbar_{n+1}, num, den
+  uint64_t *bw = reinterpret_cast<uint64_t *>(sm_r + k2dWarps * kSWarpR) + w * (2 * kSRr + kSAr);
+  uint64_t *br = bw + 2 * kSRr;  // bw[kSRr]: the window slots' barriers (both rings)
+  if (lane == 0) {
+    for (int i = 0; i < 2 * kSRr + kSAr; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bw + i)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const bool do_r = n < nt && n > 0, do_b = n > 0;
+  const float fsrc = do_r ? wav[n] * src_scale : 0.f;  // f[nt] does not exist
+  int gc = 0, ga = 0;
+  bool ok = true;
+  for (int t = blockIdx.x * k2dWarps + w; ok && t < nitems; t += gridDim.x * k2dWarps) {
+    const BShot &S = shots[item_shot[t]];
+    const Lay &L = S.L;
+    const int loc = t - S.tbase_r;
+    const int x0 = (loc % S.gx) * kTileX, zb = (loc / S.gx) * kSZ;
+    const int nrow = min(kSZ, L.NZ - zb);
+    const float *rc = (n & 1) ? S.p1 : S.p0;
+    float *rn = (n & 1) ? S.p0 : S.p1;
+    const float *bc = (n & 1) ? S.q1 : S.q0;
+    float *bn = (n & 1) ? S.q0 : S.q1;
+    const bool strip_img = x0 < S.ix1 && x0 + kTileX > S.ix0;
+    const int c0 = gc, a0 = ga;
+    auto issue_w = [&](int i) {
+      const int q = c0 + i;
+      const int o = L.origin + (zb - 4 + i) * L.pitch + x0 - 4;
+      s_expect(bw + q % kSRr, 2 * kSRow * 4);
+      s_copy(wr + (q % kSRr) * kSRow, rc + o, kSRow * 4, bw + q % kSRr);
+      s_copy(wb + (q % kSRr) * kSRow, bc + o, kSRow * 4, bw + q % kSRr);
+    };
+    auto issue_r = [&](int i) {
+      const int q = a0 + i, z = zb + i;
+      const int o = L.origin + z * L.pitch + x0;
+      float *d = rr + (q % kSAr) * 5 * kTileX;
+      const bool img = strip_img && z >= S.iz0 && z < S.iz1;
+      s_expect(br + q % kSAr, (img ? 5 : 3) * kTileX * 4);
+      s_copy(d, S.a + o, kTileX * 4, br + q % kSAr);
+      s_copy(d + kTileX, rn + o, kTileX * 4, br + q % kSAr);
+      s_copy(d + 2 * kTileX, bn + o, kTileX * 4, br + q % kSAr);
+      if (img) {
+        s_copy(d + 3 * kTileX, S.num + o, kTileX * 4, br + q % kSAr);
+        s_copy(d + 4 * kTileX, S.den + o, kTileX * 4, br + q % kSAr);
+      }
+    };
+    if (lane == 0) {
+      for (int i = 0; i < min(kSRr, nrow + 8); ++i) issue_w(i);
+      for (int i = 0; i < min(kSAr, nrow); ++i) issue_r(i);
+    }
+    int waited_w = 0, waited_r = 0;
+    const int xl = x0 + lane * 4;
+    const bool xok = xl < L.NX4;
+    int r = 0;
+    for (; r < nrow; ++r) {
+      while (ok && waited_w <= r + 8) {
+        const int q = c0 + waited_w;
+        ok = s_wait(bw + q % kSRr, (uint32_t)(q / kSRr) & 1u);
+        if (ok) ++waited_w;
+      }
+      if (ok) {
+        const int q = a0 + r;
+        ok = s_wait(br + q % kSAr, (uint32_t)(q / kSAr) & 1u);
+        if (ok) waited_r = r + 1;
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      const int z = zb + r;
+      const int o = L.origin + z * L.pitch + xl;
+      const float *d = rr + ((a0 + r) % kSAr) * 5 * kTileX + lane * 4;
+      const float4 av = *reinterpret_cast<const float4 *>(d);
+      float4 cen[2];
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {  // f = 0: p^R (Eq. 6), f = 1: pbar (Eq. 2)
+        const float *ring = f ? wb : wr;
+        const float *crow = ring + ((c0 + r + 4) % kSRr) * kSRow + lane * 4;
+        const float4 lf = *reinterpret_cast<const float4 *>(crow), c = *reinterpret_cast<const float4 *>(crow + 4),
+                     rt = *reinterpret_cast<const float4 *>(crow + 8);
+        cen[f] = c;
+        if ((f ? do_b : do_r) && xok) {
+          float4 zq[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k)
+            zq[k] = *reinterpret_cast<const float4 *>(ring + ((c0 + r + k) % kSRr) * kSRow + lane * 4 + 4);
+          const float4 po = *reinterpret_cast<const float4 *>(d + (1 + f) * kTileX);
+          float4 v = leap4_2d(lf, c, rt, zq, po, av);
+          if (!f) {
+            const int dd = S.src_off - o;
+            if ((unsigned)dd < 4u) point_sub(v, dd, cmp(av, dd) * fsrc);
+          }
+          st4((f ? bn : rn) + o, v);
+        }
+      }
+      if (strip_img && z >= S.iz0 && z < S.iz1 && xok && xl + 3 >= S.ix0 && xl < S.ix1) {
+        st4(S.num + o, add4(*reinterpret_cast<const float4 *>(d + 3 * kTileX),
+                            masked_prod(cen[0], cen[1], xl, S.ix0, S.ix1)));
+        st4(S.den + o, add4(*reinterpret_cast<const float4 *>(d + 4 * kTileX),
+                            masked_prod(cen[0], cen[0], xl, S.ix0, S.ix1)));
+      }
+      __syncwarp();  // the slots of row r are free
+      if (lane == 0) {
+        if (r + kSRr < nrow + 8) issue_w(r + kSRr);
+        if (r + kSAr < nrow) issue_r(r + kSAr);
+      }
+    }
+    if (!ok) {
+      if (lane == 0) {
+        atomicOr(err, 1);
+        for (int i = waited_w; i < min(r + kSRr, nrow + 8); ++i) {
+          const int q = c0 + i;
+          s_wait(bw + q % kSRr, (uint32_t)(q / kSRr) & 1u);
+        }
+        for (int i = waited_r; i < min(r + kSAr, nrow); ++i) {
+          const int q = a0 + i;
+          s_wait(br + q % kSAr, (uint32_t)(q / kSAr) & 1u);
+        }
+      }
+      break;
+    }
+    // Eq. 2 source term at the task's receivers, after all of its pbar_{n-1} stores
+    if (do_b) {
+      const int beg = S.tile_ptr[loc], end = S.tile_ptr[loc + 1];
+      if (end > beg) {
+        __syncwarp();
+        for (int k = beg + lane; k < end; k += 32) {
+          const int rec = S.tile_rec[k];
+          const int oo = S.rec_off[rec];
+          atomicAdd(bn + oo, rec_scale * S.a[oo] * S.seis_t[(long long)n * S.nrec + rec]);
+        }
+      }
+    }
+    gc = c0 + nrow + 8;
+    ga = a0 + nrow;
+  }
+}
+
 // Per-shot max(den) on the interior (blockIdx.y = shot).
 __global__ void k_batch_max(BShot *shots, const int *ncols, int nz) {
   BShot &S = shots[blockIdx.y];
@@ -161,7 +461,9 @@ struct rbc_batch {
   int *d_ncols = nullptr;
   int *d_item_f = nullptr, *d_item_r = nullptr;
   int nitems_f = 0, nitems_r = 0;
-  int rzf = 4, rzr = 2;
+  int rzf = 4, rzr = 2;  // rows per warp (rzf == 0: the streaming forward kernel)
+  int *err_host = nullptr, *err_dev = nullptr;  // bounded waits that gave up (mapped)
+  float tune_ms[7] = {};  // per-launch ms of the candidates: forward 0/1/2/4 rows, reverse 1/2/0
   int grid_f = 0, grid_r = 0;
   int rec_cap = 0, tile_cap = 0;
   int *d_rec_off = nullptr, *d_tile_ptr = nullptr, *d_tile_rec = nullptr;
@@ -176,6 +478,9 @@ struct rbc_batch {
 };
 
 namespace {
+
+// z rows of a reverse work item (rzr == 0: the streaming kernel's warp task)
+int rev_tile_rows(const rbc_batch *b) { return b->rzr ? k2dWarps * b->rzr : kSZ; }
 
 int bfail(int code, const char *fmt, ...) {
   char buf[512];
@@ -207,8 +512,8 @@ int build_items(rbc_batch *b) {
   for (int s = 0; s < b->nshots; ++s) {
     BShot &S = b->hs[s];
     S.gx = cdiv(S.L.NX, kTileX);
-    S.gzf = cdiv(S.L.NZ, k2dWarps * b->rzf);
-    S.gzr = cdiv(S.L.NZ, k2dWarps * b->rzr);
+    S.gzf = b->rzf ? cdiv(S.L.NZ, k2dWarps * b->rzf) : cdiv(S.L.NZ, kSZ);
+    S.gzr = cdiv(S.L.NZ, rev_tile_rows(b));
     S.tbase_f = (int)itf.size();
     S.tbase_r = (int)itr.size();
     itf.insert(itf.end(), (size_t)S.gx * S.gzf, s);
@@ -227,11 +532,11 @@ int build_items(rbc_batch *b) {
 }
 
 template <typename K>
-int resident_grid(K kern, int items) {
+int resident_grid(K kern, int items, size_t smem = 0) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * k2dWarps, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * k2dWarps, smem);
   const int slots = std::max(1, sms) * std::max(1, per);
   return std::max(1, std::min(items, slots));
 }
@@ -240,6 +545,9 @@ bool launch_fwd_b(rbc_batch *b, int n, cudaStream_t s) {
   const dim3 blk(32, k2dWarps);
   const float sc = 1.0f;  // h^(2-d) in 2-D
   switch (b->rzf) {
+  case 0:
+    k_fwd2d_stream<<<b->grid_f, blk, kStreamSmem, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc, b->err_dev);
+    break;
   case 1: k_fwd2d_batch<1><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
   case 2: k_fwd2d_batch<2><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
   default: k_fwd2d_batch<4><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
@@ -251,6 +559,10 @@ bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s) {
   const dim3 blk(32, k2dWarps);
   const int nt = b->g.nt;
   switch (b->rzr) {
+  case 0:
+    k_rev2d_stream<<<b->grid_r, blk, kStreamSmemR, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f,
+                                                        b->err_dev);
+    break;
   case 1:
     k_rev2d_batch<1><<<b->grid_r, blk, 0, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f);
     break;
@@ -263,11 +575,16 @@ bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s) {
 
 void set_grids(rbc_batch *b) {
   switch (b->rzf) {
+  case 0: b->grid_f = resident_grid(k_fwd2d_stream, cdiv(b->nitems_f, k2dWarps), kStreamSmem); break;
   case 1: b->grid_f = resident_grid(k_fwd2d_batch<1>, b->nitems_f); break;
   case 2: b->grid_f = resident_grid(k_fwd2d_batch<2>, b->nitems_f); break;
   default: b->grid_f = resident_grid(k_fwd2d_batch<4>, b->nitems_f); break;
   }
-  b->grid_r = (b->rzr == 1) ? resident_grid(k_rev2d_batch<1>, b->nitems_r) : resident_grid(k_rev2d_batch<2>, b->nitems_r);
+  switch (b->rzr) {
+  case 0: b->grid_r = resident_grid(k_rev2d_stream, cdiv(b->nitems_r, k2dWarps), kStreamSmemR); break;
+  case 1: b->grid_r = resident_grid(k_rev2d_batch<1>, b->nitems_r); break;
+  default: b->grid_r = resident_grid(k_rev2d_batch<2>, b->nitems_r); break;
+  }
 }
 
 // Autotuner: time every rows-per-warp candidate of both kernels on the batch
@@ -289,22 +606,30 @@ int autotune(rbc_batch *b) {
   };
   int best_f = 4, best_r = 2;
   float tf = 1e30f, tr = 1e30f;
-  for (int rz : {1, 2, 4}) {
-    b->rzf = rz;
+  // RBC_BATCH_TILES="f,r" restricts the candidates (a tuning and test knob)
+  int force_f = -1, force_r = -1;
+  if (const char *env = getenv("RBC_BATCH_TILES")) sscanf(env, "%d,%d", &force_f, &force_r);
+  const int cf[4] = {0, 1, 2, 4}, cr[3] = {1, 2, 0};
+  for (int i = 0; i < 4; ++i) {
+    if (force_f >= 0 && cf[i] != force_f) continue;
+    b->rzf = cf[i];
     int rc = build_items(b);
     if (rc) return rc;
     BCK(cudaMemcpy(b->ds, b->hs.data(), sizeof(BShot) * b->nshots, cudaMemcpyHostToDevice));
     const float t = time_it(true);
-    if (t < tf) tf = t, best_f = rz;
+    b->tune_ms[i] = t / 20;
+    if (t < tf) tf = t, best_f = cf[i];
   }
   b->rzf = best_f;
-  for (int rz : {1, 2}) {
-    b->rzr = rz;
+  for (int i = 0; i < 3; ++i) {
+    if (force_r >= 0 && cr[i] != force_r) continue;
+    b->rzr = cr[i];
     int rc = build_items(b);
     if (rc) return rc;
     BCK(cudaMemcpy(b->ds, b->hs.data(), sizeof(BShot) * b->nshots, cudaMemcpyHostToDevice));
     const float t = time_it(false);
-    if (t < tr) tr = t, best_r = rz;
+    b->tune_ms[4 + i] = t / 20;
+    if (t < tr) tr = t, best_r = cr[i];
   }
   b->rzr = best_r;
   cudaEventDestroy(e0);
@@ -385,6 +710,14 @@ int rbc_batch_create(const rbc_grid *g, int nshots, const int *nx_host, const fl
   b->nshots = nshots;
   const char *env = getenv("RBC_GRAPH");
   b->use_graph = !(env && env[0] == '0');
+  cudaFuncSetAttribute(k_fwd2d_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
+  cudaFuncSetAttribute(k_rev2d_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmemR);
+  if (cudaHostAlloc((void **)&b->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&b->err_dev, b->err_host, 0) != cudaSuccess) {
+    delete b;
+    return bfail(RBC_ENOMEM, "rbc_batch_create: error word allocation failed");
+  }
+  *b->err_host = 0;
   size_t total = 0;
   for (int s = 0; s < nshots; ++s) {
     if (nx_host[s] < 1 || !a_dev[s]) {
@@ -485,8 +818,11 @@ int rbc_batch_destroy(rbc_batch *b) {
   cudaFree(b->d_wav);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  const bool timed_out = b->err_host && *(volatile int *)b->err_host;
+  if (b->err_host) cudaFreeHost(b->err_host);
   delete b;
-  return RBC_OK;
+  return timed_out ? bfail(RBC_ETIMEOUT, "rbc_batch_destroy: a bounded wait gave up; the last results are invalid")
+                   : RBC_OK;
 }
 
 int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev, int flags, float eps_rel,
@@ -494,6 +830,10 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
   if (!b || !shots || !wavelet_dev || !image_dev) return bfail(RBC_EINVAL, "rbc_batch_rtm: NULL argument");
   if (flags != RBC_REINJECT_SOURCE) return bfail(RBC_EINVAL, "rbc_batch_rtm: flags must be RBC_REINJECT_SOURCE");
   if (!(eps_rel >= 0)) return bfail(RBC_EINVAL, "rbc_batch_rtm: eps_rel must be >= 0");
+  if (*(volatile int *)b->err_host) {
+    *(volatile int *)b->err_host = 0;
+    return bfail(RBC_ETIMEOUT, "rbc_batch_rtm: a bounded wait of an earlier call gave up; its results are invalid");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int nt = b->g.nt;
   // receiver tables of every shot (counting sort by reverse tile)
@@ -510,7 +850,7 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
       return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d has a bad receiver list", i);
     auto inside = [&](const int *r) { return r[0] >= 0 && r[0] < L.NX && r[1] == 0 && r[2] >= 0 && r[2] < L.NZ; };
     if (!inside(sh.src)) return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d source outside its grid", i);
-    const int gx = cdiv(L.NX, kTileX), gz = cdiv(L.NZ, k2dWarps * b->rzr);
+    const int gx = cdiv(L.NX, kTileX), gz = cdiv(L.NZ, rev_tile_rows(b));
     rec_base[i] = (int)off.size();
     ptr_base[i] = (int)ptr.size();
     std::vector<int> cnt(gx * gz + 1, 0), tile(sh.nrec);
@@ -518,7 +858,7 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
       const int *q = sh.rec_host + 3 * r;
       if (!inside(q)) return bfail(RBC_EINVAL, "rbc_batch_rtm: shot %d receiver %d outside its grid", i, r);
       off.push_back(lay_off(L, q[0], 0, q[2]));
-      tile[r] = (q[2] / (k2dWarps * b->rzr)) * gx + q[0] / kTileX;
+      tile[r] = (q[2] / rev_tile_rows(b)) * gx + q[0] / kTileX;
       cnt[tile[r] + 1]++;
     }
     for (int t = 0; t < gx * gz; ++t) cnt[t + 1] += cnt[t];
@@ -633,6 +973,7 @@ int rbc_batch_info(const rbc_batch *b, int *out) {
   out[3] = b->nitems_r;
   out[4] = b->grid_f;
   out[5] = b->grid_r;
+  for (int i = 0; i < 7; ++i) out[6 + i] = (int)(b->tune_ms[i] * 1000.0f + 0.5f);  // microseconds
   return RBC_OK;
 }
 

@@ -26,8 +26,13 @@ def _window(v, off, width):
     return np.ascontiguousarray(v[:, off:off + width])
 
 
-def test_batch_matches_single_shots_and_oracle():
+# every forward kernel the autotuner can pick (0 = the streaming kernel) and
+# both reverse shapes, forced one pair at a time, and the tuner's own choice
+@pytest.mark.parametrize("tiles", [None, "0,0", "4,2"])
+def test_batch_matches_single_shots_and_oracle(tiles, monkeypatch):
     import paper_2204_03380_gb300 as R
+    if tiles is not None:
+        monkeypatch.setenv("RBC_BATCH_TILES", tiles)
     w, inp = _small_batch()
     dev = "cuda"
     wav = torch.tensor(inp["wavelet"], dtype=torch.float32, device=dev)
@@ -47,7 +52,9 @@ def test_batch_matches_single_shots_and_oracle():
     # batched path
     b = R.rbc_batch_create(_shot_grid(R, w, 1), [sh["width"] for sh in inp["shots"]], a_mig)
     info = R.rbc_batch_info(b)
-    assert info["rows_fwd"] in (1, 2, 4) and info["rows_rev"] in (1, 2)
+    assert info["rows_fwd"] in (0, 1, 2, 4) and info["rows_rev"] in (0, 1, 2)
+    if tiles is not None:
+        assert [info["rows_fwd"], info["rows_rev"]] == [int(v) for v in tiles.split(",")]
     img_b = torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)
     shots = [dict(src=sh["src"], rec=sh["rec"], seis=d, off_x=sh["off_x"]) for sh, d in zip(inp["shots"], seis)]
     R.rbc_batch_rtm(b, shots, wav, R.RBC_REINJECT_SOURCE, 1e-6, img_b)
