@@ -33,7 +33,7 @@ constexpr int kTYf = RBC_FWD3D_ROWS;  // y rows per forward tile (one warp each)
 constexpr int kRP = 8;        // forward P ring: 5 live planes + 3 in flight
 constexpr int kRT = 5;        // forward T ring: 1 live plane + 4 in flight
 constexpr int kRPr = 8;       // reverse P ring (two fields): 5 live + 3 in flight
-constexpr int kRTr = 3;       // reverse T ring (a, p^R, pbar, num, den): 1 live + 2 in flight
+constexpr int kRTr = 4;       // reverse T ring (a, p^R, pbar, num, den): 1 live + 3 in flight
 constexpr int kHaloW = 136;   // 128 + 2 x 4 halo floats
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
