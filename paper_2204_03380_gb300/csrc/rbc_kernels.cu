@@ -71,14 +71,15 @@ __device__ __forceinline__ void inject_receivers(const RevArgs &A, int bid) {
 }
 
 // ------------------------------------------------------------------ 2-D ----
-// Block: 32 x k2dWarps threads; tile 128 (x) x k2dWarps*RZ (z); each warp
-// marches RZ rows with a (RZ + 8)-deep register queue.
+// Block: 32 x k2dWarpsF (forward) or 32 x k2dWarps (reverse) threads; tile
+// 128 (x) x warps*RZ (z); each warp marches RZ rows with an (RZ + 8)-deep
+// register queue.
 template <int RZ>
-__global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d(const StepArgs A) {
+__global__ void __launch_bounds__(32 * k2dWarpsF) k_fwd2d(const StepArgs A) {
   const Lay &L = A.L;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int x0 = blockIdx.x * kTileX + lane * 4;
-  const int zb = (blockIdx.y * k2dWarps + w) * RZ;
+  const int zb = (blockIdx.y * k2dWarpsF + w) * RZ;
   griddep_wait();
   if (A.sample) sample_receivers(A, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
   if (zb < L.NZ)  // warp-uniform; no block barrier in this kernel
@@ -138,8 +139,8 @@ static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 bool launch_fwd(const StepArgs &A, cudaStream_t s) {
   const Lay &L = A.L;
   if (L.ndim == 3) return launch_fwd3d(A, s);
-  dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarps * k2dRowsF));
-  launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarps), 0, s, A);
+  dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarpsF * k2dRowsF));
+  launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarpsF), 0, s, A);
   return true;
 }
 
