@@ -99,7 +99,8 @@ struct RevArgs {
 
 // ---- launch geometry shared by the host (CSR) and the kernels ----
 constexpr int k2dWarps = 8;   // warps per block, stacked in z (2-D reverse and batched kernels)
-constexpr int k2dWarpsF = 4;  // warps per block of the single-shot 2-D forward kernel (swept: 4, 8)
+constexpr int k2dWarpsF = 4;  // warps per block of the single-shot 2-D forward kernel (swept: 2, 4, 8)
+constexpr int k2dWarpsR = 8;  // warps per block of the single-shot 2-D reverse kernel (swept: 6, 8, 16)
 constexpr int k2dRowsF = 2;   // rows per warp, forward kernel (swept on GB300: 1, 2, 4, 8)
 constexpr int k2dRowsR = 2;   // rows per warp, reverse kernel (swept: 1, 2, 3, 4)
 constexpr int k3dBY = 16;     // y rows covered by the layout's row padding (3-D)

@@ -71,7 +71,7 @@ __device__ __forceinline__ void inject_receivers(const RevArgs &A, int bid) {
 }
 
 // ------------------------------------------------------------------ 2-D ----
-// Block: 32 x k2dWarpsF (forward) or 32 x k2dWarps (reverse) threads; tile
+// Block: 32 x k2dWarpsF (forward) or 32 x k2dWarpsR (reverse) threads; tile
 // 128 (x) x warps*RZ (z); each warp marches RZ rows with an (RZ + 8)-deep
 // register queue.
 template <int RZ>
@@ -88,11 +88,11 @@ __global__ void __launch_bounds__(32 * k2dWarpsF) k_fwd2d(const StepArgs A) {
 }
 
 template <int RZ, bool kGrad>
-__global__ void __launch_bounds__(32 * k2dWarps) k_rev2d(const RevArgs A) {
+__global__ void __launch_bounds__(32 * k2dWarpsR) k_rev2d(const RevArgs A) {
   const Lay &L = A.L;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int x0 = blockIdx.x * kTileX + lane * 4;
-  const int zb = (blockIdx.y * k2dWarps + w) * RZ;
+  const int zb = (blockIdx.y * k2dWarpsR + w) * RZ;
   const bool xok = x0 < L.NX4;
   const bool active = zb < L.NZ;  // warp-uniform
   griddep_wait();
@@ -147,9 +147,9 @@ bool launch_fwd(const StepArgs &A, cudaStream_t s) {
 void rev_tiling(const Lay &L, int zc, int *gx, int *gy, int *gz, int *t) {
   if (L.ndim == 2) {
     *gx = cdiv(L.NX, kTileX);
-    *gy = cdiv(L.NZ, k2dWarps * k2dRowsR);
+    *gy = cdiv(L.NZ, k2dWarpsR * k2dRowsR);
     *gz = 1;
-    *t = k2dWarps * k2dRowsR;
+    *t = k2dWarpsR * k2dRowsR;
   } else {
     *gx = cdiv(L.NX, kTileX);
     *gy = cdiv(L.NY, tile_rows_3d());
@@ -163,9 +163,9 @@ bool launch_rev(const RevArgs &A, cudaStream_t s) {
   int gx, gy, gz, t;
   rev_tiling(A.L, A.zc, &gx, &gy, &gz, &t);
   if (A.mode == 1)
-    launch_pdl(k_rev2d<k2dRowsR, true>, dim3(gx, gy), dim3(32, k2dWarps), 0, s, A);
+    launch_pdl(k_rev2d<k2dRowsR, true>, dim3(gx, gy), dim3(32, k2dWarpsR), 0, s, A);
   else
-    launch_pdl(k_rev2d<k2dRowsR, false>, dim3(gx, gy), dim3(32, k2dWarps), 0, s, A);
+    launch_pdl(k_rev2d<k2dRowsR, false>, dim3(gx, gy), dim3(32, k2dWarpsR), 0, s, A);
   return true;
 }
 
