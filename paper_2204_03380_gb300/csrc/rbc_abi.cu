@@ -125,7 +125,7 @@ struct rbc_ctx {
   std::vector<cudaEvent_t> ev;  // three events per timed shot
   std::vector<cudaEvent_t> ev_free;
   bool use_graph = true;
-  int zc = k3dZC;  // z planes per block of the 3-D kernels
+  int zc = k3dZC, zc_r = k3dZC;  // z planes per tile of the 3-D forward / reverse kernels
   // snapshots
   std::vector<int> snap;
   float *pf = nullptr, *pr = nullptr, *pb = nullptr;
@@ -206,7 +206,7 @@ int upload_shot(rbc_ctx *c, const int *src, int nrec, const int *rec, int reinje
   info.fault = c->fault;
   c->fault = 0;
   int gx, gy, gz, t;
-  rev_tiling(L, c->zc, &gx, &gy, &gz, &t);
+  rev_tiling(L, c->zc_r, &gx, &gy, &gz, &t);
   std::vector<int> off(std::max(nrec, 1)), tile(std::max(nrec, 1)), ptr(c->ntiles + 1, 0),
       order(std::max(nrec, 1));
   for (int r = 0; r < nrec; ++r) {
@@ -214,7 +214,7 @@ int upload_shot(rbc_ctx *c, const int *src, int nrec, const int *rec, int reinje
     off[r] = lay_off(L, x, y, z);
     int b;
     if (L.ndim == 2) b = (z / t) * gx + x / kTileX;
-    else b = (((z / c->zc) * gy + y / t) * gx + x / kTileX) * t + y % t;  // (tile, row) cells
+    else b = (((z / c->zc_r) * gy + y / t) * gx + x / kTileX) * t + y % t;  // (tile, row) cells
     tile[r] = b;
     ptr[b + 1]++;
   }
@@ -310,7 +310,7 @@ int enqueue_reverse(rbc_ctx *c, cudaStream_t s) {
   A.iz1 = top + c->g.nz;
   A.iy0 = (L.ndim == 3) ? nb : 0;
   A.iy1 = (L.ndim == 3) ? nb + c->g.ny : 1;
-  A.zc = c->zc;
+  A.zc = c->zc_r;
   A.err = c->err_dev;
   const int nt = c->g.nt;
   for (int n = nt; n >= 0; --n) {
@@ -377,7 +377,7 @@ int enq_fwi_adj(rbc_ctx *c, cudaStream_t s, int) {
   A.iz1 = nb + c->g.nz;
   A.iy0 = 0;
   A.iy1 = 1;
-  A.zc = c->zc;
+  A.zc = c->zc_r;
   A.err = c->err_dev;
   A.mode = 1;
   const int nt = c->g.nt;
@@ -574,7 +574,11 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   const char *env = getenv("RBC_GRAPH");
   c->use_graph = !(env && env[0] == '0');
   const char *zenv = getenv("RBC_ZC");  // tuning knob: z planes per 3-D block
-  if (zenv && atoi(zenv) >= 8) c->zc = atoi(zenv);
+  if (L.ndim == 3) {
+    c->zc = zc_for_3d(L, true);
+    c->zc_r = zc_for_3d(L, false);
+  }
+  if (zenv && atoi(zenv) >= 8) c->zc = c->zc_r = atoi(zenv);
   const size_t fb = sizeof(float) * (size_t)L.total;
   cudaError_t ea = cudaMalloc(&c->buf, 7 * fb);
   if (ea != cudaSuccess) {
@@ -589,7 +593,7 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   c->num = c->buf + 5 * L.total;
   c->den = c->buf + 6 * L.total;
   int gx, gy, gz, t;
-  rev_tiling(L, c->zc, &gx, &gy, &gz, &t);
+  rev_tiling(L, c->zc_r, &gx, &gy, &gz, &t);
   c->ntiles = gx * gy * gz * (L.ndim == 3 ? t : 1);  // 3-D: one receiver list per (tile, row)
   if (cudaHostAlloc((void **)&c->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer((void **)&c->err_dev, c->err_host, 0) != cudaSuccess) {

@@ -116,6 +116,7 @@ bool launch_rev(const RevArgs &A, cudaStream_t s);
 bool launch_fwd3d(const StepArgs &A, cudaStream_t s);
 bool launch_rev3d(const RevArgs &A, cudaStream_t s);
 int tile_rows_3d();
+int zc_for_3d(const Lay &L, bool fwd);  // z planes per tile of the forward / reverse 3-D kernel
 void *tmap_encode_fn();  // cuTensorMapEncodeTiled from the driver, or NULL
 void rev_tiling(const Lay &L, int zc, int *gx, int *gy, int *gz, int *tz_or_by);
 void launch_copy_in(const Lay &L, const float *dense, float *pitched, cudaStream_t s);

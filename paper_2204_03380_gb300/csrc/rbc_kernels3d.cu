@@ -542,6 +542,26 @@ void *tmap_encode_fn() { return reinterpret_cast<void *>(encode_fn()); }
 
 int tile_rows_3d() { return kTY; }
 
+// z planes per tile of the 3-D kernels for this grid: with one persistent
+// block per SM, the busiest block streams ceil(tiles / SMs) tiles of zc + 8
+// planes each (8 halo planes per tile), so take the chunking that minimises
+// that product (on 580 x 580 x 380: 95 planes forward, 190 reverse).
+int zc_for_3d(const Lay &L, bool fwd) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+  const long long per = (long long)cdiv(L.NX, kTileX) * cdiv(L.NY, fwd ? RBC_FWD3D_ROWS : kTY);
+  int best = k3dZC;
+  long long best_cost = -1;
+  for (int c = 1; c <= cdiv(L.NZ, 16); ++c) {
+    const int zc = cdiv(L.NZ, c);
+    const long long cost = ((per * c + sms - 1) / sms) * (zc + 8);
+    if (best_cost < 0 || cost < best_cost) best_cost = cost, best = zc;
+  }
+  return best;
+}
+
 // The pitched buffers start at their allocation; tensor coordinates are the
 // padded node plus (32, 4, 4).  Field pointers passed in StepArgs/RevArgs are
 // buffer starts (the kernels add L.origin for plain loads and stores).
