@@ -275,8 +275,12 @@ int rbc_batch_destroy(rbc_batch *b);
  * work list of (shot, tile) items; then, per shot, I = num / (den + eps_rel
  * max den) (Eq. 3) is stacked into image_dev (nz, survey_nx) at column off_x
  * (+=, shots may overlap).  shots: nshots descriptors (host); flags must be
- * RBC_REINJECT_SOURCE.  Both time loops run as CUDA graphs captured on the
- * first call and replayed afterwards.
+ * RBC_REINJECT_SOURCE.  The shots run in groups of consecutive shots whose
+ * seven fields fit an L2 budget (environment RBC_BATCH_L2MB, megabytes,
+ * default 96; 0 = one group), each group's forward then reverse phase, so
+ * that a group's fields stay in L2 through its time loops.  Each phase of
+ * each group runs as a CUDA graph captured on the first call and replayed
+ * afterwards.
  * Errors: RBC_EINVAL (window, nodes, flags), RBC_ENOMEM, RBC_ECUDA.
  */
 int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
@@ -288,11 +292,12 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
  * reverse ms, forward launches, reverse launches, calls). */
 int rbc_batch_timing(rbc_batch *b, int enable, double *out);
 
-/* rbc_batch_info -- out[0..12]: forward and reverse rows per warp chosen by
+/* rbc_batch_info -- out[0..13]: forward and reverse rows per warp chosen by
  * the autotuner (0 = the streaming kernels), work items of both kernels,
  * their grids, then the measured per-launch time in microseconds of every
- * candidate: forward streaming / 1 / 2 / 4 rows, reverse 1 / 2 rows /
- * streaming (0 where a candidate was not timed).  Host only. */
+ * candidate on the first shot group: forward streaming / 1 / 2 / 4 rows,
+ * reverse 1 / 2 rows / streaming (0 where a candidate was not timed), then
+ * the number of shot groups.  Host only. */
 int rbc_batch_info(const rbc_batch *b, int *out);
 
 /* ------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 // warp of the forward and reverse kernels are chosen at creation by timing
 // the candidates on the batch itself.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -46,36 +47,48 @@ struct BShot {
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// warps per block of the tiled forward kernel (the single-shot forward kernel
+// runs 4 as well; the reverse and streaming kernels run k2dWarps)
+constexpr int kBWarpsF = 4;
+
 // ---------------------------------------------------------------- kernels --
 template <int RZ>
-__global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d_batch(const BShot *__restrict__ shots,
-                                                                const int *__restrict__ item_shot, int nitems,
-                                                                int n, const float *__restrict__ wav,
+__global__ void __launch_bounds__(32 * kBWarpsF) k_fwd2d_batch(const BShot *__restrict__ shots,
+                                                                const int *__restrict__ item_shot, int item0,
+                                                                int item1, int n, const float *__restrict__ wav,
                                                                 float src_scale) {
   const int lane = threadIdx.x, w = threadIdx.y;
+  griddep_wait();
   const float f = wav[n] * src_scale;
-  for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-    const BShot &S = shots[item_shot[t]];
+  // the next item's shot index is fetched one item ahead
+  int sh = item0 + (int)blockIdx.x < item1 ? __ldg(item_shot + item0 + blockIdx.x) : 0;
+  for (int t = item0 + blockIdx.x; t < item1; t += gridDim.x) {
+    const BShot &S = shots[sh];
+    sh = t + (int)gridDim.x < item1 ? __ldg(item_shot + t + gridDim.x) : 0;
     const int loc = t - S.tbase_f;
     const int bx = loc % S.gx, bz = loc / S.gx;
-    const int zb = (bz * k2dWarps + w) * RZ;
+    const int zb = (bz * kBWarpsF + w) * RZ;
     if (zb >= S.L.NZ) continue;  // warp-uniform
     const float *cur = (n & 1) ? S.p1 : S.p0;
     float *nxt = (n & 1) ? S.p0 : S.p1;
     fwd2d_rows<RZ>(S.L, S.a, cur, nxt, lane, bx * kTileX + lane * 4, zb, S.src_off, f);
   }
+  griddep_launch();
 }
 
 template <int RZ>
 __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__restrict__ shots,
-                                                                const int *__restrict__ item_shot, int nitems,
-                                                                int n, int nt, const float *__restrict__ wav,
+                                                                const int *__restrict__ item_shot, int item0,
+                                                                int item1, int n, int nt, const float *__restrict__ wav,
                                                                 float src_scale, float rec_scale) {
   const int lane = threadIdx.x, w = threadIdx.y;
   const bool do_r = n < nt && n > 0, do_b = n > 0;
+  griddep_wait();
   const float fsrc = do_r ? wav[n] * src_scale : 0.f;  // f[nt] does not exist
-  for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
-    const BShot &S = shots[item_shot[t]];
+  int sh = item0 + (int)blockIdx.x < item1 ? __ldg(item_shot + item0 + blockIdx.x) : 0;
+  for (int t = item0 + blockIdx.x; t < item1; t += gridDim.x) {
+    const BShot &S = shots[sh];
+    sh = t + (int)gridDim.x < item1 ? __ldg(item_shot + t + gridDim.x) : 0;
     const Lay &L = S.L;
     const int loc = t - S.tbase_r;
     const int bx = loc % S.gx, bz = loc / S.gx;
@@ -118,6 +131,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
       }
     }
   }
+  griddep_launch();
 }
 
 // Streaming form of the forward step for DRAM-bound batches: every warp owns
@@ -158,8 +172,8 @@ __device__ __forceinline__ void s_expect(uint64_t *b, uint32_t bytes) {
 }
 
 __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d_stream(const BShot *__restrict__ shots,
-                                                                 const int *__restrict__ item_shot, int nitems,
-                                                                 int n, const float *__restrict__ wav,
+                                                                 const int *__restrict__ item_shot, int item0,
+                                                                 int item1, int n, const float *__restrict__ wav,
                                                                  float src_scale, int *err) {
   extern __shared__ __align__(128) float sm_s[];
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -174,10 +188,11 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d_stream(const BShot *__r
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
+  griddep_wait();
   const float f = wav[n] * src_scale;
   int gc = 0, ga = 0;  // copies issued so far into the p^n / (a, p^{n-1}) rings
   bool ok = true;
-  for (int t = blockIdx.x * k2dWarps + w; ok && t < nitems; t += gridDim.x * k2dWarps) {
+  for (int t = item0 + blockIdx.x * k2dWarps + w; ok && t < item1; t += gridDim.x * k2dWarps) {
     const BShot &S = shots[item_shot[t]];
     const Lay &L = S.L;
     const int loc = t - S.tbase_f;
@@ -264,6 +279,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_fwd2d_stream(const BShot *__r
     gc = c0 + nrow + 8;
     ga = a0 + nrow;
   }
+  griddep_launch();
 }
 
 // Streaming form of the fused reverse step (Eqs. 6, 2 and 3): the same
@@ -277,8 +293,8 @@ constexpr size_t kStreamSmemR =
     sizeof(float) * kSWarpR * k2dWarps + sizeof(uint64_t) * (2 * kSRr + kSAr) * k2dWarps;
 
 __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_stream(const BShot *__restrict__ shots,
-                                                                 const int *__restrict__ item_shot, int nitems,
-                                                                 int n, int nt, const float *__restrict__ wav,
+                                                                 const int *__restrict__ item_shot, int item0,
+                                                                 int item1, int n, int nt, const float *__restrict__ wav,
                                                                  float src_scale, float rec_scale, int *err) {
   extern __shared__ __align__(128) float sm_r[];
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -293,11 +309,12 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_stream(const BShot *__r
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
+  griddep_wait();
   const bool do_r = n < nt && n > 0, do_b = n > 0;
   const float fsrc = do_r ? wav[n] * src_scale : 0.f;  // f[nt] does not exist
   int gc = 0, ga = 0;
   bool ok = true;
-  for (int t = blockIdx.x * k2dWarps + w; ok && t < nitems; t += gridDim.x * k2dWarps) {
+  for (int t = item0 + blockIdx.x * k2dWarps + w; ok && t < item1; t += gridDim.x * k2dWarps) {
     const BShot &S = shots[item_shot[t]];
     const Lay &L = S.L;
     const int loc = t - S.tbase_r;
@@ -418,6 +435,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_stream(const BShot *__r
     gc = c0 + nrow + 8;
     ga = a0 + nrow;
   }
+  griddep_launch();
 }
 
 // Per-shot max(den) on the interior (blockIdx.y = shot).
@@ -470,11 +488,14 @@ struct rbc_batch {
   float *d_seis_t = nullptr;
   float *d_wav = nullptr;
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  long long gnodes[2] = {0, 0};
+  // shots migrated together, so that a group's fields stay in L2 for its whole
+  // time loop: group g = shots grp[g] .. grp[g+1]-1
+  std::vector<int> grp;
+  std::vector<cudaGraphExec_t> gexec;  // [kind * groups + g], kind 0 forward, 1 reverse
   bool use_graph = true;
   bool timing = false;
-  std::vector<cudaEvent_t> ev;  // three per timed call
+  std::vector<cudaEvent_t> ev;  // three per group of every timed call
+  int timed_calls = 0;
 };
 
 namespace {
@@ -500,7 +521,7 @@ int bfail(int code, const char *fmt, ...) {
   } while (0)
 
 void drop_graphs(rbc_batch *b) {
-  for (int k = 0; k < 2; ++k) {
+  for (size_t k = 0; k < b->gexec.size(); ++k) {
     if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
     b->gexec[k] = nullptr;
   }
@@ -512,7 +533,7 @@ int build_items(rbc_batch *b) {
   for (int s = 0; s < b->nshots; ++s) {
     BShot &S = b->hs[s];
     S.gx = cdiv(S.L.NX, kTileX);
-    S.gzf = b->rzf ? cdiv(S.L.NZ, k2dWarps * b->rzf) : cdiv(S.L.NZ, kSZ);
+    S.gzf = b->rzf ? cdiv(S.L.NZ, kBWarpsF * b->rzf) : cdiv(S.L.NZ, kSZ);
     S.gzr = cdiv(S.L.NZ, rev_tile_rows(b));
     S.tbase_f = (int)itf.size();
     S.tbase_r = (int)itr.size();
@@ -532,42 +553,64 @@ int build_items(rbc_batch *b) {
 }
 
 template <typename K>
-int resident_grid(K kern, int items, size_t smem = 0) {
+int resident_grid(K kern, int items, size_t smem = 0, int warps = k2dWarps) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * k2dWarps, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * warps, smem);
   const int slots = std::max(1, sms) * std::max(1, per);
   return std::max(1, std::min(items, slots));
 }
 
-bool launch_fwd_b(rbc_batch *b, int n, cudaStream_t s) {
+// Work items [i0, i1) of a time step (all items by default).  The persistent
+// grid shrinks to the items when a group has fewer than the resident slots.
+bool launch_fwd_b(rbc_batch *b, int n, cudaStream_t s, int i0 = 0, int i1 = -1) {
+  if (i1 < 0) i1 = b->nitems_f;
   const dim3 blk(32, k2dWarps);
   const float sc = 1.0f;  // h^(2-d) in 2-D
+  const int items = i1 - i0;
   switch (b->rzf) {
-  case 0:
-    k_fwd2d_stream<<<b->grid_f, blk, kStreamSmem, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc, b->err_dev);
+  case 0: {
+    const int gr = std::max(1, std::min(b->grid_f, cdiv(items, k2dWarps)));
+    launch_pdl(k_fwd2d_stream, dim3(gr), blk, kStreamSmem, s, (const BShot *)b->ds, (const int *)b->d_item_f, i0, i1,
+               n, (const float *)b->d_wav, sc, b->err_dev);
     break;
-  case 1: k_fwd2d_batch<1><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
-  case 2: k_fwd2d_batch<2><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
-  default: k_fwd2d_batch<4><<<b->grid_f, blk, 0, s>>>(b->ds, b->d_item_f, b->nitems_f, n, b->d_wav, sc); break;
+  }
+  case 1:
+    launch_pdl(k_fwd2d_batch<1>, dim3(std::min(b->grid_f, items)), dim3(32, kBWarpsF), 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_f, i0, i1, n, (const float *)b->d_wav, sc);
+    break;
+  case 2:
+    launch_pdl(k_fwd2d_batch<2>, dim3(std::min(b->grid_f, items)), dim3(32, kBWarpsF), 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_f, i0, i1, n, (const float *)b->d_wav, sc);
+    break;
+  default:
+    launch_pdl(k_fwd2d_batch<4>, dim3(std::min(b->grid_f, items)), dim3(32, kBWarpsF), 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_f, i0, i1, n, (const float *)b->d_wav, sc);
+    break;
   }
   return cudaPeekAtLastError() == cudaSuccess;
 }
 
-bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s) {
+bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s, int i0 = 0, int i1 = -1) {
+  if (i1 < 0) i1 = b->nitems_r;
   const dim3 blk(32, k2dWarps);
   const int nt = b->g.nt;
+  const int items = i1 - i0;
   switch (b->rzr) {
-  case 0:
-    k_rev2d_stream<<<b->grid_r, blk, kStreamSmemR, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f,
-                                                        b->err_dev);
+  case 0: {
+    const int gr = std::max(1, std::min(b->grid_r, cdiv(items, k2dWarps)));
+    launch_pdl(k_rev2d_stream, dim3(gr), blk, kStreamSmemR, s, (const BShot *)b->ds, (const int *)b->d_item_r, i0,
+               i1, n, nt, (const float *)b->d_wav, 1.f, 1.f, b->err_dev);
     break;
+  }
   case 1:
-    k_rev2d_batch<1><<<b->grid_r, blk, 0, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f);
+    launch_pdl(k_rev2d_batch<1>, dim3(std::min(b->grid_r, items)), blk, 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_r, i0, i1, n, nt, (const float *)b->d_wav, 1.f, 1.f);
     break;
   default:
-    k_rev2d_batch<2><<<b->grid_r, blk, 0, s>>>(b->ds, b->d_item_r, b->nitems_r, n, nt, b->d_wav, 1.f, 1.f);
+    launch_pdl(k_rev2d_batch<2>, dim3(std::min(b->grid_r, items)), blk, 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_r, i0, i1, n, nt, (const float *)b->d_wav, 1.f, 1.f);
     break;
   }
   return cudaPeekAtLastError() == cudaSuccess;
@@ -576,9 +619,9 @@ bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s) {
 void set_grids(rbc_batch *b) {
   switch (b->rzf) {
   case 0: b->grid_f = resident_grid(k_fwd2d_stream, cdiv(b->nitems_f, k2dWarps), kStreamSmem); break;
-  case 1: b->grid_f = resident_grid(k_fwd2d_batch<1>, b->nitems_f); break;
-  case 2: b->grid_f = resident_grid(k_fwd2d_batch<2>, b->nitems_f); break;
-  default: b->grid_f = resident_grid(k_fwd2d_batch<4>, b->nitems_f); break;
+  case 1: b->grid_f = resident_grid(k_fwd2d_batch<1>, b->nitems_f, 0, kBWarpsF); break;
+  case 2: b->grid_f = resident_grid(k_fwd2d_batch<2>, b->nitems_f, 0, kBWarpsF); break;
+  default: b->grid_f = resident_grid(k_fwd2d_batch<4>, b->nitems_f, 0, kBWarpsF); break;
   }
   switch (b->rzr) {
   case 0: b->grid_r = resident_grid(k_rev2d_stream, cdiv(b->nitems_r, k2dWarps), kStreamSmemR); break;
@@ -587,17 +630,23 @@ void set_grids(rbc_batch *b) {
   }
 }
 
-// Autotuner: time every rows-per-warp candidate of both kernels on the batch
-// itself (zero fields, no receivers) and keep the fastest.
+void group_items(const rbc_batch *b, int g, bool fwd, int *i0, int *i1);
+
+// Autotuner: time every rows-per-warp candidate of both kernels on the first
+// shot group of the batch itself (zero fields, no receivers), as the time
+// loop runs it, and keep the fastest.
 int autotune(rbc_batch *b) {
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   auto time_it = [&](bool fwd) -> float {
     set_grids(b);
-    for (int k = 0; k < 3; ++k) fwd ? launch_fwd_b(b, 10, 0) : launch_rev_b(b, 10, 0);
+    int i0, i1;
+    group_items(b, 0, fwd, &i0, &i1);
+    auto go = [&](int n) { fwd ? launch_fwd_b(b, n, 0, i0, i1) : launch_rev_b(b, n, 0, i0, i1); };
+    for (int k = 0; k < 3; ++k) go(10);
     cudaEventRecord(e0, 0);
-    for (int k = 0; k < 20; ++k) fwd ? launch_fwd_b(b, 10 + (k & 1), 0) : launch_rev_b(b, 10 + (k & 1), 0);
+    for (int k = 0; k < 20; ++k) go(10 + (k & 1));
     cudaEventRecord(e1, 0);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -642,39 +691,54 @@ int autotune(rbc_batch *b) {
   return RBC_OK;
 }
 
-int enq_fwd(rbc_batch *b, cudaStream_t s) {
-  for (int i = 0; i < b->nshots; ++i) {
+// Work items of group g: the items of its shots are contiguous in both lists.
+void group_items(const rbc_batch *b, int g, bool fwd, int *i0, int *i1) {
+  const BShot &f = b->hs[b->grp[g]], &l = b->hs[b->grp[g + 1] - 1];
+  *i0 = fwd ? f.tbase_f : f.tbase_r;
+  *i1 = fwd ? l.tbase_f + l.gx * l.gzf : l.tbase_r + l.gx * l.gzr;
+}
+
+int enq_fwd(rbc_batch *b, int g, cudaStream_t s) {
+  for (int i = b->grp[g]; i < b->grp[g + 1]; ++i) {
     const size_t bytes = sizeof(float) * (size_t)b->L[i].total;
     BCK(cudaMemsetAsync(b->hs[i].p0, 0, bytes, s));
     BCK(cudaMemsetAsync(b->hs[i].p1, 0, bytes, s));
   }
+  int i0, i1;
+  group_items(b, g, true, &i0, &i1);
   for (int n = 0; n < b->g.nt; ++n)
-    if (!launch_fwd_b(b, n, s)) return bfail(RBC_ECUDA, "batched forward launch failed");
+    if (!launch_fwd_b(b, n, s, i0, i1)) return bfail(RBC_ECUDA, "batched forward launch failed");
   return RBC_OK;
 }
 
-int enq_rev(rbc_batch *b, cudaStream_t s) {
-  for (int i = 0; i < b->nshots; ++i) {
+int enq_rev(rbc_batch *b, int g, cudaStream_t s) {
+  for (int i = b->grp[g]; i < b->grp[g + 1]; ++i) {
     const size_t bytes = sizeof(float) * (size_t)b->L[i].total;
     BCK(cudaMemsetAsync(b->hs[i].q0, 0, bytes, s));
     BCK(cudaMemsetAsync(b->hs[i].q1, 0, bytes, s));
     BCK(cudaMemsetAsync(b->hs[i].num, 0, bytes, s));
     BCK(cudaMemsetAsync(b->hs[i].den, 0, bytes, s));
   }
+  int i0, i1;
+  group_items(b, g, false, &i0, &i1);
   for (int n = b->g.nt; n >= 0; --n)
-    if (!launch_rev_b(b, n, s)) return bfail(RBC_ECUDA, "batched reverse launch failed");
+    if (!launch_rev_b(b, n, s, i0, i1)) return bfail(RBC_ECUDA, "batched reverse launch failed");
   return RBC_OK;
 }
 
-int run_b(rbc_batch *b, int kind, cudaStream_t s, long long *launches) {
+// One phase (kind 0 forward, 1 reverse) of group g, as its cached graph.
+int run_b(rbc_batch *b, int kind, int g, cudaStream_t s, long long *launches) {
   const long long per = kind == 0 ? b->g.nt : b->g.nt + 1;
   if (!b->use_graph) {
     *launches += per;
-    return kind == 0 ? enq_fwd(b, s) : enq_rev(b, s);
+    return kind == 0 ? enq_fwd(b, g, s) : enq_rev(b, g, s);
   }
-  if (!b->gexec[kind]) {
+  const int ng = (int)b->grp.size() - 1;
+  if ((int)b->gexec.size() != 2 * ng) b->gexec.assign(2 * ng, nullptr);
+  cudaGraphExec_t &ge = b->gexec[kind * ng + g];
+  if (!ge) {
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = kind == 0 ? enq_fwd(b, b->cap) : enq_rev(b, b->cap);
+    int rc = kind == 0 ? enq_fwd(b, g, b->cap) : enq_rev(b, g, b->cap);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (rc) {
@@ -682,14 +746,14 @@ int run_b(rbc_batch *b, int kind, cudaStream_t s, long long *launches) {
       return rc;
     }
     if (e != cudaSuccess) return bfail(RBC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->gexec[kind], graph, 0);
+    e = cudaGraphInstantiate(&ge, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      b->gexec[kind] = nullptr;
+      ge = nullptr;
       return bfail(RBC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
   }
-  BCK(cudaGraphLaunch(b->gexec[kind], s));
+  BCK(cudaGraphLaunch(ge, s));
   *launches += per;
   return RBC_OK;
 }
@@ -793,6 +857,27 @@ int rbc_batch_create(const rbc_grid *g, int nshots, const int *nx_host, const fl
     for (int s = 0; s < nshots; ++s) b->hs[s].tile_ptr = b->d_tile_ptr;
   }
   cudaMemset(b->d_wav, 0, sizeof(float) * g->nt);
+  // shot groups: the fewest runs of consecutive shots whose seven fields fit
+  // the L2 budget on average (RBC_BATCH_L2MB, megabytes; 0 puts every shot
+  // in one group), cut where the running total crosses a multiple of the
+  // mean group size, so that no group is left with a remainder of shots
+  {
+    double budget = 96.0;
+    if (const char *e2 = getenv("RBC_BATCH_L2MB")) budget = atof(e2);
+    std::vector<double> mb(nshots);
+    double total_mb = 0;
+    for (int s = 0; s < nshots; ++s) total_mb += mb[s] = 7.0 * sizeof(float) * (double)b->L[s].total / 1e6;
+    const int ng = budget > 0 ? std::max(1, std::min(nshots, (int)ceil(total_mb / budget))) : 1;
+    const double target = total_mb / ng;
+    b->grp.assign(1, 0);
+    double acc = 0;
+    for (int s = 0; s < nshots; ++s) {
+      const int k = std::min(ng - 1, (int)((acc + 0.5 * mb[s]) / target));  // group of shot s
+      if (s > 0 && k > (int)b->grp.size() - 1) b->grp.push_back(s);
+      acc += mb[s];
+    }
+    b->grp.push_back(nshots);
+  }
   rc = autotune(b);
   if (rc) {
     rbc_batch_destroy(b);
@@ -913,19 +998,24 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
       launch_transpose(shots[i].seis_dev, b->d_seis_t + seis_base[i], shots[i].nrec, nt + 1, s);
       ++launches;
     }
-  cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
-  if (b->timing)
-    for (int k = 0; k < 3; ++k) {
-      BCK(cudaEventCreate(&e3[k]));
-      b->ev.push_back(e3[k]);
-    }
-  if (b->timing) BCK(cudaEventRecord(e3[0], s));
-  int rc = run_b(b, 0, s, &launches);
-  if (rc) return rc;
-  if (b->timing) BCK(cudaEventRecord(e3[1], s));
-  rc = run_b(b, 1, s, &launches);
-  if (rc) return rc;
-  if (b->timing) BCK(cudaEventRecord(e3[2], s));
+  // each group: forward phase then reverse phase, while its fields sit in L2
+  const int ng = (int)b->grp.size() - 1;
+  for (int g = 0; g < ng; ++g) {
+    cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
+    if (b->timing)
+      for (int k = 0; k < 3; ++k) {
+        BCK(cudaEventCreate(&e3[k]));
+        b->ev.push_back(e3[k]);
+      }
+    if (b->timing) BCK(cudaEventRecord(e3[0], s));
+    int rc = run_b(b, 0, g, s, &launches);
+    if (rc) return rc;
+    if (b->timing) BCK(cudaEventRecord(e3[1], s));
+    rc = run_b(b, 1, g, s, &launches);
+    if (rc) return rc;
+    if (b->timing) BCK(cudaEventRecord(e3[2], s));
+  }
+  if (b->timing) b->timed_calls++;
   int maxnx = 0;
   for (int x : b->nx) maxnx = std::max(maxnx, x);
   const long long per = (long long)maxnx * b->g.nz;
@@ -941,9 +1031,9 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
 int rbc_batch_timing(rbc_batch *b, int enable, double *out) {
   if (!b) return bfail(RBC_EINVAL, "rbc_batch_timing: NULL batch");
   double f = 0, r = 0;
-  const size_t calls = b->ev.size() / 3;
+  const size_t triples = b->ev.size() / 3, calls = (size_t)b->timed_calls;
   if (!enable || b->timing) {
-    for (size_t k = 0; k < calls; ++k) {
+    for (size_t k = 0; k < triples; ++k) {
       float t1 = 0, t2 = 0;
       BCK(cudaEventSynchronize(b->ev[3 * k + 2]));
       BCK(cudaEventElapsedTime(&t1, b->ev[3 * k], b->ev[3 * k + 1]));
@@ -954,6 +1044,7 @@ int rbc_batch_timing(rbc_batch *b, int enable, double *out) {
   }
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   b->ev.clear();
+  b->timed_calls = 0;
   b->timing = enable != 0;
   if (!enable && out) {
     out[0] = f;
@@ -974,6 +1065,7 @@ int rbc_batch_info(const rbc_batch *b, int *out) {
   out[4] = b->grid_f;
   out[5] = b->grid_r;
   for (int i = 0; i < 7; ++i) out[6 + i] = (int)(b->tune_ms[i] * 1000.0f + 0.5f);  // microseconds
+  out[13] = (int)b->grp.size() - 1;
   return RBC_OK;
 }
 

@@ -27,6 +27,29 @@ constexpr float kC4 = -0.0017857142857142857f; // -1/560
 // |symbol of L8| at the Nyquist wavenumber: stability needs a * ndim * it < 4.
 constexpr double kSymbolMax = 6.501587301587302;
 
+// Programmatic dependent launch: the kernels of consecutive time steps are
+// launched with programmatic stream serialisation, so the next step's grid
+// can be scheduled while this one drains; each kernel waits for its
+// predecessor's completion (and memory) before touching the fields and lets
+// its dependents launch after its own stores.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 constexpr int kTileX = 128;  // x extent of a block tile: 32 lanes x float4
 constexpr int kHaloX = 32;   // zero floats before x = 0
 constexpr int kHaloR = 4;    // stencil radius

@@ -19,29 +19,6 @@
 
 namespace rbc {
 
-// Programmatic dependent launch: the kernels of consecutive time steps are
-// launched with programmatic stream serialisation, so the next step's grid
-// can be scheduled while this one drains; each kernel waits for its
-// predecessor's completion (and memory) before touching the fields and lets
-// its dependents launch after its own stores.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 // Record the current level at every receiver (Algorithm 1 "record
 // seismogram"): grid-strided so any block may sample any receiver.
 __device__ __forceinline__ void sample_receivers(const StepArgs &A, int nblocks, int bid) {

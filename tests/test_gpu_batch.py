@@ -27,12 +27,17 @@ def _window(v, off, width):
 
 
 # every forward kernel the autotuner can pick (0 = the streaming kernel) and
-# both reverse shapes, forced one pair at a time, and the tuner's own choice
-@pytest.mark.parametrize("tiles", [None, "0,0", "4,2"])
-def test_batch_matches_single_shots_and_oracle(tiles, monkeypatch):
+# both reverse shapes, forced one pair at a time, and the tuner's own choice;
+# one group of all shots, one shot per group (0.3 MB) and groups of two or
+# three shots (1.5 MB)
+@pytest.mark.parametrize("tiles,l2mb,groups", [(None, None, 1), ("0,0", None, 1), ("4,2", None, 1),
+                                               (None, "0.3", 5), ("0,0", "1.5", None), ("1,1", "0", 1)])
+def test_batch_matches_single_shots_and_oracle(tiles, l2mb, groups, monkeypatch):
     import paper_2204_03380_gb300 as R
     if tiles is not None:
         monkeypatch.setenv("RBC_BATCH_TILES", tiles)
+    if l2mb is not None:
+        monkeypatch.setenv("RBC_BATCH_L2MB", l2mb)
     w, inp = _small_batch()
     dev = "cuda"
     wav = torch.tensor(inp["wavelet"], dtype=torch.float32, device=dev)
@@ -55,6 +60,10 @@ def test_batch_matches_single_shots_and_oracle(tiles, monkeypatch):
     assert info["rows_fwd"] in (0, 1, 2, 4) and info["rows_rev"] in (0, 1, 2)
     if tiles is not None:
         assert [info["rows_fwd"], info["rows_rev"]] == [int(v) for v in tiles.split(",")]
+    if groups is not None:
+        assert info["groups"] == groups
+    else:
+        assert 1 < info["groups"] < len(inp["shots"])
     img_b = torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)
     shots = [dict(src=sh["src"], rec=sh["rec"], seis=d, off_x=sh["off_x"]) for sh, d in zip(inp["shots"], seis)]
     R.rbc_batch_rtm(b, shots, wav, R.RBC_REINJECT_SOURCE, 1e-6, img_b)
