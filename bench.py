@@ -69,13 +69,15 @@ def parse():
     p.add_argument("--denoise-steps", type=int, default=20000, help="denoise: Adam steps (batch 32)")
     p.add_argument("--cnn-batch", type=int, nargs=3, default=[32, 512, 512],
                    help="cnn: images, height, width of one training / inference batch")
-    p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d", "denoise", "cnn"], default="survey2d",
+    p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d", "denoise", "cnn", "fwi"], default="survey2d",
                    help="survey2d: the 240-shot 2-D survey (default); shot3d: one 3-D shot on "
                         "500 x 500 x 300 + 40 (one step = one RTM shot); batch2d: 64 shots of "
-                        "400-1200 columns x 600 rows in one launch per time step (one step = the batch)")
+                        "400-1200 columns x 600 rows in one launch per time step (one step = the batch); "
+                        "fwi: the FWI misfit and velocity gradient of 4 shots on 300 x 300 + 50 through "
+                        "the autograd function (one step = one gradient)")
     a = p.parse_args()
     if a.steps is None:
-        a.steps = {"survey2d": 30, "shot3d": 3, "batch2d": 5, "denoise": 3, "cnn": 20}[a.workload]
+        a.steps = {"survey2d": 30, "shot3d": 3, "batch2d": 5, "denoise": 3, "cnn": 20, "fwi": 20}[a.workload]
     if a.shots_per_step is None:
         a.shots_per_step = 8 if a.workload == "survey2d" else 1
     return a
@@ -555,6 +557,140 @@ def run_cnn(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_fwi(args, rank, world):
+    """fwi: one step = J(v) and dJ/dv for the 4-shot 300 x 300 model through
+    the autograd function (rbc_fwi_forward per shot, then rbc_fwi_backward:
+    reconstruction through the random boundary fused with the exact adjoint).
+    Stencil updates per gradient: 3 nt - 1 per padded node per shot, as RTM."""
+    import torch
+    import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300.fwi import fwi_misfit, _streams_for as fwi_streams
+    import workloads as W
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = W.FWI_2D
+    if args.nt:
+        w = W.dataclasses.replace(w, nt=args.nt, name=f"{w.name}_nt{args.nt}")
+    inp = W.fwi_2d_inputs(w)
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    wav = torch.tensor(inp["wavelet"], device=dev)
+    rec, srcs = inp["rec"], inp["srcs"]
+    rbc = (w.v_lo, w.v_hi, w.v_max, w.rbc_seed)
+    # observed records from the true model (setup, untimed)
+    a = torch.empty(g.padded, dtype=torch.float32, device=dev)
+    R.rbc_build_velocity(g, torch.tensor(inp["v_true"], device=dev), *rbc[:3], rbc[3], 0, None, a)
+    ctx = R.rbc_create(g, a)
+    dobs = []
+    for s in srcs:
+        d = torch.empty((len(rec), w.nt + 1), dtype=torch.float32, device=dev)
+        R.rbc_model(ctx, s, wav, rec, d)
+        dobs.append(d)
+    torch.cuda.synchronize()
+    R.rbc_destroy(ctx)
+    del a
+    v0 = torch.tensor(inp["v0"], device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def gradient(obs, ev=None):
+        v = v0.clone().requires_grad_(True)
+        if ev:
+            ev[0].record()
+        J = fwi_misfit(v, g, srcs, wav, rec, obs, rbc)
+        if ev:
+            ev[1].record()
+        J.backward()
+        if ev:
+            ev[2].record()
+        return J, v.grad
+
+    for _ in range(args.warmup):
+        gradient(dobs)
+    torch.cuda.synchronize()
+    smi = ClockSampler(smi_device_id(torch, 0))
+    smi.start()
+    time.sleep(0.3)
+    R.rbc_launch_count(reset=True)
+    # per step: forward phase (all shots, modeling + residual) and backward
+    # phase (all shots, reconstruction + adjoint + gradient), on the stream the
+    # autograd function joins its shot streams to
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for k in range(args.steps):
+        flush.zero_()
+        J, grad = gradient(dobs, evs[k])
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = R.rbc_launch_count()
+    clocks = smi.stop()
+    el = ev0.elapsed_time(ev1) / 1e3
+    t_f = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3 / args.steps
+    t_b = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3 / args.steps
+    t_grad = t_f + t_b
+    upd = updates_per_shot(w) * len(srcs)
+    value = upd * args.steps / el / 1e9
+    nint = w.nx * w.nz
+    rev_bytes = 28 * w.npad + 8 * nint        # gradient mode: num += pbar x increment
+    # shots run concurrently (one stream each): launch time = phase time per
+    # launch of one shot's loop, i.e. the launches of all shots share the phase
+    rev_launch_s = t_b / (len(srcs) * (w.nt + 1))
+    fwd_launch_s = t_f / (len(srcs) * w.nt)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = rev_bytes / rev_launch_s / 1e9
+    # end to end: observed records from pinned host memory, gradient and misfit read back
+    e2e = None
+    if not args.no_e2e:
+        host = [d.cpu().pin_memory() for d in dobs]
+        stage = [torch.empty_like(d) for d in dobs]
+        g_host = torch.empty((w.nz, w.nx), dtype=torch.float32).pin_memory()
+        j_host = torch.empty((), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            for st, hs in zip(stage, host):
+                st.copy_(hs, non_blocking=True)
+            J, grad = gradient(stage)
+            g_host.copy_(grad, non_blocking=True)
+            j_host.copy_(J.detach(), non_blocking=True)
+        torch.cuda.synchronize()
+        el_e = time.perf_counter() - t0
+        e2e = {"value": upd * args.steps / el_e / 1e9, "unit": "Gpts/s",
+               "h2d_bytes_per_step": int(sum(d.numel() for d in dobs)) * 4,
+               "d2h_bytes_per_step": int(w.nx * w.nz + 1) * 4}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        vp = oracle.rbc_velocity(inp["v0"], w.nb, w.v_lo, w.v_hi, w.v_max, w.rbc_seed)
+        ao = oracle.coef(vp, w.dt, w.h)[1].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.fwi_grad(ao, w.h, w.dt, w.nt, srcs[0], inp["wavelet"], rec, dobs[0].cpu().numpy().astype(np.float64),
+                        w.nb, (w.nx, 1, w.nz))
+        dt_o = time.perf_counter() - t0
+        cpu = {"value": updates_per_shot(w) / dt_o / 1e9, "unit": "Gpts/s", "cores": cores_used(), "kind": "oracle",
+               "sample": f"oracle.fwi_grad of shot 0 (of {len(srcs)}), full {w.nt} steps: {dt_o:.2f} s"}
+    out = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "shots": len(srcs), "receivers": int(len(rec)), "nt": w.nt,
+                      "s_per_gradient": t_grad, "forward_phase_s": t_f, "backward_phase_s": t_b,
+                      "shot_streams": fwi_streams(g, len(srcs)), "misfit": float(J.detach()),
+                      "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+           "roofline": {"bound": "hbm", "kernel": "k_rev2d<2, true> (reconstruction + exact adjoint + gradient; "
+                                                  "shots on concurrent streams: backward phase / launches)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                        "traffic": None, "bytes_per_launch": rev_bytes, "launch_us": rev_launch_s * 1e6,
+                        "forward_kernel": {"kernel": "k_fwd2d", "launch_us": fwd_launch_s * 1e6,
+                                           "achieved": 16 * w.npad / fwd_launch_s / 1e9}},
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -599,6 +735,9 @@ def main():
         return
     if args.workload == "cnn":
         run_cnn(args, rank, world)
+        return
+    if args.workload == "fwi":
+        run_fwi(args, rank, world)
         return
     import torch
     import paper_2204_03380_gb300 as R

@@ -120,6 +120,18 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out);
 int rbc_destroy(rbc_ctx *ctx);
 
 /*
+ * rbc_set_coef -- replace the context's coefficient a = (v dt/h)^2 (Eq. 1)
+ * with a_dev (dense padded fp32, the layout rbc_create takes), enqueued on
+ * `stream`; buffers and captured graphs are kept, so repeated evaluations on
+ * one grid (an FWI iteration's updated model) pay no allocation or capture.
+ * check = 1 tests stability as rbc_create does (synchronises `stream`; the
+ * old coefficient stays on RBC_ECFL); check = 0 skips the test, for an a_dev
+ * already checked.  a_dev is read by the copy on `stream` only.
+ * Errors: RBC_EINVAL (NULL), RBC_ECFL, RBC_ECUDA.
+ */
+int rbc_set_coef(rbc_ctx *ctx, const float *a_dev, int check, void *stream);
+
+/*
  * rbc_model -- Algorithm 1 (seismic modeling) for one shot.
  *   src_host: (x, y, z) padded node of the point source.
  *   wavelet_dev: f[0..nt-1] fp32 (f[n] drives step n -> n+1).
@@ -231,7 +243,8 @@ int rbc_fwi_forward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,
  * p^n rebuilt backwards from the two panels (Eq. 6 with the source
  * re-subtracted).  resid_dev: from rbc_fwi_forward; panels_dev: the panels
  * it exported, or NULL to use those the context still holds from that call.
- * grad_dev: interior (nz, nx) fp32, ACCUMULATED (+=).
+ * grad_dev: interior (nz, nx) fp32, ACCUMULATED (+=, by atomic adds, so
+ * calls on different contexts and streams may share one grad_dev).
  * Errors: RBC_EINVAL, RBC_ENOTSUP (3-D or free_surface), RBC_ECUDA.
  */
 int rbc_fwi_backward(rbc_ctx *ctx, const int *src_host, const float *wavelet_dev,

@@ -70,6 +70,8 @@ def _load():
     lib.rbc_build_velocity.argtypes = [G, P, F, F, F, C.c_uint64, I, P, P, P]
     lib.rbc_create.argtypes = [G, P, C.POINTER(C.c_void_p)]
     lib.rbc_destroy.argtypes = [P]
+    lib.rbc_set_coef.argtypes = [P, P, I, P]
+    lib.rbc_set_coef.restype = I
     lib.rbc_model.argtypes = [P, P, P, I, P, P, P]
     lib.rbc_rtm_shot.argtypes = [P, P, P, I, P, P, I, P, P, P]
     lib.rbc_image_stack.argtypes = [G, P, P, F, I, I, G, P, P]
@@ -122,7 +124,8 @@ EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc
             "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing",
             "rbc_cnn_param_count", "rbc_cnn_workspace_bytes", "rbc_cnn_forward", "rbc_cnn_backward",
             "rbc_cnn_mse", "rbc_cnn_adam", "rbc_inject_fault", "rbc_last_error",
-            "rbc_launch_count", "rbc_nyquist_stride", "rbc_storage_bytes", "rbc_rtm_storage")
+            "rbc_launch_count", "rbc_nyquist_stride", "rbc_storage_bytes", "rbc_rtm_storage",
+            "rbc_set_coef")
 
 
 def _check(code):
@@ -169,6 +172,11 @@ def rbc_create(grid, a):
 
 def rbc_destroy(ctx):
     _check(_lib.rbc_destroy(C.c_void_p(ctx)))
+
+
+def rbc_set_coef(ctx, grid, a, check=True, stream=None):
+    """Replace the context's padded coefficient a (grid.padded fp32 CUDA)."""
+    _check(_lib.rbc_set_coef(C.c_void_p(ctx), _dev(a, grid.padded, "a"), int(bool(check)), _stream(stream)))
 
 
 def rbc_model(ctx, src, wavelet, rec, seis, stream=None):

@@ -120,6 +120,7 @@ struct rbc_ctx {
   float *store = nullptr;  // Algorithm 2: the kept levels of the graphs 4/5
   int stride = 0;
   double *misfit_tmp = nullptr;
+  unsigned int *dmax = nullptr;  // rbc_set_coef's stability check
   // phase timing (rbc_phase_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // three events per timed shot
@@ -631,6 +632,31 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   return RBC_OK;
 }
 
+int rbc_set_coef(rbc_ctx *c, const float *a_dev, int check, void *stream) {
+  if (!c || !a_dev) return fail(RBC_EINVAL, "ctx and a_dev must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Lay &L = c->L;
+  if (check) {
+    const long long n = (long long)L.NX * L.NY * L.NZ;
+    if (!c->dmax) CK(cudaMalloc(&c->dmax, sizeof(unsigned int)));
+    CK(cudaMemsetAsync(c->dmax, 0, sizeof(unsigned int), s));
+    launch_max(a_dev, n, c->dmax, s);
+    ++g_launches;
+    unsigned int bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->dmax, sizeof bits, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float amax;
+    std::memcpy(&amax, &bits, sizeof amax);
+    if (!(amax * c->g.ndim * kSymbolMax < 4.0))
+      return fail(RBC_ECFL, "unstable: max (v dt/h)^2 = %g exceeds %g for %d-D", amax,
+                  4.0 / (c->g.ndim * kSymbolMax), c->g.ndim);
+  }
+  launch_copy_in(L, a_dev, c->a, s);
+  ++g_launches;
+  CKL();
+  return RBC_OK;
+}
+
 int rbc_destroy(rbc_ctx *c) {
   if (!c) return RBC_OK;
   cudaDeviceSynchronize();
@@ -643,6 +669,7 @@ int rbc_destroy(rbc_ctx *c) {
   cudaFree(c->tile_rec);
   cudaFree(c->tile_ptr);
   cudaFree(c->seis_t);
+  cudaFree(c->dmax);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->err_host) cudaFreeHost(c->err_host);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

@@ -324,7 +324,7 @@ __global__ void k_fwi_finalize(const Lay L, const float *__restrict__ num, const
     const int x = (int)(i % nx), z = (int)(i / nx);
     const int o = lay_off(L, x + nb, 0, z + nb);
     const double av = a[o];
-    grad[i] += (float)(-2.0 * (double)num[o] * dt / (av * sqrt(av) * h));
+    atomicAdd(grad + i, (float)(-2.0 * (double)num[o] * dt / (av * sqrt(av) * h)));
   }
 }
 

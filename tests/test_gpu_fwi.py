@@ -88,3 +88,76 @@ def test_fwi_gradient_is_zero_at_the_true_model():
     J = fwi_misfit(v, g, shots, wt, rec, [d], (w.v_lo, w.v_hi, w.v_max, w.rbc_seed))
     J.backward()
     assert float(J.detach()) == 0.0 and float(v.grad.abs().max()) == 0.0
+
+
+def test_set_coef_replaces_the_model_in_place():
+    """rbc_set_coef: a context given a new coefficient models exactly what a
+    fresh context on that coefficient models; an unstable coefficient is
+    refused and the previous one stays in use."""
+    import paper_2204_03380_gb300 as R
+    w, vt, v0, shots, rec, wav = _fwi_case(60, 50, 10, 300, 1)
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    wt = torch.tensor(wav, dtype=torch.float32, device="cuda")
+
+    def coef(v):
+        a = torch.empty(g.padded, dtype=torch.float32, device="cuda")
+        R.rbc_build_velocity(g, torch.tensor(v, dtype=torch.float32, device="cuda"), w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, a)
+        return a
+
+    def record(ctx):
+        d = torch.empty((len(rec), w.nt + 1), dtype=torch.float32, device="cuda")
+        R.rbc_model(ctx, shots[0], wt, rec, d)
+        torch.cuda.synchronize()
+        return d.cpu().numpy()
+
+    a1, a2 = coef(vt), coef(v0)
+    fresh = R.rbc_create(g, a2)
+    d_fresh = record(fresh)
+    R.rbc_destroy(fresh)
+    ctx = R.rbc_create(g, a1)
+    d1 = record(ctx)
+    R.rbc_set_coef(ctx, g, a2)
+    d2 = record(ctx)
+    assert np.array_equal(d2, d_fresh) and not np.array_equal(d1, d2)
+    with pytest.raises(R.RBCError) as e:
+        R.rbc_set_coef(ctx, g, torch.full(g.padded, 0.5, device="cuda"))
+    from paper_2204_03380_gb300._native import RBC_ECFL
+    assert e.value.code == RBC_ECFL
+    assert np.array_equal(record(ctx), d_fresh)
+    R.rbc_set_coef(ctx, g, a1, check=False)
+    assert np.array_equal(record(ctx), d1)
+    R.rbc_destroy(ctx)
+
+
+def test_fwi_gradient_of_an_earlier_forward():
+    """Two forward evaluations before the first backward: the pooled contexts
+    hold the second model by then, and the first gradient must still be the
+    gradient at the first model."""
+    import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300.fwi import fwi_misfit
+    w, vt, v0, shots, rec, wav = _fwi_case(60, 50, 10, 300, 3)
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    wt = torch.tensor(wav, dtype=torch.float32, device="cuda")
+    rbc = (w.v_lo, w.v_hi, w.v_max, w.rbc_seed)
+    a = torch.empty(g.padded, dtype=torch.float32, device="cuda")
+    R.rbc_build_velocity(g, torch.tensor(vt, dtype=torch.float32, device="cuda"), w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, a)
+    ctx = R.rbc_create(g, a)
+    dobs = []
+    for s in shots:
+        d = torch.empty((len(rec), w.nt + 1), dtype=torch.float32, device="cuda")
+        R.rbc_model(ctx, s, wt, rec, d)
+        dobs.append(d)
+    R.rbc_destroy(ctx)
+    v1 = torch.tensor(v0, dtype=torch.float32, device="cuda", requires_grad=True)
+    J1 = fwi_misfit(v1, g, shots, wt, rec, dobs, rbc)
+    J1.backward()
+    g_ref = v1.grad.clone()
+    va = torch.tensor(v0, dtype=torch.float32, device="cuda", requires_grad=True)
+    vb = torch.tensor(0.5 * (v0 + vt), dtype=torch.float32, device="cuda", requires_grad=True)
+    Ja = fwi_misfit(va, g, shots, wt, rec, dobs, rbc)
+    Jb = fwi_misfit(vb, g, shots, wt, rec, dobs, rbc)
+    Ja.backward()
+    Jb.backward()
+    assert float(Ja) == pytest.approx(float(J1), rel=1e-6) and float(Jb) < float(Ja)
+    assert rel(va.grad.cpu().numpy(), g_ref.cpu().numpy()) <= 1e-5
+    assert rel(vb.grad.cpu().numpy(), g_ref.cpu().numpy()) > 1e-2

@@ -69,6 +69,11 @@ SHOT_3D = Workload("3d_500x500x300_nb40_3000steps", 3, 500, 500, 300, 40, 10.0, 
 BATCH_2D = Workload("2d_batch_64shots_w400-1200_600rows_nb50_3000steps", 2, 4000, 1, 600, 50, 5.0,
                     0.5e-3, 3000, 25.0, 1500.0, 4000.0, 4000.0, 4, nshots=64)
 
+# FWI gradient: 300 x 300 three-layer model with a Gaussian velocity anomaly,
+# 10 m cells, 50-cell random boundary, 1000 steps of 1 ms, 15 Hz, 4 shots
+FWI_2D = Workload("2d_fwi_300x300_nb50_1000steps_4shots", 2, 300, 1, 300, 50, 10.0, 1e-3, 1000,
+                  15.0, 1500.0, 4500.0, 3500.0, 1, nshots=4)
+
 
 def scaled(w: Workload, nx=None, ny=None, nz=None, nb=None, nt=None, name=None) -> Workload:
     """A smaller copy of a preset (same spacing, velocities and source)."""
@@ -275,3 +280,19 @@ def batch_2d_inputs(w: Workload = BATCH_2D, model_seed: int = 9, width_seed: int
         src = np.array([width // 2 + w.nb, 0, w.nb + 1], np.int32)
         shots.append(dict(width=width, off_x=off, src=src, rec=rec))
     return dict(v_true=v_true, v_mig=v_mig, shots=shots, wavelet=ricker(w.nt, w.dt, w.f_peak))
+
+
+def fwi_2d_inputs(w: Workload = FWI_2D, rec_step: int = 2):
+    """True model: three flat layers (boundaries at 35 % and 70 % of the
+    depth) times 1 + 0.1 exp(-r^2 / (2 (nz/20)^2)) around the centre; starting
+    model: its slowness smoothed over nz/20 cells; w.nshots evenly spaced
+    sources at depth 1, receivers every rec_step columns at depth 1."""
+    nx, nz = w.nx, w.nz
+    vt = three_layers(nx, nz, (nz * 7 // 20, nz * 14 // 20))
+    zz, xx = np.mgrid[0:nz, 0:nx]
+    vt = vt * (1 + 0.1 * np.exp(-((zz - nz / 2) ** 2 + (xx - nx / 2) ** 2) / (2 * (nz / 20) ** 2)))
+    v0 = smooth_slowness(vt, nz / 20)
+    return dict(v_true=vt.astype(np.float32), v0=v0.astype(np.float32),
+                srcs=[source_at(w, int(x)) for x in shot_columns(w, w.nshots)],
+                rec=surface_line(w, step=rec_step),
+                wavelet=ricker(w.nt, w.dt, w.f_peak).astype(np.float32))
