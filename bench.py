@@ -218,9 +218,9 @@ def load_workload(W, args):
 #   the traffic grows in proportion, so the full launch gets 1.122 x its own.
 TRAFFIC = {
     2: {"sources": ["rbc_kernels.cu", "rbc_tile2d.cuh", "rbc_stencil.cuh", "rbc_internal.cuh"],
-        "sha1": "014d852b58f0a55c", "bytes_per_launch": 27.8e6, "ratio": None},
+        "sha1": "5fe0dda59493d4db", "bytes_per_launch": 27.8e6, "ratio": None},
     3: {"sources": ["rbc_kernels3d.cu", "rbc_stencil.cuh", "rbc_internal.cuh"],
-        "sha1": "67add0ae306ed090", "bytes_per_launch": None, "ratio": 1.122},
+        "sha1": "f496bf492f99cf4a", "bytes_per_launch": None, "ratio": 1.122},
 }
 
 
