@@ -266,6 +266,19 @@ def oracle_rtm_sample(w, inp, nsteps: int):
     return updates_per_shot(ws) / dt / 1e9, dt
 
 
+def oracle_cnn_sample(H, W, backward=False):
+    """Time the FP64 oracle network (as it stands) on one H x W image:
+    forward, or forward + backward.  Returns seconds."""
+    import oracle.cnn as OC
+    params = OC.init_params(0)
+    x = np.random.default_rng(0).standard_normal((1, H, W))
+    t0 = time.perf_counter()
+    y, cache = OC.forward(params, x)
+    if backward:
+        OC.backward(params, cache, y - x)
+    return time.perf_counter() - t0
+
+
 def cores_used():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
@@ -373,6 +386,25 @@ def run_batch(args, rank, world):
     achieved = rev_bytes / rev_s / 1e9
     if rank != 0:
         return
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's RTM of shot 0 (its own window and record) over the first
+        # nsamp steps, about 6e9 stencil updates
+        import oracle
+        sh = inp["shots"][0]
+        ws = W.dataclasses.replace(w, nx=sh["width"])
+        nsamp = int(max(10, min(w.nt, 6e9 / (3 * npads[0]))))
+        vw = np.ascontiguousarray(inp["v_mig"][:, sh["off_x"]:sh["off_x"] + sh["width"]]).astype(np.float32)
+        ao = oracle.coef(oracle.rbc_velocity(vw, w.nb, w.v_lo, w.v_hi, w.v_max, w.rbc_seed), w.dt, w.h)[1]
+        d0 = seis[0].cpu().numpy()[:, :nsamp + 1].astype(np.float64)
+        t0 = time.perf_counter()
+        r = oracle.rtm_shot(ao.astype(np.float64), w.h, nsamp, sh["src"], inp["wavelet"][:nsamp], sh["rec"], d0,
+                            w.nb, (ws.nx, 1, w.nz))
+        dt_o = time.perf_counter() - t0
+        assert np.isfinite(r["num"]).all()
+        cpu = {"value": npads[0] * (3 * nsamp - 1) / dt_o / 1e9, "unit": "Gpts/s", "cores": cores_used(),
+               "kind": "oracle", "sample": f"oracle RTM of shot 0 ({sh['width']} + {2 * w.nb} columns), "
+                                           f"{nsamp} of the {w.nt} steps: {dt_o:.1f} s"}
     out = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -386,7 +418,7 @@ def run_batch(args, rank, world):
                         "traffic": None, "bytes_per_launch": rev_bytes, "launch_us": rev_s * 1e6,
                         "forward_kernel": {"kernel": "k_fwd2d_batch", "launch_us": fwd_s * 1e6,
                                            "achieved": 16 * sum(npads) / fwd_s / 1e9}},
-           "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -488,6 +520,13 @@ def run_denoise(args, rank, world):
     peaks = measured_peaks()
     peak = peaks["bf16_tflops"] if peaks else 1900.0
     achieved = flops / t_inf / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle network on one x-z slice, scaled to the volume's slices
+        dt_o = oracle_cnn_sample(w3.nz, w3.nx)
+        cpu = {"value": dt_o * w3.ny, "unit": "s per volume (oracle network, extrapolated)",
+               "cores": cores_used(), "kind": "oracle",
+               "sample": f"oracle.cnn forward of 1 of the {w3.ny} x-z slices ({w3.nz}x{w3.nx}): {dt_o:.1f} s"}
     out = {"metric": METRIC, "value": 16 * t_rtm / t_inf, "unit": "x (16-realization 3-D stack time / network time)",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_inf * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
@@ -501,7 +540,7 @@ def run_denoise(args, rank, world):
            "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05, hidden layers) + k_conv_1to32 + k_conv_32to1", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
-           "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+           "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": None}
     print(json.dumps(out), flush=True)
 
 
@@ -530,6 +569,11 @@ def run_cnn(args, rank, world):
     ev1.record()
     torch.cuda.synchronize()
     t_train = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    cpu = None
+    if not args.no_cpu_baseline:
+        dt_o = oracle_cnn_sample(H, Wd, backward=True)
+        cpu = {"value": H * Wd / dt_o / 1e9, "unit": "Gpx/s (forward + backward)", "cores": cores_used(),
+               "kind": "oracle", "sample": f"oracle.cnn forward + backward of 1 image of {H}x{Wd}: {dt_o:.1f} s"}
     for _ in range(args.warmup):
         y = net(x)
     torch.cuda.synchronize()
@@ -553,7 +597,7 @@ def run_cnn(args, rank, world):
            "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05, hidden layers) + k_conv_1to32 + k_conv_32to1", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
-           "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+           "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": None}
     print(json.dumps(out), flush=True)
 
 
