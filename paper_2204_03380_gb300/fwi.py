@@ -67,14 +67,11 @@ def _fan_out(grid, a, nshots, device, check):
     work so far."""
     main = torch.cuda.current_stream(device)
     pool = _pool(grid, a, _streams_for(grid, nshots), device)
-    if check:
-        N.rbc_set_coef(pool[0][0], grid, a, True, main)
     start = torch.cuda.Event()
     start.record(main)
     for k, (ctx, s) in enumerate(pool):
         s.wait_event(start)
-        if k or not check:
-            N.rbc_set_coef(ctx, grid, a, False, s)
+        N.rbc_set_coef(ctx, grid, a, check and k == 0, s)   # ordered after the context's earlier work
     return main, pool
 
 
