@@ -65,6 +65,7 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert lib.rbc_image_stack(C.byref(shot), p, p, 1e-6, 0, 0, C.byref(other), p, None) == 1
     assert lib.rbc_model(None, None, None, 0, None, None, None) == 1
     assert lib.rbc_set_snapshots(None, 0, None, None, None, None) == 1
+    assert lib.rbc_set_coef(None, C.c_void_p(16), 1, None) == 1
 
 
 def test_nyquist_stride_and_storage_size_on_the_host():
