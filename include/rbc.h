@@ -302,7 +302,10 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
 
 /* rbc_batch_timing -- as rbc_phase_timing, for the forward and reverse
  * phases of every rbc_batch_rtm call while enabled (out[0..4]: forward ms,
- * reverse ms, forward launches, reverse launches, calls). */
+ * reverse ms, forward time steps, reverse time steps, calls).  The phases of
+ * all shot groups are summed, and a time step counts once however many
+ * groups it was launched for, so ms / steps is the time of one step of the
+ * whole batch. */
 int rbc_batch_timing(rbc_batch *b, int enable, double *out);
 
 /* rbc_batch_info -- out[0..13]: forward and reverse rows per warp chosen by
