@@ -608,7 +608,7 @@ def run_fwi(args, rank, world):
     Stencil updates per gradient: 3 nt - 1 per padded node per shot, as RTM."""
     import torch
     import paper_2204_03380_gb300 as R
-    from paper_2204_03380_gb300.fwi import fwi_misfit, _streams_for as fwi_streams
+    from paper_2204_03380_gb300.fwi import fwi_misfit, shot_streams
     import workloads as W
     if rank != 0:
         return
@@ -722,7 +722,7 @@ def run_fwi(args, rank, world):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "shots": len(srcs), "receivers": int(len(rec)), "nt": w.nt,
                       "s_per_gradient": t_grad, "forward_phase_s": t_f, "backward_phase_s": t_b,
-                      "shot_streams": fwi_streams(g, len(srcs)), "misfit": float(J.detach()),
+                      "shot_streams": shot_streams(g, len(srcs)), "misfit": float(J.detach()),
                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
            "roofline": {"bound": "hbm", "kernel": "k_rev2d<2, true> (reconstruction + exact adjoint + gradient; "
                                                   "shots on concurrent streams: backward phase / launches)",

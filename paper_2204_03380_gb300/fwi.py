@@ -35,7 +35,9 @@ def _grid_key(grid):
     return tuple(getattr(grid, f) for f, _ in grid._fields_)
 
 
-def _streams_for(grid, nshots):
+def shot_streams(grid, nshots):
+    """Shots in flight at once for this grid: at most MAX_STREAMS, and no more
+    than the contexts whose seven fields fit in POOL_BYTES."""
     nodes = 1
     for n in grid.padded:
         nodes *= n
@@ -66,7 +68,7 @@ def _fan_out(grid, a, nshots, device, check):
     (checked once when check); the streams start after the current stream's
     work so far."""
     main = torch.cuda.current_stream(device)
-    pool = _pool(grid, a, _streams_for(grid, nshots), device)
+    pool = _pool(grid, a, shot_streams(grid, nshots), device)
     start = torch.cuda.Event()
     start.record(main)
     for k, (ctx, s) in enumerate(pool):
