@@ -48,10 +48,6 @@ __device__ __forceinline__ void mma16816(float *c, const uint32_t *a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
 enum { kHidden = 0, kLast = 1, kBackData = 2 };
 
 // The one-channel ends of the network carry 32x fewer flops than the hidden
@@ -444,128 +440,165 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
-// Weight and bias gradients of one layer, on the tensor cores:
-//   dW[t][co][ci] += sum_p dz[p][co] x[p + off(t)][ci],  db[co] += sum_p dz[p][co]
-// For every tap this is a GEMM with M = output channels, N = input channels
-// and K = pixels; warp t of the block owns tap t.  The tile's dz (256 pixels)
-// and x halo are staged channel-major in shared memory so that consecutive K
-// (pixels) are adjacent.  dz: NHWC bf16 (COUT ch) or fp32 (dzf, COUT = 1).
-// Persistent blocks walk 8 x 32 pixel tiles, keep the partial sums in
-// registers and add them to dW / db once.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(288) k_conv_wgrad(const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ dz,
-                                                    const float *__restrict__ dzf, float *__restrict__ dw,
-                                                    float *__restrict__ db, int nimg, int H, int W) {
-  constexpr int MT = (COUT + 15) / 16, NT = (CIN + 7) / 8;
-  constexpr int CM = MT * 16, CN = NT * 8;   // padded channel counts
-  constexpr int HP = (TH + 2) * (TW + 2);    // halo pixels
-  __shared__ __nv_bfloat16 s_x[CN * HP];     // [ci][halo pixel]
-  __shared__ __nv_bfloat16 s_dz[CM * TH * TW];  // [co][pixel]
+// Weight and bias gradients of a convolution layer:
+//   dW[tap][co][ci] = sum_p dz[co][p] x[ci][p + tap],  db[co] = sum_p dz[co][p],
+// with x and dz 32-channel planar; the one-channel ends of the network pass
+// their single channel as channel 0 of a 32-channel operand (k_expand_c0) and
+// keep the CI x CO corner of the result.
+// Per tap a GEMM with M = 32 output channels, N = 32 input channels and K =
+// the pixels, on mma.sync m16n8k16 (bf16 in, fp32 accumulate).  Persistent
+// blocks of nine warps (one per tap) walk 8 x 32-pixel tiles; a tile's input
+// halo (10 x 34 pixels) and its 256 output gradients are copied into shared
+// memory as they lie in global memory (channel-group planar: 16 bytes = 8
+// channels of one pixel), by 16-byte cp.async copies that zero-fill outside
+// the image, double-buffered so that tile k + 1 arrives while tile k is
+// multiplied.  Both operands come out of that layout with ldmatrix.trans: a
+// pixel's 16-byte chunk is one row of an 8 x 8 matrix whatever the tap's
+// shift, so every tap reads the same halo at a different start pixel.  The
+// centre-tap warp also multiplies by a column of ones: the bias gradient.
+constexpr int kWgHP = (TH + 2) * (TW + 2);  // halo pixels of a tile
+constexpr int kWgNP = TH * TW;              // output pixels of a tile
+constexpr int kWgBuf = 4 * (kWgHP + kWgNP) * 8;  // bf16 per buffer: x halo, then dz
+constexpr size_t kWgSmem = 2 * sizeof(__nv_bfloat16) * kWgBuf;
+
+__device__ __forceinline__ void cp16_zfill(void *smem, const void *gmem, bool valid) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *smem_row) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(sa));
+}
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(288) k_conv_wgrad32(const __nv_bfloat16 *__restrict__ x,
+                                                      const __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
+                                                      float *__restrict__ db, int nimg, int H, int W) {
+  extern __shared__ __align__(16) __nv_bfloat16 s_wg[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, tig = lane & 3;
-  const int dy = warp / 3, dx = warp % 3;    // this warp's tap
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int m = 0; m < MT; ++m)
-#pragma unroll
-    for (int n = 0; n < NT; ++n)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[m][n][r] = 0.f;
-  float bacc = 0.f;
+  const int g = lane >> 2, tq = lane & 3;
+  const int dy = warp / 3, dx = warp % 3;  // this warp's tap
   const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
-  const long long ntiles = (long long)tx * ty * nimg;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const long long ntiles = (long long)tx * ty * nimg, HWp = (long long)H * W;
+  // stage tile `tile` into buffer b (one cp.async group)
+  auto stage = [&](long long tile, int b) {
     const int img = (int)(tile / ((long long)tx * ty));
     const int rem = (int)(tile % ((long long)tx * ty));
     const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
-    const long long ibase = (long long)img * H * W;
-    __syncthreads();
-    const long long HWp = (long long)H * W;
-    if (CIN == 32) {
-      // 16-byte chunks (8 channels of one pixel) of the channel-group planes
-      for (int i = threadIdx.x; i < HP * 4; i += blockDim.x) {
-        const int hp = i % HP, cg = i / HP;
-        const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-          v = reinterpret_cast<const uint4 *>(x)[((long long)img * 4 + cg) * HWp + (long long)yy * W + xx];
-        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) s_x[(cg * 8 + k) * HP + hp] = e[k];
-      }
-    } else {
-      for (int i = threadIdx.x; i < HP * CN; i += blockDim.x) {
-        const int c = i / HP, hp = i % HP;
-        const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
-        s_x[c * HP + hp] = (c < CIN && yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[ibase + (long long)yy * W + xx] : zero;
-      }
+    __nv_bfloat16 *sx = s_wg + b * kWgBuf, *sd = sx + 4 * kWgHP * 8;
+    for (int i = threadIdx.x; i < 4 * kWgHP; i += blockDim.x) {
+      const int cg = i / kWgHP, hp = i % kWgHP;
+      const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
+      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+      const __nv_bfloat16 *src = ok ? x + (((long long)img * 4 + cg) * HWp + (long long)yy * W + xx) * 8 : x;
+      cp16_zfill(sx + (cg * kWgHP + hp) * 8, src, ok);
     }
-    if (COUT == 32) {
-      for (int i = threadIdx.x; i < TH * TW * 4; i += blockDim.x) {
-        const int q = i % (TH * TW), cg = i / (TH * TW);
-        const int yy = y0 + q / TW, xx = x0 + q % TW;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (yy < H && xx < W) v = reinterpret_cast<const uint4 *>(dz)[((long long)img * 4 + cg) * HWp + (long long)yy * W + xx];
-        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+    for (int i = threadIdx.x; i < 4 * kWgNP; i += blockDim.x) {
+      const int cg = i / kWgNP, q = i % kWgNP;
+      const int yy = y0 + q / TW, xx = x0 + q % TW;
+      const bool ok = yy < H && xx < W;
+      const __nv_bfloat16 *src = ok ? dz + (((long long)img * 4 + cg) * HWp + (long long)yy * W + xx) * 8 : dz;
+      cp16_zfill(sd + (cg * kWgNP + q) * 8, src, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  float acc[2][4][4], accb[2][4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s_dz[(cg * 8 + k) * TH * TW + q] = e[k];
-      }
+  for (int m = 0; m < 2; ++m) {
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[m][n][r] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) accb[m][r] = 0.f;
+  }
+  const uint32_t ones[2] = {0x3F803F80u, 0x3F803F80u};  // bf16 1.0 pairs
+  // ldmatrix row of this lane: matrix j = lane / 8, row r = lane % 8
+  const int lj = lane >> 3, lr = lane & 7;
+  int b = 0;
+  if ((long long)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    if (next < ntiles) {
+      stage(next, b ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
     } else {
-      for (int i = threadIdx.x; i < TH * TW * CM; i += blockDim.x) {
-        const int c = i / (TH * TW), q = i % (TH * TW);
-        const int yy = y0 + q / TW, xx = x0 + q % TW;
-        __nv_bfloat16 v = zero;
-        if (c < COUT && yy < H && xx < W) v = __float2bfloat16(dzf[ibase + (long long)yy * W + xx]);
-        s_dz[c * TH * TW + q] = v;
-      }
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
     if (warp < 9) {
+      const __nv_bfloat16 *sx = s_wg + b * kWgBuf, *sd = sx + 4 * kWgHP * 8;
 #pragma unroll 1
-      for (int q0 = 0; q0 < TH * TW; q0 += 16) {
-        const int row = q0 / TW, col0 = q0 % TW;
-        uint32_t a[MT][4], b[NT][2];
+      for (int k0 = 0; k0 < kWgNP; k0 += 16) {
+        const int row = k0 / TW, c0 = k0 % TW;
+        // A (dz): matrices (co 0-7 | 8-15) x (pixels 0-7 | 8-15) of each 16-channel half
+        uint32_t a[2][4];
 #pragma unroll
-        for (int m = 0; m < MT; ++m) {
-          const __nv_bfloat16 *r0 = s_dz + (m * 16 + g) * TH * TW + q0 + tig * 2;
-          const __nv_bfloat16 *r1 = r0 + 8 * TH * TW;
-          a[m][0] = pack2(r0[0], r0[1]);
-          a[m][1] = pack2(r1[0], r1[1]);
-          a[m][2] = pack2(r0[8], r0[9]);
-          a[m][3] = pack2(r1[8], r1[9]);
+        for (int m = 0; m < 2; ++m)
+          ldsm_x4_t(a[m], sd + ((2 * m + (lj & 1)) * kWgNP + k0 + (lj >> 1) * 8 + lr) * 8);
+        // B (x shifted by the tap): channel groups 2h, 2h + 1, pixels 0-7 | 8-15
+        const int hq = (row + dy) * (TW + 2) + c0 + dx;
+        uint32_t bf[4][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t r4[4];
+          ldsm_x4_t(r4, sx + ((2 * h + (lj >> 1)) * kWgHP + hq + (lj & 1) * 8 + lr) * 8);
+          bf[2 * h][0] = r4[0];
+          bf[2 * h][1] = r4[1];
+          bf[2 * h + 1][0] = r4[2];
+          bf[2 * h + 1][1] = r4[3];
         }
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-          const __nv_bfloat16 *c0 = s_x + (n * 8 + g) * HP + (row + dy) * (TW + 2) + col0 + dx + tig * 2;
-          b[n][0] = pack2(c0[0], c0[1]);
-          b[n][1] = pack2(c0[8], c0[9]);
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+          for (int n = 0; n < 4; ++n) mma16816(acc[m][n], a[m], bf[n]);
+        if (warp == 4) {
+#pragma unroll
+          for (int m = 0; m < 2; ++m) mma16816(accb[m], a[m], ones);
         }
-#pragma unroll
-        for (int m = 0; m < MT; ++m)
-#pragma unroll
-          for (int n = 0; n < NT; ++n) mma16816(acc[m][n], a[m], b[n]);
       }
     }
-    if (threadIdx.x < COUT) {
-      float sb = 0.f;
-      for (int q = 0; q < TH * TW; ++q) sb += __bfloat162float(s_dz[threadIdx.x * TH * TW + q]);
-      bacc += sb;
-    }
+    __syncthreads();  // buffer b is refilled by the stage two tiles on
+    b ^= 1;
   }
   if (warp < 9) {
-    const int t = warp;
 #pragma unroll
-    for (int m = 0; m < MT; ++m)
+    for (int m = 0; m < 2; ++m)
 #pragma unroll
-      for (int n = 0; n < NT; ++n)
+      for (int n = 0; n < 4; ++n)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const int co = m * 16 + g + (r >> 1) * 8, ci = n * 8 + tig * 2 + (r & 1);
-          if (co < COUT && ci < CIN) atomicAdd(dw + (t * COUT + co) * CIN + ci, acc[m][n][r]);
+          const int co = m * 16 + g + (r >> 1) * 8, ci = n * 8 + tq * 2 + (r & 1);
+          if (co < CO && ci < CI) atomicAdd(dw + (warp * CO + co) * CI + ci, acc[m][n][r]);
         }
+    if (warp == 4 && tq == 0) {
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        if (m * 16 + g < CO) atomicAdd(db + m * 16 + g, accb[m][0]);
+        if (m * 16 + g + 8 < CO) atomicAdd(db + m * 16 + g + 8, accb[m][2]);
+      }
+    }
   }
-  if (threadIdx.x < COUT) atomicAdd(db + threadIdx.x, bacc);
+}
+
+// One channel [img][pixel] -> 32-channel planar bf16 with the value in
+// channel 0 and zeros elsewhere (the operand form of k_conv_wgrad32).
+template <typename T>
+__global__ void k_expand_c0(const T *__restrict__ in, __nv_bfloat16 *__restrict__ out, long long HWp, int nimg) {
+  uint4 *o = reinterpret_cast<uint4 *>(out);
+  const long long n = HWp * nimg;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long img = i / HWp, p = i % HWp;
+    const __nv_bfloat16 v = __float2bfloat16((float)in[i]);
+    o[(img * 4 + 0) * HWp + p] = make_uint4((uint32_t)__bfloat16_as_ushort(v), 0u, 0u, 0u);
+    o[(img * 4 + 1) * HWp + p] = make_uint4(0u, 0u, 0u, 0u);
+    o[(img * 4 + 2) * HWp + p] = make_uint4(0u, 0u, 0u, 0u);
+    o[(img * 4 + 3) * HWp + p] = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 // fp32 master weights -> bf16 compute weights: forward copies and the
@@ -622,6 +655,9 @@ void set_attrs() {
   if (done) return;
   cudaFuncSetAttribute(k_conv_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   cudaFuncSetAttribute(k_conv_tc<kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+  cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+  cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   done = true;
 }
 
@@ -749,7 +785,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const int pg = 2 * sms;
   // layer 5: dW5, db5 from dy; dz4 = conv^T(dy) masked by act4 > 0
-  k_conv_wgrad<C, 1><<<pg, 288, 0, s>>>(w.act[3], nullptr, dy_dev, grad_dev + kW5, grad_dev + kB5, nimg, H, W);
+  k_expand_c0<float><<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dz[1], (long long)H * W, nimg);
+  k_conv_wgrad32<C, 1><<<pg, 288, kWgSmem, s>>>(w.act[3], w.dz[1], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
   k_conv_1to32<kBackData><<<grid, 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3], w.dz[0], H, W);
@@ -759,15 +796,16 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   const int woff[3] = {kW4, kW3, kW2}, boff[3] = {kB4, kB3, kB2};
   for (int l = 0; l < 3; ++l) {
     const int layer_in = 2 - l;  // act index of this layer's input: act3 (l=0) ... act1
-    k_conv_wgrad<C, C><<<pg, 288, 0, s>>>(w.act[layer_in], w.dz[cur], nullptr, grad_dev + woff[l], grad_dev + boff[l],
-                                           nimg, H, W);
+    k_conv_wgrad32<C, C><<<pg, 288, kWgSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l], grad_dev + boff[l],
+                                                   nimg, H, W);
     ok_tc = ok_tc && launch_conv_tc<kBackData>(w.dz[cur], w.wb + woff[l], nullptr, w.act[layer_in], w.dz[1 - cur], nimg, H, W, s);
     cur = 1 - cur;
   }
   // layer 1
-  k_conv_wgrad<1, C><<<pg, 288, 0, s>>>(w.x0, w.dz[cur], nullptr, grad_dev + kW1, grad_dev + kB1, nimg, H, W);
+  k_expand_c0<__nv_bfloat16><<<grid_of(npx), 256, 0, s>>>(w.x0, w.dz[1 - cur], (long long)H * W, nimg);
+  k_conv_wgrad32<1, C><<<pg, 288, kWgSmem, s>>>(w.dz[1 - cur], w.dz[cur], grad_dev + kW1, grad_dev + kB1, nimg, H, W);
   if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_backward: tensor map encoding failed");
-  rbc::add_launches(10);
+  rbc::add_launches(12);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
   return RBC_OK;
