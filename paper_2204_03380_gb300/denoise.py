@@ -5,7 +5,7 @@ wavefield carries incoherent scattering from the random pad, which leaks into
 the image; it differs from one boundary realization to the next, so the plain
 fix is to migrate K realizations and average them (the K-stack).  This module
 trains the small CNN of librbc (rbc_cnn_*) to map a single-realization image
-to the K-stack, and keeps the K-stack as the fallback and as the judge of the
+to the K-stack, and keeps the K-stack as the fallback and as the yardstick of the
 network's error.  Every image, gradient and update is computed by librbc's
 kernels; this module sequences the calls and holds the tensors.
 """
@@ -102,7 +102,7 @@ class ImageSet:
         return self.images[:, 0]
 
     @property
-    def stack(self):       # the K-stack: the fallback and the judge
+    def stack(self):       # the K-stack: the fallback and the yardstick
         return self.images.mean(dim=1)
 
 

@@ -1,7 +1,7 @@
 """The learned denoiser end to end: images from the RTM pipeline (K random
 boundary realizations per model, via the batched path), training by the
 project's own kernels, and the gain of the trained network over the method
-without it (a single realization), judged against the K-stack on held-out
+without it (a single realization), measured against the K-stack on held-out
 models."""
 import numpy as np
 import pytest

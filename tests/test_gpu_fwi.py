@@ -28,8 +28,8 @@ def _fwi_case(nx, nz, nb, nt, nshots, seed=0):
 @pytest.mark.parametrize("dims", [(60, 50, 10, 400, 2), (300, 300, 50, 1000, 4)], ids=["small", "300x300_4shots"])
 def test_fwi_gradient_matches_oracle(dims):
     """The residual record - d_obs is a small difference of two records (their
-    direct waves cancel), so its fp32 error is judged at the scale of the
-    record; the adjoint (the gradient) is judged against the oracle run on the
+    direct waves cancel), so its fp32 error is measured at the scale of the
+    record; the adjoint (the gradient) is compared with the oracle run on the
     same adjoint source, i.e. d_obs shifted so that the oracle's residual is the
     GPU's."""
     import paper_2204_03380_gb300 as R

@@ -47,7 +47,7 @@ def snap_err(g, o):
     """Snapshot error relative to the largest snapshot of the same field: the
     fp32 leapfrog (forward or reversed) carries an absolute rounding error at
     the scale of the field over the whole record, so a level where the exact
-    field is still tiny is judged against that scale, not its own norm."""
+    field is still tiny is measured against that scale, not its own norm."""
     scale = max(np.linalg.norm(x) for x in o)
     return max(np.linalg.norm(a - b) for a, b in zip(g, o)) / scale
 
