@@ -66,6 +66,33 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert lib.rbc_model(None, None, None, 0, None, None, None) == 1
     assert lib.rbc_set_snapshots(None, 0, None, None, None, None) == 1
     assert lib.rbc_set_coef(None, C.c_void_p(16), 1, None) == 1
+    # the other entry points' argument checks come before any device work
+    assert lib.rbc_rtm_shot(None, None, None, 0, None, None, 1, None, None, None) == 1
+    assert lib.rbc_rtm_storage(None, None, None, 0, None, None, 1, None, C.c_longlong(0), 0, None, None, None) == 1
+    assert lib.rbc_fwi_forward(None, None, None, 1, None, None, None, None, None, None) == 1
+    assert lib.rbc_fwi_backward(None, None, None, 1, None, None, None, None, None) == 1
+    assert lib.rbc_get_panels(None, None, None, None) == 1
+    assert lib.rbc_phase_timing(None, 1, None) == 1
+    assert lib.rbc_inject_fault(None, 1) == 1
+    out_b = C.c_void_p()
+    nx1 = (C.c_int * 1)(10)
+    assert lib.rbc_batch_create(C.byref(g), 0, nx1, None, C.byref(out_b)) == 1
+    g3 = R.make_grid(3, 10, 10, 10, 5, 10.0, 1e-3, 10)
+    ptrs = (C.c_void_p * 1)(16)
+    assert lib.rbc_batch_create(C.byref(g3), 1, nx1, ptrs, C.byref(out_b)) == 6   # batches are 2-D
+    assert lib.rbc_batch_create(C.byref(R.make_grid(2, 10, 1, 10, 5, 10.0, 1e-3, 10, free_surface=1)), 1, nx1,
+                                ptrs, C.byref(out_b)) == 1
+    assert lib.rbc_batch_rtm(None, None, None, 1, C.c_float(1e-6), None, 10, None) == 1
+    assert lib.rbc_batch_timing(None, 0, None) == 1
+    assert lib.rbc_batch_info(None, None) == 1
+    p16 = C.c_void_p(16)
+    assert lib.rbc_cnn_forward(None, 1, 8, 8, p16, p16, p16, None) == 1
+    assert lib.rbc_cnn_forward(p16, 0, 8, 8, p16, p16, p16, None) == 1
+    assert lib.rbc_cnn_backward(p16, 1, 0, 8, p16, p16, p16, None) == 1
+    assert lib.rbc_cnn_mse(p16, p16, C.c_longlong(0), None, p16, None) == 1
+    assert lib.rbc_cnn_adam(p16, p16, p16, p16, C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999),
+                            C.c_float(1e-8), 0, None) == 1
+    assert lib.rbc_model_static(None, None, None, None, 0, None, None, None) == 1
 
 
 def test_nyquist_stride_and_storage_size_on_the_host():
