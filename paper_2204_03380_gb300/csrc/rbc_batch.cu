@@ -3,12 +3,15 @@
 //
 // Every shot keeps its own padded grid (its aperture window plus the random
 // boundary) in the pitched, zero-haloed layout; all grids share nz, nb, h,
-// dt and nt.  One kernel launch per time step walks a global work list of
-// (shot, tile) items with persistent blocks, so shots of any width share the
-// machine without a tail per shot; the shot descriptors live in device memory
-// and each time loop is one CUDA graph replayed for every batch.  Rows per
-// warp of the forward and reverse kernels are chosen at creation by timing
-// the candidates on the batch itself.
+// dt and nt.  One kernel launch per time step walks a work list of (shot,
+// tile) items with persistent blocks, so shots of any width share the
+// machine without a tail per shot; the shot descriptors live in device
+// memory.  The shots run in groups of consecutive shots whose fields fit in
+// L2 (each group's whole forward loop, then its whole reverse loop, over the
+// group's contiguous range of the work list), and every group's two loops
+// are CUDA graphs replayed for every batch.  Rows per warp of the forward
+// and reverse kernels are chosen at creation by timing the candidates on the
+// first group.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
