@@ -1,0 +1,56 @@
+"""Host logic of the denoiser driver: the training pairs' scaling, the error
+measure and the fallback to the K-stack, on CPU tensors (no kernels run)."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2204_03380_gb300 import denoise as D  # noqa: E402
+
+
+def _set(models=3, K=4, n=6, seed=0):
+    g = torch.Generator().manual_seed(seed)
+    return D.ImageSet(torch.randn((models, K, n, n), generator=g, dtype=torch.float64))
+
+
+def test_single_and_stack_views():
+    s = _set()
+    assert torch.equal(s.single, s.images[:, 0])
+    assert torch.allclose(s.stack, s.images.mean(dim=1))
+
+
+def test_pairs_are_scaled_by_the_input_rms_only():
+    s = _set()
+    x, t, scale = D.normalized_pairs(s)
+    # every input has unit RMS; the target carries the same per-model factor
+    assert torch.allclose(x.pow(2).mean(dim=(1, 2)), torch.ones(3, dtype=torch.float64))
+    assert torch.allclose(t * scale, s.stack) and torch.allclose(x * scale, s.single)
+    # scaling a model's realizations leaves its pair unchanged
+    s2 = D.ImageSet(s.images.clone())
+    s2.images[1] *= 7.0
+    x2, t2, _ = D.normalized_pairs(s2)
+    assert torch.allclose(x2, x) and torch.allclose(t2, t)
+
+
+def test_rel_l2():
+    b = torch.tensor([3.0, 4.0])
+    assert D.rel_l2(b, b) == 0.0
+    assert D.rel_l2(torch.zeros(2), b) == pytest.approx(1.0)
+    assert D.rel_l2(b * 1.1, b) == pytest.approx(0.1)
+
+
+def test_fallback_to_the_k_stack():
+    calls = []
+
+    def net(x):
+        return x + 1
+
+    def stack_fn():
+        calls.append(1)
+        return "stack"
+
+    single = torch.zeros(2)
+    out, which = D.denoise_or_stack(net, single, stack_fn, val_error=0.04)
+    assert which == "network" and torch.equal(out, single + 1) and not calls
+    out, which = D.denoise_or_stack(net, single, stack_fn, val_error=0.06)
+    assert which == "k-stack" and out == "stack" and calls == [1]
+    assert D.denoise_or_stack(net, single, stack_fn, val_error=0.05)[1] == "network"
