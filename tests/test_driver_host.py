@@ -1,5 +1,6 @@
-"""Host logic of the denoiser driver: the training pairs' scaling, the error
-measure and the fallback to the K-stack, on CPU tensors (no kernels run)."""
+"""Host logic of the Python drivers above the ABI, on CPU tensors (no kernels
+run): the denoiser's training-pair scaling, error measure and fallback to the
+K-stack, and the FWI function's shots in flight."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -54,3 +55,16 @@ def test_fallback_to_the_k_stack():
     out, which = D.denoise_or_stack(net, single, stack_fn, val_error=0.06)
     assert which == "k-stack" and out == "stack" and calls == [1]
     assert D.denoise_or_stack(net, single, stack_fn, val_error=0.05)[1] == "network"
+
+
+def test_fwi_shots_in_flight():
+    """The FWI autograd function runs several shots at once only while their
+    contexts' fields stay within the pool's L2-sized budget."""
+    import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300 import fwi
+    small = R.make_grid(2, 300, 1, 300, 50, 10.0, 1e-3, 1000)      # 0.64 MB per field
+    assert fwi.shot_streams(small, 4) == 4 and fwi.shot_streams(small, 2) == 2 and fwi.shot_streams(small, 9) == 4
+    survey = R.make_grid(2, 2301, 1, 751, 60, 4.0, 4e-4, 12500)   # 8.4 MB per field
+    assert fwi.shot_streams(survey, 8) == 1
+    assert fwi._grid_key(small) != fwi._grid_key(survey)
+    assert fwi._grid_key(small) == fwi._grid_key(R.make_grid(2, 300, 1, 300, 50, 10.0, 1e-3, 1000))
