@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--shots-per-step", type=int, default=None, help="default 8 (survey2d), 1 (shot3d)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-3d", action="store_true",
+                   help="survey2d: skip the 3-D shot sub-record (one 500 x 500 x 300 + 40 shot of 3000 steps "
+                        "after the survey; also skipped with --nt / --interior and on more than one GPU)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--nt", type=int, default=None,
                    help="record length override (default: the workload's full record); only for "
@@ -151,11 +154,8 @@ def smi_device_id(torch, dev_index: int) -> str:
 def shot_plan(nshots_total: int, steps: int, warmup: int, per_step: int, rank: int, world: int):
     """Shots of every (warm-up then timed) step on this rank: disjoint across
     ranks within a step, cycling through the survey."""
-    plan = []
-    for s in range(warmup + steps):
-        base = (s * world + rank) * per_step
-        plan.append([(base + k) % nshots_total for k in range(per_step)])
-    return plan
+    from paper_2204_03380_gb300.survey import shard_shots
+    return shard_shots(nshots_total, rank, world, per_step, steps, warmup)
 
 
 def updates_per_shot(w) -> int:
@@ -210,32 +210,42 @@ def load_workload(W, args):
     return w, inp
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the fused
-# reverse kernels from ncu captures (profiles/), recorded with a hash of the
-# kernel sources they were taken on: a capture of older sources reads as null.
-#   2-D survey grid, warm L2 (the time loop's state): 27.8 MB per launch.
-#   3-D: captured on the 380 x 380 x 280 grid at 1.122 x the algorithmic bytes;
-#   the traffic grows in proportion, so the full launch gets 1.122 x its own.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the stencil
+# kernels from ncu captures (profiles/), recorded with a hash of the kernel
+# sources they were taken on: a capture of older sources reads as null.
+#   k_rev2d on the 2-D survey grid, warm L2 (the time loop's state): bytes per launch.
+#   3-D kernels: captured on the 380 x 380 x 280 grid as a multiple of their
+#   algorithmic bytes; the traffic of their tiles grows in proportion to the
+#   nodes, so a full 580 x 580 x 380 launch gets that multiple of its own.
+_SRC2 = ["rbc_kernels.cu", "rbc_tile2d.cuh", "rbc_stencil.cuh", "rbc_internal.cuh"]
+_SRC3 = ["rbc_kernels3d.cu", "rbc_stencil.cuh", "rbc_internal.cuh"]
 TRAFFIC = {
-    2: {"sources": ["rbc_kernels.cu", "rbc_tile2d.cuh", "rbc_stencil.cuh", "rbc_internal.cuh"],
-        "sha1": "5fe0dda59493d4db", "bytes_per_launch": 27.8e6, "ratio": None},
-    3: {"sources": ["rbc_kernels3d.cu", "rbc_stencil.cuh", "rbc_internal.cuh"],
-        "sha1": "f496bf492f99cf4a", "bytes_per_launch": None, "ratio": 1.122},
+    "k_rev2d": {"sources": _SRC2, "sha1": "5fe0dda59493d4db", "bytes_per_launch": 27.8e6, "ratio": None},
+    "k_rev3d_tma": {"sources": _SRC3, "sha1": "f496bf492f99cf4a", "bytes_per_launch": None, "ratio": 1.122},
+    "k_fwd3d_tma": {"sources": _SRC3, "sha1": "f496bf492f99cf4a", "bytes_per_launch": None, "ratio": 1.087},
 }
 
 
-def reverse_traffic(ndim, algorithmic_bytes):
-    """Per-launch DRAM traffic of the fused reverse kernel from the recorded
-    ncu capture, or None when the kernel sources changed since."""
+def sources_sha(files):
     import hashlib
-    t = TRAFFIC[ndim]
     m = hashlib.sha1()
-    for f in t["sources"]:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2204_03380_gb300", "csrc", f), "rb") as fh:
             m.update(fh.read())
-    if m.hexdigest()[:16] != t["sha1"]:
+    return m.hexdigest()[:16]
+
+
+def kernel_traffic(kernel, algorithmic_bytes):
+    """Per-launch DRAM traffic of a kernel from its recorded ncu capture, or
+    None when the kernel sources changed since."""
+    t = TRAFFIC[kernel]
+    if sources_sha(t["sources"]) != t["sha1"]:
         return None
     return t["bytes_per_launch"] if t["bytes_per_launch"] else t["ratio"] * algorithmic_bytes
+
+
+def reverse_traffic(ndim, algorithmic_bytes):
+    return kernel_traffic("k_rev2d" if ndim == 2 else "k_rev3d_tma", algorithmic_bytes)
 
 
 def measured_peaks():
@@ -735,6 +745,76 @@ def run_fwi(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def shot3d_subrecord(R, W, torch, dev, peaks, warmup=1, shots=1):
+    """The 3-D shot workload (500 x 500 x 300 + 40 = 580 x 580 x 380 padded,
+    3000 steps of 1 ms, 62 500 surface receivers): `shots` RTM shots of
+    Algorithm 3 timed with CUDA events after `warmup` shots, on inputs
+    resident in HBM (the 4 GB of fields exceed L2 by 30x).  Returns s per
+    shot, Gpts/s, the HBM roofline of its two stencil kernels and the clocks
+    sampled while it ran."""
+    a3 = argparse.Namespace(workload="shot3d", interior=None, nt=None)
+    w, inp = load_workload(W, a3)
+    g = R.make_grid(3, w.nx, w.ny, w.nz, w.nb, w.h, w.dt, w.nt)
+    a = torch.empty(g.padded, dtype=torch.float32, device=dev)
+    R.rbc_build_velocity(g, torch.tensor(inp["v_true"], dtype=torch.float32, device=dev), w.v_lo, w.v_hi,
+                         w.v_max, w.rbc_seed, 0, None, a)
+    wav = torch.tensor(inp["wavelet"], dtype=torch.float32, device=dev)
+    rec, src = inp["rec"], inp["srcs"][0]
+    seis = torch.empty((len(rec), w.nt + 1), dtype=torch.float32, device=dev)
+    ctx = R.rbc_create(g, a)
+    R.rbc_model(ctx, src, wav, rec, seis)          # the shot's observed record (setup, untimed)
+    torch.cuda.synchronize()
+    R.rbc_destroy(ctx)
+    R.rbc_build_velocity(g, torch.tensor(inp["v_mig"], dtype=torch.float32, device=dev), w.v_lo, w.v_hi,
+                         w.v_max, w.rbc_seed, 0, None, a)
+    ctx = R.rbc_create(g, a)
+    del a
+    num = torch.empty(g.interior, dtype=torch.float32, device=dev)
+    den = torch.empty_like(num)
+    image = torch.zeros_like(num)
+    flags = R.RBC_REINJECT_SOURCE | R.RBC_ZERO_FIRST
+    try:
+        for _ in range(warmup):
+            R.rbc_rtm_shot(ctx, src, wav, rec, seis, flags, num, den)
+            R.rbc_image_stack(g, num, den, EPS_REL, 0, 0, g, image)
+        torch.cuda.synchronize()
+        smi = ClockSampler(smi_device_id(torch, dev.index or 0))
+        smi.start()
+        time.sleep(0.3)
+        R.rbc_phase_timing(ctx, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(shots):
+            R.rbc_rtm_shot(ctx, src, wav, rec, seis, flags, num, den)
+            R.rbc_image_stack(g, num, den, EPS_REL, 0, 0, g, image)
+        ev1.record()
+        torch.cuda.synchronize()
+        phases = R.rbc_phase_timing(ctx, False)
+        clocks = smi.stop()
+    finally:
+        R.rbc_destroy(ctx)
+    el = ev0.elapsed_time(ev1) / 1e3 / shots
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    rev_s = phases["rev_ms"] / 1e3 / max(phases["rev_launches"], 1)
+    fwd_s = phases["fwd_ms"] / 1e3 / max(phases["fwd_launches"], 1)
+    rb, fb = rev_bytes_per_launch(w), fwd_bytes_per_launch(w)
+    src_note = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    return {"workload": w.name, "padded_grid": list(w.padded[::-1]), "nt": w.nt, "receivers": int(len(rec)),
+            "shots_timed": shots, "s_per_shot": el, "value": updates_per_shot(w) / el / 1e9, "unit": "Gpts/s",
+            "target_s_per_shot": 4.9,
+            "roofline": {"bound": "hbm", "kernel": "k_rev3d_tma (fused reverse pass)",
+                         "achieved": rb / rev_s / 1e9, "peak": peak, "unit": "GB/s", "frac": rb / rev_s / 1e9 / peak,
+                         "peak_source": src_note, "traffic": kernel_traffic("k_rev3d_tma", rb),
+                         "traffic_source": "ncu dram bytes of k_rev3d_tma on 380x380x280, scaled by the "
+                                           "algorithmic bytes",
+                         "bytes_per_launch": rb, "launch_us": rev_s * 1e6,
+                         "forward_kernel": {"kernel": "k_fwd3d_tma", "achieved": fb / fwd_s / 1e9,
+                                            "frac": fb / fwd_s / 1e9 / peak,
+                                            "traffic": kernel_traffic("k_fwd3d_tma", fb),
+                                            "launch_us": fwd_s * 1e6, "bytes_per_launch": fb}},
+            "clocks": clocks}
+
+
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
@@ -785,6 +865,7 @@ def main():
         return
     import torch
     import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300.survey import reduce_image
     import workloads as W
 
     torch.cuda.set_device(local)
@@ -852,6 +933,7 @@ def main():
     smi = ClockSampler(smi_device_id(torch, local))
     smi.start()
     time.sleep(0.3)
+    image.zero_()              # the timed steps' survey image
     R.rbc_launch_count(reset=True)
     R.rbc_phase_timing(ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -861,6 +943,7 @@ def main():
         flush.zero_()
         for shot in plan[s]:
             migrate(shot, seis[shot])
+    reduce_image(image)        # Algorithm 3's stack over every rank's shots (no-op on one GPU)
     ev1.record()
     barrier()
     phases = R.rbc_phase_timing(ctx, False)
@@ -882,6 +965,7 @@ def main():
         host = {s: seis[s].cpu().pin_memory() for s in needed}
         stage = [torch.empty((nrec, w.nt + 1), dtype=torch.float32, device=dev) for _ in range(B)]
         img_host = torch.empty(g.interior, dtype=torch.float32).pin_memory()
+        image.zero_()
         barrier()
         t0 = time.perf_counter()
         ev0.record()
@@ -891,6 +975,8 @@ def main():
                 stage[k].copy_(host[shot], non_blocking=True)
                 migrate(shot, stage[k])
             img_host.copy_(image, non_blocking=True)
+        reduce_image(image)
+        img_host.copy_(image, non_blocking=True)
         ev1.record()
         barrier()
         el_e2e = max(ev0.elapsed_time(ev1) / 1e3, 0.0)
@@ -937,6 +1023,7 @@ def main():
                     "forward_phase": {"bytes": fb, "s": fwd_s, "GB/s": fb / fwd_s / 1e9},
                     "reverse_phase": {"bytes": rb, "s": rev_s, "GB/s": rb / rev_s / 1e9}}
     if rank != 0:
+        R.rbc_destroy(ctx)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -947,6 +1034,14 @@ def main():
         cpu = {"value": v, "unit": "Gpts/s", "cores": cores_used(), "kind": "oracle",
                "sample": f"one full-grid shot ({'x'.join(map(str, w.padded[::-1]))} padded) of Algorithm 3 "
                          f"with {ns} of the {w.nt} time steps, {dt:.1f} s"}
+    R.rbc_destroy(ctx)
+    ctx = None
+    shot3d = None
+    if (args.workload == "survey2d" and not storage and world == 1 and not args.no_3d and not args.nt
+            and not args.interior):
+        del seis, num, den, flush
+        torch.cuda.empty_cache()
+        shot3d = shot3d_subrecord(R, W, torch, dev, peaks)
     out = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -963,8 +1058,9 @@ def main():
                                 "rbc: Algorithm 3, reconstruction through the random boundary"},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": clocks}
+    if shot3d is not None:
+        out["shot3d"] = shot3d
     print(json.dumps(out), flush=True)
-    R.rbc_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
 

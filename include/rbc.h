@@ -390,18 +390,24 @@ int rbc_get_panels(rbc_ctx *ctx, float *prev_dev, float *last_dev,
 int rbc_phase_timing(rbc_ctx *ctx, int enable, double *out);
 
 /*
- * rbc_model_static -- the same seismic modeling as rbc_model (Algorithm 1,
- * one shot), for callers that cannot allocate device memory.  The paper has
- * no counterpart: it is an interface addition.
+ * rbc_model_static -- the same seismic modeling as rbc_model (one shot), for
+ * callers that cannot allocate device memory.  The paper has no counterpart:
+ * it is an interface addition.
  *   Some callers cannot call cudaMalloc: code that runs while a caching
  *   allocator owns (or has exhausted) the device heap, plugins whose host
  *   runtime forbids allocation on its worker threads, and real-time loops
  *   where an allocation's implicit synchronisation or failure is not
- *   acceptable.  This call needs no context and allocates nothing: its
- *   scratch (coefficient in the zero-haloed layout, two wavefield panels,
- *   the time-major record, the shot tables) lives in one file-scope device
- *   array of 16 MiB (4 Mi floats) that every GPU loading the library holds
- *   until the process exits.
+ *   acceptable.  This call needs no context and calls no allocator: its
+ *   scratch (coefficient in the zero-haloed layout, two wavefield panels, the
+ *   time-major record, the shot tables) lives in one file-scope device array
+ *   of 16 MiB (4 Mi floats) inside the library.
+ *   Placement of that array: CUDA loads the library's modules lazily by
+ *   default, so the array is placed on a device when the first call on that
+ *   device looks up its address (with that device current).  A caller whose
+ *   heap may be exhausted later should make one small call early (or run with
+ *   CUDA_MODULE_LOADING=EAGER, which places it when the CUDA context is
+ *   created).  Once placed, it stays until the process exits.  Make the first
+ *   call on a device before any stream capture starts.
  *   Arguments are those of rbc_create (grid, a_dev) and rbc_model (source,
  *   wavelet, receivers, seis_dev [nrec][nt + 1] output), all caller-owned.
  *   Grids and records whose scratch exceeds the 16 MiB maximum return
@@ -409,10 +415,14 @@ int rbc_phase_timing(rbc_ctx *ctx, int enable, double *out);
  *   All calls on a device share the array and it keeps the previous call's
  *   contents; each call clears its fields itself.  Calls whose work overlaps
  *   on the GPU (other streams or host threads) race on the array: serialise
- *   them.  The first call on a device looks up the array's device address
- *   with that device current; make it before any stream capture starts.
- *   The stability check of rbc_create runs first and waits on `stream`.
- * Errors: RBC_EINVAL, RBC_ECFL, RBC_ENOTSUP (free_surface), RBC_ECUDA.
+ *   them.  The stability check of rbc_create runs first and waits on
+ *   `stream`.
+ *   Failure reporting is deferred, as for contexts: a bounded device wait of
+ *   the 3-D kernels that gives up is recorded in the array, and the NEXT call
+ *   on that device returns RBC_ETIMEOUT (that earlier record is invalid; the
+ *   reporting call does no work and clears the record).
+ * Errors: RBC_EINVAL, RBC_ECFL, RBC_ETIMEOUT, RBC_ENOTSUP (free_surface),
+ * RBC_ECUDA.
  */
 int rbc_model_static(const rbc_grid *g, const float *a_dev,
                      const int *src_host, const float *wavelet_dev, int nrec,
@@ -426,7 +436,9 @@ int rbc_model_static(const rbc_grid *g, const float *a_dev,
  * timeout in the context's error word, drains its other copies and leaves,
  * and the next call on the context returns RBC_ETIMEOUT (the results of the
  * faulted call are invalid).  Nothing faults, traps or hangs.  mode 0
- * clears a pending request.  Errors: RBC_EINVAL, RBC_ENOTSUP (2-D).
+ * clears a pending request.  With ctx = NULL the request applies to the next
+ * 3-D rbc_model_static call instead (reported by the call after it).
+ * Errors: RBC_EINVAL, RBC_ENOTSUP (2-D context).
  */
 int rbc_inject_fault(rbc_ctx *ctx, int mode);
 

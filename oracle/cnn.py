@@ -5,7 +5,8 @@ convolutions with zero padding, channels 1 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
 after the first four, the input added to the output.  Parameter vector
 [W1 b1 W2 b2 W3 b3 W4 b4 W5 b5], each W stored [tap][out][in] with
 tap = 3 (dy + 1) + (dx + 1) for the input offset (dy, dx) in {-1, 0, 1}^2.
-Images are (nimg, H, W).  The backward pass is the chain rule written out.
+Images are (nimg, H, W).  The backward pass is the chain rule written out;
+the optimiser is Adam (Kingma & Ba 2015, Algorithm 1).
 """
 from __future__ import annotations
 
@@ -92,6 +93,23 @@ def backward(params, cache, dy):
 
 def mse(y, t):
     return float(np.mean((y - t) ** 2))
+
+
+def adam(params, grad, m, v, lr, b1, b2, eps, step):
+    """One Adam step (Kingma & Ba 2015, Algorithm 1), in fp64: the moment
+    estimates are updated with the new gradient, divided by the bias
+    corrections 1 - b1^step and 1 - b2^step, and the parameters move by
+    lr * m_hat / (sqrt(v_hat) + eps).  step counts from 1.  Returns the new
+    (params, m, v); the inputs are left unchanged."""
+    if step < 1:
+        raise ValueError("step counts from 1")
+    g = np.asarray(grad, np.float64)
+    m_new = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v_new = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    m_hat = m_new / (1.0 - b1 ** step)
+    v_hat = v_new / (1.0 - b2 ** step)
+    p_new = np.asarray(params, np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return p_new, m_new, v_new
 
 
 def init_params(seed=0):

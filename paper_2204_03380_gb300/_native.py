@@ -383,7 +383,8 @@ def rbc_cnn_adam(params, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-8, strea
 
 def rbc_inject_fault(ctx, mode=1):
     """Test hook: make the next call's first 3-D forward launch run a bounded
-    wait out (see include/rbc.h); the call after it reports RBC_ETIMEOUT."""
+    wait out (see include/rbc.h); the call after it reports RBC_ETIMEOUT.
+    ctx = None arms the next 3-D rbc_model_static call instead."""
     _check(_lib.rbc_inject_fault(C.c_void_p(ctx), int(mode)))
 
 

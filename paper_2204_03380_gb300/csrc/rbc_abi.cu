@@ -63,25 +63,13 @@ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 // half the stencil length (4) of zero-pressure rows.
 inline int top_rows(const rbc_grid *g) { return g->free_surface ? kHaloR : g->nb; }
 
-Lay make_layout(const rbc_grid *g) {
-  Lay L;
-  L.ndim = g->ndim;
-  L.NX = g->nx + 2 * g->nb;
-  L.NY = (g->ndim == 3) ? g->ny + 2 * g->nb : 1;
-  L.NZ = g->nz + g->nb + top_rows(g);
-  L.NX4 = (L.NX + 3) / 4 * 4;
-  L.pitch = cdiv(L.NX, kTileX) * kTileX + 2 * kHaloX;
-  if (g->ndim == 2) {
-    L.rows = 1;
-    L.plane = L.pitch;
-    L.origin = kHaloR * L.plane + kHaloX;
-  } else {
-    L.rows = cdiv(L.NY, k3dBY) * k3dBY + 2 * kHaloR;
-    L.plane = L.pitch * L.rows;
-    L.origin = kHaloR * L.plane + kHaloR * L.pitch + kHaloX;
-  }
-  L.total = (long long)(L.NZ + 2 * kHaloR) * L.plane;
-  return L;
+// The context layout of grid g; false when a buffer would not be
+// addressable by 32-bit offsets (extents formed in 64-bit first).
+bool make_layout(const rbc_grid *g, Lay *L) {
+  const long long NX = (long long)g->nx + 2LL * g->nb;
+  const long long NY = (g->ndim == 3) ? (long long)g->ny + 2LL * g->nb : 1;
+  const long long NZ = (long long)g->nz + g->nb + top_rows(g);
+  return lay_make(g->ndim, NX, NY, NZ, L);
 }
 
 } // namespace
@@ -94,6 +82,7 @@ int set_error(int code, const char *msg) {
 }
 // Count kernel launches queued by another translation unit.
 void add_launches(long long n) { g_launches += n; }
+void static_inject_fault(int mode);  // rbc_static.cu
 } // namespace rbc
 
 struct rbc_ctx {
@@ -550,8 +539,8 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   if (rc) return rc;
   if (!a_dev || !out) return fail(RBC_EINVAL, "a_dev and out must not be NULL");
   *out = nullptr;
-  Lay L = make_layout(g);
-  if (L.total * 1 >= (1LL << 31)) return fail(RBC_EINVAL, "grid too large for 32-bit offsets (%lld floats)", L.total);
+  Lay L;
+  if (!make_layout(g, &L)) return fail(RBC_EINVAL, "grid too large for 32-bit offsets");
   // stability: max(a) * ndim * |symbol|max < 4
   const long long n = (long long)L.NX * L.NY * L.NZ;
   unsigned int *dmax = nullptr;
@@ -932,8 +921,11 @@ int rbc_phase_timing(rbc_ctx *c, int enable, double *out) {
 }
 
 int rbc_inject_fault(rbc_ctx *c, int mode) {
-  if (!c) return fail(RBC_EINVAL, "ctx is NULL");
   if (mode != 0 && mode != 1) return fail(RBC_EINVAL, "unknown fault mode %d", mode);
+  if (!c) {  // the next 3-D rbc_model_static call
+    static_inject_fault(mode);
+    return RBC_OK;
+  }
   if (mode == 1 && c->L.ndim != 3) return fail(RBC_ENOTSUP, "fault mode 1 needs a 3-D context");
   c->fault = mode;
   return RBC_OK;

@@ -797,16 +797,10 @@ int rbc_batch_create(const rbc_grid *g, int nshots, const int *nx_host, const fl
     }
     b->nx.push_back(nx_host[s]);
     Lay L;
-    L.ndim = 2;
-    L.NX = nx_host[s] + 2 * g->nb;
-    L.NY = 1;
-    L.NZ = g->nz + 2 * g->nb;
-    L.NX4 = (L.NX + 3) / 4 * 4;
-    L.pitch = cdiv(L.NX, kTileX) * kTileX + 2 * kHaloX;
-    L.rows = 1;
-    L.plane = L.pitch;
-    L.origin = kHaloR * L.plane + kHaloX;
-    L.total = (long long)(L.NZ + 2 * kHaloR) * L.plane;
+    if (!lay_make(2, (long long)nx_host[s] + 2LL * g->nb, 1, (long long)g->nz + 2LL * g->nb, &L)) {
+      delete b;
+      return bfail(RBC_EINVAL, "rbc_batch_create: shot %d is too large for 32-bit offsets", s);
+    }
     b->L.push_back(L);
     total += 7 * (size_t)L.total;
   }

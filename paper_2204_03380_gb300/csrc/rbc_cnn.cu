@@ -823,7 +823,8 @@ int rbc_cnn_mse(const float *y_dev, const float *t_dev, long long n, float *dy_d
 int rbc_cnn_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, float lr, float b1, float b2,
                  float eps, int step, void *stream) {
   if (!params_dev || !grad_dev || !m_dev || !v_dev || step < 1) return rbc::set_error(RBC_EINVAL, "rbc_cnn_adam: bad arguments");
-  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  // bias corrections formed in fp64: 1 - b2^step cancels badly in fp32 at small steps
+  const float c1 = (float)(1.0 - pow((double)b1, (double)step)), c2 = (float)(1.0 - pow((double)b2, (double)step));
   k_adam<<<grid_of(kNParams), 256, 0, (cudaStream_t)stream>>>(params_dev, grad_dev, m_dev, v_dev, kNParams, lr, b1, b2,
                                                               eps, c1, c2);
   rbc::add_launches(1);

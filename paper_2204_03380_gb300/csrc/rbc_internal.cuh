@@ -129,6 +129,35 @@ constexpr int k2dRowsR = 2;   // rows per warp, reverse kernel (swept: 1, 2, 3, 
 constexpr int k3dBY = 16;     // y rows covered by the layout's row padding (3-D)
 constexpr int k3dZC = 32;     // z planes per block (3-D)
 
+// Fill L for a padded grid NX x NY x NZ (NY = 1 in 2-D).  Every extent and
+// offset is formed in 64-bit first: the grid is refused (false, L untouched)
+// when a buffer would not be addressable by the kernels' 32-bit offsets.
+inline bool lay_make(int ndim, long long NX, long long NY, long long NZ, Lay *out) {
+  if (NX < 1 || NY < 1 || NZ < 1 || NX >= (1LL << 31) || NY >= (1LL << 31) || NZ >= (1LL << 31)) return false;
+  const long long pitch = (NX + kTileX - 1) / kTileX * kTileX + 2 * kHaloX;
+  long long rows = 1, plane = pitch, origin = kHaloR * pitch + kHaloX;
+  if (ndim == 3) {
+    rows = (NY + k3dBY - 1) / k3dBY * k3dBY + 2 * kHaloR;
+    plane = pitch * rows;
+    origin = kHaloR * plane + kHaloR * pitch + kHaloX;
+  }
+  const long long total = (NZ + 2 * kHaloR) * plane;
+  if (total >= (1LL << 31)) return false;
+  Lay L;
+  L.ndim = ndim;
+  L.NX = (int)NX;
+  L.NY = (int)NY;
+  L.NZ = (int)NZ;
+  L.NX4 = (int)((NX + 3) / 4 * 4);
+  L.pitch = (int)pitch;
+  L.rows = (int)rows;
+  L.plane = (int)plane;
+  L.origin = (int)origin;
+  L.total = total;
+  *out = L;
+  return true;
+}
+
 } // namespace rbc
 
 // kernel launchers (rbc_kernels.cu)

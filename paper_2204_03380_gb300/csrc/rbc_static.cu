@@ -24,6 +24,7 @@
 //   * the call checks stability like rbc_create, which waits on `stream`.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -45,6 +46,8 @@ static __device__ __align__(256) float g_static_ws[kStaticFloats];
 
 std::mutex g_static_mu;
 float *g_static_ptr[kMaxDevices] = {nullptr};
+// rbc_inject_fault(NULL, 1): the next 3-D call withholds one TMA plane copy
+std::atomic<int> g_static_fault{0};
 
 
 // The record and tables sit after the three fields; 64-float (256-byte)
@@ -78,6 +81,12 @@ int static_workspace(float **out) {
 
 } // namespace
 
+namespace rbc {
+// Arm (mode 1) or clear (mode 0) the withheld-copy test fault of the next
+// 3-D rbc_model_static call (rbc_inject_fault with a NULL context).
+void static_inject_fault(int mode) { g_static_fault.store(mode); }
+} // namespace rbc
+
 extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int *src_host,
                                 const float *wavelet_dev, int nrec, const int *rec_host, float *seis_dev,
                                 void *stream) {
@@ -87,24 +96,13 @@ extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int
       g->nt < 1 || !(g->h > 0) || !(g->dt > 0))
     return set_err(RBC_EINVAL, "rbc_model_static: bad grid");
   if (g->free_surface != 0) return set_err(RBC_ENOTSUP, "rbc_model_static: free_surface is not supported");
-  // the same layout as a context's fields
+  // the same layout as a context's fields, extents formed in 64-bit before
+  // any 32-bit field is set
   Lay L;
-  L.ndim = g->ndim;
-  L.NX = g->nx + 2 * g->nb;
-  L.NY = (g->ndim == 3) ? g->ny + 2 * g->nb : 1;
-  L.NZ = g->nz + 2 * g->nb;
-  L.NX4 = (L.NX + 3) / 4 * 4;
-  L.pitch = (L.NX + kTileX - 1) / kTileX * kTileX + 2 * kHaloX;
-  if (g->ndim == 2) {
-    L.rows = 1;
-    L.plane = L.pitch;
-    L.origin = kHaloR * L.plane + kHaloX;
-  } else {
-    L.rows = (L.NY + k3dBY - 1) / k3dBY * k3dBY + 2 * kHaloR;
-    L.plane = L.pitch * L.rows;
-    L.origin = kHaloR * L.plane + kHaloR * L.pitch + kHaloX;
-  }
-  L.total = (long long)(L.NZ + 2 * kHaloR) * L.plane;
+  if (!lay_make(g->ndim, (long long)g->nx + 2LL * g->nb, g->ndim == 3 ? (long long)g->ny + 2LL * g->nb : 1,
+                (long long)g->nz + 2LL * g->nb, &L) || L.total > kStaticFloats)
+    return set_err(RBC_EINVAL, "rbc_model_static: the grid's fields exceed the static maximum of 4 Mi floats "
+                               "(use rbc_create + rbc_model)");
   const long long o_info = 0;
   const long long o_rec = 64;
   const long long o_wav = o_rec + align64(nrec > 0 ? nrec : 1);
@@ -139,16 +137,23 @@ extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int
   unsigned int *amax = reinterpret_cast<unsigned int *>(ws + o_max);
   float *a = ws + o_a, *p[2] = {ws + o_p0, ws + o_p1}, *seis_t = ws + o_seis;
 
-  // stability, as rbc_create checks it
-  if (cudaMemsetAsync(amax, 0, sizeof(unsigned int), s) != cudaSuccess)
-    return set_err(RBC_ECUDA, "rbc_model_static: memset failed");
+  // Word 0 of the max slot receives max(a); word 1 is the bounded-wait error
+  // word of the 3-D kernels.  The previous call's error word is read back
+  // before both are cleared, together with this call's stability check (as
+  // rbc_create checks it).
+  unsigned int words[2] = {0u, 0u};  // [0]: max(a) bits, [1]: the previous call's error word
+  if (cudaMemcpyAsync(&words[1], amax + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned int), s) != cudaSuccess)
+    return set_err(RBC_ECUDA, "rbc_model_static: workspace words could not be read or cleared");
   launch_max(a_dev, (long long)L.NX * L.NY * L.NZ, amax, s);
-  unsigned int bits = 0;
-  if (cudaMemcpyAsync(&bits, amax, sizeof bits, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(&words[0], amax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return set_err(RBC_ECUDA, "rbc_model_static: stability check failed");
+  if (words[1] != 0u)
+    return set_err(RBC_ETIMEOUT, "rbc_model_static: a bounded wait of the previous call gave up (data in flight "
+                                 "did not arrive); that call's record is invalid; this call did no work");
   float am;
-  memcpy(&am, &bits, sizeof am);
+  memcpy(&am, &words[0], sizeof am);
   if (!(am * g->ndim * kSymbolMax < 4.0)) return set_err(RBC_ECFL, "rbc_model_static: unstable (v dt/h)^2");
 
   // tables of this shot
@@ -159,6 +164,7 @@ extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int
   hi.src_fwd = (float)ps;
   hi.src_rev = (float)ps;
   hi.rec_scale = (float)ps;
+  hi.fault = (L.ndim == 3) ? g_static_fault.exchange(0) : 0;
   std::vector<int> off(nrec > 0 ? nrec : 1);
   for (int r = 0; r < nrec; ++r) off[r] = lay_off(L, rec_host[3 * r], rec_host[3 * r + 1], rec_host[3 * r + 2]);
   // the workspace keeps the last call's contents: clear the three fields
@@ -178,7 +184,7 @@ extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int
   A.seis_t = seis_t;
   A.sample = nrec > 0 ? 1 : 0;
   A.zc = k3dZC;
-  A.err = reinterpret_cast<int *>(amax) + 1;  // bounded-wait error word (not reported)
+  A.err = reinterpret_cast<int *>(amax) + 1;  // bounded-wait error word, reported by the next call
   for (int n = 0; n < g->nt; ++n) {
     A.cur = p[n & 1];
     A.nxt = p[(n + 1) & 1];

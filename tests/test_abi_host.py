@@ -73,7 +73,9 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert lib.rbc_fwi_backward(None, None, None, 1, None, None, None, None, None) == 1
     assert lib.rbc_get_panels(None, None, None, None) == 1
     assert lib.rbc_phase_timing(None, 1, None) == 1
-    assert lib.rbc_inject_fault(None, 1) == 1
+    assert lib.rbc_inject_fault(None, 2) == 1          # unknown mode
+    assert lib.rbc_inject_fault(None, 1) == 0          # arms the next 3-D rbc_model_static call
+    assert lib.rbc_inject_fault(None, 0) == 0          # and clears it again
     out_b = C.c_void_p()
     nx1 = (C.c_int * 1)(10)
     assert lib.rbc_batch_create(C.byref(g), 0, nx1, None, C.byref(out_b)) == 1
@@ -93,6 +95,15 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert lib.rbc_cnn_adam(p16, p16, p16, p16, C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999),
                             C.c_float(1e-8), 0, None) == 1
     assert lib.rbc_model_static(None, None, None, None, 0, None, None, None) == 1
+    # grids whose plane (pitch x rows) or buffer exceeds 32-bit offsets are
+    # refused on the host, before any device work, by the context and the
+    # static path alike (the extents are formed in 64-bit first)
+    src = (C.c_int * 3)(5, 5, 1)
+    for big in (R.make_grid(3, 60000, 60000, 1, 2, 10.0, 1e-3, 10), R.make_grid(2, 2000000000, 1, 4, 2, 10.0, 1e-3, 10),
+                R.make_grid(3, 3000, 3000, 300, 2, 10.0, 1e-3, 10)):
+        assert lib.rbc_model_static(C.byref(big), p16, src, p16, 0, None, None, None) == 1
+        out_c = C.c_void_p()
+        assert lib.rbc_create(C.byref(big), p16, C.byref(out_c)) == 1 and not out_c.value
 
 
 def test_nyquist_stride_and_storage_size_on_the_host():

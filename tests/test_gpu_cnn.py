@@ -70,3 +70,32 @@ def test_cnn_adam_steps_reduce_the_loss():
         R.rbc_cnn_adam(P, G, M, V, 2e-3, step)
         losses.append(float(loss))
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+def test_cnn_adam_matches_the_oracle_step_by_step():
+    # rbc_cnn_adam against oracle.cnn.adam (Kingma & Ba 2015, Algorithm 1) on
+    # the same fp32 gradients: parameters and both moments after every step,
+    # element by element; the hyper-parameters are the fp32 values the kernel
+    # receives.  Gradients mix magnitudes (down to eps) and exact zeros.
+    import paper_2204_03380_gb300 as R
+    rng = np.random.default_rng(11)
+    n = R.rbc_cnn_param_count()
+    lr, b1, b2, eps = (float(np.float32(x)) for x in (3e-3, 0.9, 0.999, 1e-8))
+    p = (0.05 * rng.standard_normal(n)).astype(np.float32).astype(np.float64)   # weights of the trained scale
+    m = np.zeros(n)
+    v = np.zeros(n)
+    dev = "cuda"
+    P = torch.tensor(p, dtype=torch.float32, device=dev)
+    M, V = torch.zeros_like(P), torch.zeros_like(P)
+    p0 = p.copy()
+    for step in range(1, 9):
+        g = (rng.standard_normal(n) * 10.0 ** rng.integers(-8, 1, n)).astype(np.float32)
+        g[rng.random(n) < 0.05] = 0.0
+        G = torch.tensor(g, device=dev)
+        R.rbc_cnn_adam(P, G, M, V, lr, step, b1, b2, eps)
+        p, m, v = cnn.adam(p, g.astype(np.float64), m, v, lr, b1, b2, eps, step)
+        torch.cuda.synchronize()
+        assert rel(M.cpu().numpy(), m) <= 1e-6
+        assert rel(V.cpu().numpy(), v) <= 1e-6
+        # the accumulated update (the parameters themselves hide it behind |p|)
+        assert rel(P.cpu().numpy().astype(np.float64) - p0, p - p0) <= 1e-5

@@ -161,3 +161,61 @@ def test_fwi_gradient_of_an_earlier_forward():
     assert float(Ja) == pytest.approx(float(J1), rel=1e-6) and float(Jb) < float(Ja)
     assert rel(va.grad.cpu().numpy(), g_ref.cpu().numpy()) <= 1e-5
     assert rel(vb.grad.cpu().numpy(), g_ref.cpu().numpy()) > 1e-2
+
+
+def test_fwi_gradient_independent_oracle_and_finite_differences_300x300():
+    """The FWI workload as stated (300 x 300 + 50, 1000 steps, 4 shots): the
+    GPU gradient against (a) the oracle's gradient computed on the oracle's
+    own synthetic records and residuals (nothing from the GPU enters it) and
+    (b) central finite differences of the FP64 oracle misfit, summed over the
+    shots, at 20 seeded interior points (delta v = 1e-4 v; edge cells also set
+    the boundary's v_edge, which the gradient holds fixed, so they are left
+    out)."""
+    import paper_2204_03380_gb300 as R
+    from paper_2204_03380_gb300.fwi import fwi_misfit
+    w, vt, v0, shots, rec, wav = _fwi_case(300, 300, 50, 1000, 4)
+
+    def vp_of(v):
+        return oracle.rbc_velocity(v, w.nb, w.v_lo, w.v_hi, w.v_max, w.rbc_seed)
+
+    dobs = [oracle.model(oracle.coef(vp_of(vt), w.dt, w.h)[1].astype(float), w.h, w.nt, s, wav, rec)["seis"]
+            for s in shots]
+    g = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    dev = "cuda"
+    v = torch.tensor(v0, dtype=torch.float32, device=dev, requires_grad=True)
+    wt = torch.tensor(wav, dtype=torch.float32, device=dev)
+    J = fwi_misfit(v, g, shots, wt, rec, [torch.tensor(d, dtype=torch.float32, device=dev) for d in dobs],
+                   (w.v_lo, w.v_hi, w.v_max, w.rbc_seed))
+    J.backward()
+    gg = v.grad.cpu().numpy().astype(np.float64)
+    # (a) the oracle on its own residuals, with the fp32 coefficient the GPU uses
+    a32 = oracle.coef(vp_of(v0), w.dt, w.h)[1].astype(float)
+    J_o, g_o = 0.0, np.zeros(v0.shape)
+    for s, d in zip(shots, dobs):
+        Js, gs = oracle.fwi_grad(a32, w.h, w.dt, w.nt, s, wav, rec, f32(d), w.nb, (w.nx, 1, w.nz))
+        J_o += Js
+        g_o += gs
+    e_a = rel(gg, g_o)
+    print(f"FWI 300x300: misfit GPU {float(J.detach()):.6e} oracle {J_o:.6e}; gradient rel L2 {e_a:.2e}")
+    assert float(J.detach()) == pytest.approx(J_o, rel=1e-4)
+    assert e_a <= TOL
+    # (b) finite differences of the fp64 misfit (fp64 coefficient)
+    rng = np.random.default_rng(20)
+    pts = [(int(rng.integers(1, w.nz - 1)), int(rng.integers(1, w.nx - 1))) for _ in range(20)]
+    gmax = np.abs(gg).max()
+
+    def J64(vv):
+        a = oracle.coef(vp_of(vv), w.dt, w.h)[0]
+        return sum(oracle.misfit(a, w.h, w.nt, s, wav, rec, f32(d)) for s, d in zip(shots, dobs))
+
+    worst = 0.0
+    for iz, ix in pts:
+        dv = 1e-4 * v0[iz, ix]
+        vp, vm = v0.copy(), v0.copy()
+        vp[iz, ix] += dv
+        vm[iz, ix] -= dv
+        fd = (J64(vp) - J64(vm)) / (2 * dv)
+        err = abs(gg[iz, ix] - fd)
+        worst = max(worst, err / gmax)
+        assert err <= 1e-3 * abs(fd) + 1e-4 * gmax, (iz, ix, gg[iz, ix], fd)
+    print(f"FWI 300x300: worst |g - FD| at 20 points {worst:.2e} of max |g|")

@@ -54,3 +54,54 @@ def test_two_ranks_shard_the_survey():
         b = set(plans[1][s * per_step:(s + 1) * per_step])
         assert not (a & b)
     assert set(plans[0]) | set(plans[1]) == set(range(240))
+
+
+def _reduce_worker(rank, world, port, q):
+    """Each rank stacks its own shots' images (fp32 +=, in shot order, as
+    rbc_image_stack does) over a sharded pass of the survey, then the ranks
+    sum their partial images with reduce_image."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import numpy as np
+    from paper_2204_03380_gb300.survey import reduce_image, shard_shots
+    nshots, per_step = 48, 4
+    plan = shard_shots(nshots, rank, world, per_step, steps=nshots // (per_step * world))
+    partial = torch.zeros((17, 29), dtype=torch.float32)
+    for step in plan:
+        for s in step:
+            img = np.random.default_rng(1000 + s).standard_normal((17, 29)).astype(np.float32)
+            partial += torch.from_numpy(img)
+    mine = partial.clone()
+    reduce_image(partial)
+    q.put((rank, mine.numpy(), partial.numpy(), sorted(s for step in plan for s in step)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_sum_their_partial_images():
+    import numpy as np
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    port = _free_port()
+    procs = [ctx.Process(target=_reduce_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict((r, (mine, red, shots)) for r, mine, red, shots in (q.get(), q.get()))
+    (m0, r0, s0), (m1, r1, s1) = got[0], got[1]
+    # every shot of the survey stacked exactly once
+    assert not set(s0) & set(s1) and sorted(s0 + s1) == list(range(48))
+    # both ranks hold the survey image, exactly partial_0 + partial_1 in fp32
+    assert np.array_equal(r0, r1)
+    assert np.array_equal(r0, m0 + m1)
+    # one process stacking all shots in shot order differs only by rounding
+    seq = np.zeros((17, 29), np.float32)
+    mag = np.zeros((17, 29), np.float64)
+    for s in range(48):
+        img = np.random.default_rng(1000 + s).standard_normal((17, 29)).astype(np.float32)
+        seq += img
+        mag += np.abs(img)
+    assert not np.array_equal(r0, seq)        # the orders really differ
+    assert np.all(np.abs(r0.astype(np.float64) - seq) <= 47 * np.finfo(np.float32).eps * mag)
