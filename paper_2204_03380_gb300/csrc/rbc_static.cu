@@ -40,6 +40,7 @@ int set_error(int code, const char *msg);  // rbc_abi.cu
 namespace {
 
 constexpr long long kStaticFloats = 4LL << 20;  // 16 MiB of fp32 workspace
+static_assert(sizeof(ShotInfo) <= 16 * sizeof(float), "the shot tables must end before the header's words");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float g_static_ws[kStaticFloats];
@@ -103,11 +104,15 @@ extern "C" int rbc_model_static(const rbc_grid *g, const float *a_dev, const int
                 (long long)g->nz + 2LL * g->nb, &L) || L.total > kStaticFloats)
     return set_err(RBC_EINVAL, "rbc_model_static: the grid's fields exceed the static maximum of 4 Mi floats "
                                "(use rbc_create + rbc_model)");
+  // A fixed 64-float header holds the shot tables (floats 0..7) and, at
+  // floats 16 and 17, the stability maximum and the bounded-wait error word:
+  // their place does not depend on the call's sizes, so a call reads the
+  // previous call's error word where that call left it.
   const long long o_info = 0;
+  const long long o_max = 16;
   const long long o_rec = 64;
   const long long o_wav = o_rec + align64(nrec > 0 ? nrec : 1);
-  const long long o_max = o_wav + align64(g->nt);
-  const long long o_a = o_max + 64;
+  const long long o_a = o_wav + align64(g->nt);
   const long long o_p0 = o_a + L.total;
   const long long o_p1 = o_p0 + L.total;
   const long long o_seis = o_p1 + L.total;
