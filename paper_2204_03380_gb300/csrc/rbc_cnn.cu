@@ -679,8 +679,16 @@ __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, 
     if (dy) dy[i] = 2.f * d / (float)n;
     acc += (double)d * d;
   }
+  // one atomic per block (atomics of every warp on one address serialise)
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)n);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) atomicAdd(loss, acc / (double)n);
+  }
 }
 
 // Adam (Kingma & Ba 2015) with bias correction.

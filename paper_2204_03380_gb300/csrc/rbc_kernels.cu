@@ -15,6 +15,9 @@
 // neighbours come from the adjacent lanes by warp shuffles (lanes 0/31 fetch
 // the 4-float halo) and the z neighbours from a register queue marching down
 // z.  The 3-D kernels (TMA-fed plane rings) are in rbc_kernels3d.cu.
+#include <cstdio>
+#include <cstdlib>
+
 #include "rbc_tile2d.cuh"
 
 namespace rbc {
@@ -110,23 +113,217 @@ __global__ void __launch_bounds__(32 * k2dWarpsR) k_rev2d(const RevArgs A) {
   griddep_launch();
 }
 
+// ---------------------------------------------- 2-D, shared-memory tiles ----
+// A block of NW warps covers 128 columns x T = NW * RZ rows.  The current
+// level(s) over the tile and its 4-node halo (T + 8 rows x 136 columns) are
+// staged in shared memory by 16-byte cp.async copies of the whole block (each
+// row crosses L2 once per tile instead of (RZ + 8) / RZ times through a
+// per-warp register queue, and no register holds a copy in flight), while
+// every lane loads its own a and p^{n-1} float4s into registers; one barrier,
+// then each warp updates its RZ rows with x and z neighbours from shared
+// memory.  Rows beyond the zero halo below the grid are zero-filled.
+__device__ __forceinline__ void cp_async16z(float *dst, const float *src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+constexpr int kStRow = kTileX + 2 * kHaloR;  // staged floats per row: x0 - 4 .. x0 + 131
+
+// Stage rows Z0 - 4 .. Z0 + T + 3 of `f` (columns X0 - 4 .. X0 + 131) into `s`.
+template <int T>
+__device__ __forceinline__ void stage_rows(const Lay &L, const float *__restrict__ f, float *s, int X0, int Z0,
+                                           int tid, int nthr) {
+  constexpr int kCh = kStRow / 4;  // 16-byte chunks per row
+  for (int i = tid; i < (T + 8) * kCh; i += nthr) {
+    const int r = i / kCh, c = i - r * kCh;
+    const int z = Z0 - kHaloR + r;
+    const bool ok = z < L.NZ + kHaloR;  // rows -4 .. NZ + 3 exist (zero halo); z >= -4 always
+    const float *src = f + (ok ? L.origin + z * L.pitch + X0 - kHaloR + 4 * c : 0);
+    cp_async16z(s + r * kStRow + 4 * c, src, ok);
+  }
+}
+
+// The leapfrog of Eq. 1 for the float4 of lane `lane` in staged row rr
+// (rr = 4 + local row) of `s`.
+__device__ __forceinline__ float4 leap_staged(const float *s, int rr, int lane, const float4 po, const float4 av,
+                                              float4 *cen) {
+  const float *row = s + rr * kStRow + 4 * lane;
+  const float4 lf = *reinterpret_cast<const float4 *>(row);
+  const float4 c = *reinterpret_cast<const float4 *>(row + 4);
+  const float4 rt = *reinterpret_cast<const float4 *>(row + 8);
+  float4 zq[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) zq[k] = *reinterpret_cast<const float4 *>(row + (k - 4) * kStRow + 4);
+  *cen = c;
+  return leap4_2d(lf, c, rt, zq, po, av);
+}
+
+__device__ __forceinline__ float4 staged_c(const float *s, int rr, int lane) {
+  return *reinterpret_cast<const float4 *>(s + rr * kStRow + 4 * lane + 4);
+}
+
+template <int RZ, int NW, int MB>
+__global__ void __launch_bounds__(32 * NW, MB) k_fwd2d_tile(const StepArgs A) {
+  constexpr int T = NW * RZ;
+  __shared__ __align__(16) float s_p[(T + 8) * kStRow];
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+  const int X0 = blockIdx.x * kTileX, Z0 = blockIdx.y * T;
+  const int x0 = X0 + lane * 4, zb = Z0 + w * RZ;
+  const bool xok = x0 < L.NX4;
+  griddep_wait();
+  if (A.sample) sample_receivers(A, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+  stage_rows<T>(L, A.cur, s_p, X0, Z0, tid, 32 * NW);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  float4 av[RZ], po[RZ];
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int o = L.origin + x0 + (zb + j) * L.pitch;
+    const bool ok = xok && zb + j < L.NZ;
+    av[j] = ok ? ldg4(A.a + o) : zero4();
+    po[j] = ok ? ld4(A.nxt + o) : zero4();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int src = A.info->src_off;
+  const float fsrc = A.wav[A.n] * A.info->src_fwd;
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int z = zb + j;
+    if (xok && z < L.NZ) {
+      const int o = L.origin + x0 + z * L.pitch;
+      float4 c;
+      float4 r = leap_staged(s_p, w * RZ + j + kHaloR, lane, po[j], av[j], &c);
+      const int d = src - o;
+      if ((unsigned)d < 4u) point_sub(r, d, cmp(av[j], d) * fsrc);
+      st4(A.nxt + o, r);
+    }
+  }
+  griddep_launch();
+}
+
+template <int RZ, int NW, int MB, bool kGrad>
+__global__ void __launch_bounds__(32 * NW, MB) k_rev2d_tile(const RevArgs A) {
+  constexpr int T = NW * RZ;
+  __shared__ __align__(16) float s_r[(T + 8) * kStRow], s_b[(T + 8) * kStRow];
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+  const int X0 = blockIdx.x * kTileX, Z0 = blockIdx.y * T;
+  const int x0 = X0 + lane * 4, zb = Z0 + w * RZ;
+  const bool xok = x0 < L.NX4;
+  griddep_wait();
+  stage_rows<T>(L, A.rc, s_r, X0, Z0, tid, 32 * NW);
+  stage_rows<T>(L, A.bc, s_b, X0, Z0, tid, 32 * NW);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  float4 av[RZ], pr[RZ], pb[RZ];
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int o = L.origin + x0 + (zb + j) * L.pitch;
+    const bool ok = xok && zb + j < L.NZ;
+    av[j] = ok ? ldg4(A.a + o) : zero4();
+    pr[j] = ok && A.do_r ? ld4(A.rn + o) : zero4();
+    pb[j] = ok && A.do_b ? ld4(A.bn + o) : zero4();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int src = A.info->src_off;
+  const float fsrc = A.do_r ? A.wav[A.n_src] * A.info->src_rev : 0.f;  // f[nt] does not exist
+  const bool img = xok && x0 + 3 >= A.ix0 && x0 < A.ix1;
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int z = zb + j, rr = w * RZ + j + kHaloR;
+    if (!(xok && z < L.NZ)) continue;
+    const int o = L.origin + x0 + z * L.pitch;
+    const int d = src - o;
+    float4 cr = staged_c(s_r, rr, lane), cb = staged_c(s_b, rr, lane), inc = zero4();
+    if (A.do_r) {
+      // Eq. 6: reconstruction (exact inverse of the forward step)
+      float4 r;
+      if (kGrad) {
+        const float *row = s_r + rr * kStRow + 4 * lane;
+        const float4 lf = *reinterpret_cast<const float4 *>(row), rt = *reinterpret_cast<const float4 *>(row + 8);
+        float4 zq[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) zq[k] = *reinterpret_cast<const float4 *>(row + (k - 4) * kStRow + 4);
+        const float w12[12] = {lf.x, lf.y, lf.z, lf.w, cr.x, cr.y, cr.z, cr.w, rt.x, rt.y, rt.z, rt.w};
+        r = leap4p_inc(w12, zq, pr[j], av[j], &inc);
+        if ((unsigned)d < 4u) point_sub(inc, d, cmp(av[j], d) * fsrc);
+      } else {
+        r = leap_staged(s_r, rr, lane, pr[j], av[j], &cr);
+      }
+      if ((unsigned)d < 4u) point_sub(r, d, cmp(av[j], d) * fsrc);
+      st4(A.rn + o, r);
+    }
+    if (A.do_b) {
+      // Eq. 2 (or the FWI adjoint): the record is added below, after the stores
+      st4(A.bn + o, leap_staged(s_b, rr, lane, pb[j], av[j], &cb));
+    }
+    if (img && z >= A.iz0 && z < A.iz1) {
+      if (kGrad) {
+        // FWI: num += mu^m (p^m - 2 p^{m-1} + p^{m-2}) on the interior
+        if (A.do_r) st4(A.num + o, add4(ld4(A.num + o), masked_prod(cb, inc, x0, A.ix0, A.ix1)));
+      } else {
+        // Eq. 3: the two time integrals, interior only
+        st4(A.num + o, add4(ld4(A.num + o), masked_prod(cr, cb, x0, A.ix0, A.ix1)));
+        st4(A.den + o, add4(ld4(A.den + o), masked_prod(cr, cr, x0, A.ix0, A.ix1)));
+      }
+    }
+  }
+  if (A.do_b) inject_receivers(A, blockIdx.y * gridDim.x + blockIdx.x);
+  griddep_launch();
+}
+
 // ------------------------------------------------------------ launchers ----
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// 2-D kernel shapes: 0 = register-queue kernels (k_fwd2d / k_rev2d); 1..5 =
+// shared-memory tiles (rows per warp x warps, resident blocks per SM asked
+// of the compiler): 1 = 2 x 4 (7), 2 = 2 x 8 (3), 3 = 4 x 4 (4), 4 = 1 x 8
+// (4), 5 = 2 x 4 (no register cap).  RBC_TILE2D="fwd,rev" overrides the
+// default (read once per process).
+struct Shape2d { int fwd, rev; };
+static Shape2d shape2d() {
+  static Shape2d sh = [] {
+    Shape2d v{1, 1};
+    const char *e = getenv("RBC_TILE2D");
+    if (e) {
+      int f = -1, r = -1;
+      if (sscanf(e, "%d,%d", &f, &r) == 2 && f >= 0 && f <= 5 && r >= 0 && r <= 5) v = Shape2d{f, r};
+    }
+    return v;
+  }();
+  return sh;
+}
+static int tile_rows_2d(int k, bool fwd) {
+  switch (k) {
+  case 1: case 4: case 5: return 8;
+  case 2: case 3: return 16;
+  default: return fwd ? k2dWarpsF * k2dRowsF : k2dWarpsR * k2dRowsR;
+  }
+}
 
 bool launch_fwd(const StepArgs &A, cudaStream_t s) {
   const Lay &L = A.L;
   if (L.ndim == 3) return launch_fwd3d(A, s);
-  dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, k2dWarpsF * k2dRowsF));
-  launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarpsF), 0, s, A);
+  const int k = shape2d().fwd;
+  dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, tile_rows_2d(k, true)));
+  switch (k) {
+  case 1: launch_pdl(k_fwd2d_tile<2, 4, 7>, grid, dim3(32, 4), 0, s, A); break;
+  case 2: launch_pdl(k_fwd2d_tile<2, 8, 3>, grid, dim3(32, 8), 0, s, A); break;
+  case 3: launch_pdl(k_fwd2d_tile<4, 4, 4>, grid, dim3(32, 4), 0, s, A); break;
+  case 4: launch_pdl(k_fwd2d_tile<1, 8, 4>, grid, dim3(32, 8), 0, s, A); break;
+  case 5: launch_pdl(k_fwd2d_tile<2, 4, 1>, grid, dim3(32, 4), 0, s, A); break;
+  default: launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarpsF), 0, s, A); break;
+  }
   return true;
 }
 
 void rev_tiling(const Lay &L, int zc, int *gx, int *gy, int *gz, int *t) {
   if (L.ndim == 2) {
+    *t = tile_rows_2d(shape2d().rev, false);
     *gx = cdiv(L.NX, kTileX);
-    *gy = cdiv(L.NZ, k2dWarpsR * k2dRowsR);
+    *gy = cdiv(L.NZ, *t);
     *gz = 1;
-    *t = k2dWarpsR * k2dRowsR;
   } else {
     *gx = cdiv(L.NX, kTileX);
     *gy = cdiv(L.NY, tile_rows_3d());
@@ -139,10 +336,18 @@ bool launch_rev(const RevArgs &A, cudaStream_t s) {
   if (A.L.ndim == 3) return launch_rev3d(A, s);
   int gx, gy, gz, t;
   rev_tiling(A.L, A.zc, &gx, &gy, &gz, &t);
-  if (A.mode == 1)
-    launch_pdl(k_rev2d<k2dRowsR, true>, dim3(gx, gy), dim3(32, k2dWarpsR), 0, s, A);
-  else
-    launch_pdl(k_rev2d<k2dRowsR, false>, dim3(gx, gy), dim3(32, k2dWarpsR), 0, s, A);
+  const dim3 grid(gx, gy);
+  const bool g = A.mode == 1;
+  switch (shape2d().rev) {
+  case 1: launch_pdl(g ? k_rev2d_tile<2, 4, 7, true> : k_rev2d_tile<2, 4, 7, false>, grid, dim3(32, 4), 0, s, A); break;
+  case 2: launch_pdl(g ? k_rev2d_tile<2, 8, 3, true> : k_rev2d_tile<2, 8, 3, false>, grid, dim3(32, 8), 0, s, A); break;
+  case 3: launch_pdl(g ? k_rev2d_tile<4, 4, 4, true> : k_rev2d_tile<4, 4, 4, false>, grid, dim3(32, 4), 0, s, A); break;
+  case 4: launch_pdl(g ? k_rev2d_tile<1, 8, 4, true> : k_rev2d_tile<1, 8, 4, false>, grid, dim3(32, 8), 0, s, A); break;
+  case 5: launch_pdl(g ? k_rev2d_tile<2, 4, 1, true> : k_rev2d_tile<2, 4, 1, false>, grid, dim3(32, 4), 0, s, A); break;
+  default:
+    launch_pdl(g ? k_rev2d<k2dRowsR, true> : k_rev2d<k2dRowsR, false>, grid, dim3(32, k2dWarpsR), 0, s, A);
+    break;
+  }
   return true;
 }
 
