@@ -220,9 +220,9 @@ def load_workload(W, args):
 _SRC2 = ["rbc_kernels.cu", "rbc_tile2d.cuh", "rbc_stencil.cuh", "rbc_internal.cuh"]
 _SRC3 = ["rbc_kernels3d.cu", "rbc_stencil.cuh", "rbc_internal.cuh"]
 TRAFFIC = {
-    "k_rev2d": {"sources": _SRC2, "sha1": "5fe0dda59493d4db", "bytes_per_launch": 27.8e6, "ratio": None},
-    "k_rev3d_tma": {"sources": _SRC3, "sha1": "f496bf492f99cf4a", "bytes_per_launch": None, "ratio": 1.122},
-    "k_fwd3d_tma": {"sources": _SRC3, "sha1": "f496bf492f99cf4a", "bytes_per_launch": None, "ratio": 1.087},
+    "k_rev2d_tile": {"sources": _SRC2, "sha1": "", "bytes_per_launch": None, "ratio": None},
+    "k_rev3d_tma": {"sources": _SRC3, "sha1": "ea60ae780e5ae202", "bytes_per_launch": None, "ratio": 1.122},
+    "k_fwd3d_tma": {"sources": _SRC3, "sha1": "ea60ae780e5ae202", "bytes_per_launch": None, "ratio": 1.082},
 }
 
 
@@ -245,7 +245,7 @@ def kernel_traffic(kernel, algorithmic_bytes):
 
 
 def reverse_traffic(ndim, algorithmic_bytes):
-    return kernel_traffic("k_rev2d" if ndim == 2 else "k_rev3d_tma", algorithmic_bytes)
+    return kernel_traffic("k_rev2d_tile" if ndim == 2 else "k_rev3d_tma", algorithmic_bytes)
 
 
 def measured_peaks():
@@ -547,7 +547,7 @@ def run_denoise(args, rank, world):
                                                      "8_stack": e_half, "target": 5e-2},
                       "train_data_s": t_data, "train_s": t_train, "rtm_3d_s": t_rtm, "stack16_s": 16 * t_rtm,
                       "inference_s": t_inf},
-           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05, hidden layers) + k_conv_1to32 + k_conv_32to1", "achieved": achieved,
+           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05: hidden layers and the 32 -> 1 last layer) + k_conv_1to32", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
            "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": None}
@@ -604,7 +604,7 @@ def run_cnn(args, rank, world):
            "data": "synthetic", "config": {"workload": f"cnn: batch of {n} images of {H}x{Wd}",
                                            "train_step_ms": t_train * 1e3, "inference_ms": t_inf * 1e3,
                                            "training_tflops": 3 * 56448.0 * px / t_train / 1e12},
-           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05, hidden layers) + k_conv_1to32 + k_conv_32to1", "achieved": achieved,
+           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05: hidden layers and the 32 -> 1 last layer) + k_conv_1to32", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
            "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": None}
@@ -734,7 +734,7 @@ def run_fwi(args, rank, world):
                       "s_per_gradient": t_grad, "forward_phase_s": t_f, "backward_phase_s": t_b,
                       "shot_streams": shot_streams(g, len(srcs)), "misfit": float(J.detach()),
                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
-           "roofline": {"bound": "hbm", "kernel": "k_rev2d<2, true> (reconstruction + exact adjoint + gradient; "
+           "roofline": {"bound": "hbm", "kernel": "k_rev2d_tile<2, 4, 7, true> (reconstruction + exact adjoint + gradient; "
                                                   "shots on concurrent streams: backward phase / launches)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
@@ -995,13 +995,13 @@ def main():
     rev_launch_s = phases["rev_ms"] / 1e3 / max(phases["rev_launches"], 1)
     achieved = rev_bytes_per_launch(w) / rev_launch_s / 1e9
     fwd_launch_s = phases["fwd_ms"] / 1e3 / max(phases["fwd_launches"], 1)
-    kname = "k_rev2d" if w.ndim == 2 else "k_rev3d_tma"
+    kname = "k_rev2d_tile" if w.ndim == 2 else "k_rev3d_tma"
     roofline = {"bound": "hbm", "kernel": f"{kname} (fused reverse pass)", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
                 "traffic": (reverse_traffic(w.ndim, rev_bytes_per_launch(w))
                             if w.ndim == 3 or tuple(w.padded) == (871, 2421) else None),
-                "traffic_source": ("ncu dram bytes of k_rev2d on this grid, warm L2" if w.ndim == 2 else
+                "traffic_source": ("ncu dram bytes of k_rev2d_tile on this grid, warm L2" if w.ndim == 2 else
                                    "ncu dram bytes of k_rev3d_tma on 380x380x280, scaled by the algorithmic bytes"),
                 "bytes_per_launch": rev_bytes_per_launch(w), "launch_us": rev_launch_s * 1e6,
                 "forward_kernel": {"kernel": "k_fwd2d" if w.ndim == 2 else "k_fwd3d_tma",

@@ -12,10 +12,10 @@
 // [tap][out][in] (tap = 3 * dy + dx, dy, dx in 0..2 for offsets -1..1).
 // The 32 -> 32 convolutions (three hidden layers, and their backward-data
 // passes: the same kernel with the taps mirrored and the channel roles
-// swapped, its epilogue applying the ReLU mask of the layer below) run as
-// implicit GEMMs on the 5th-generation tensor cores (tcgen05.mma, operands
-// in shared memory, fp32 accumulators in tensor memory).  The one-channel
-// first and last layers run on the CUDA cores.  Weight gradients are per-tap
+// swapped, its epilogue applying the ReLU mask of the layer below) and the
+// 32 -> 1 last layer run as implicit GEMMs on the 5th-generation tensor cores
+// (tcgen05.mma, operands in shared memory, fp32 accumulators in tensor
+// memory).  The one-channel first layer runs on the CUDA cores.  Weight gradients are per-tap
 // GEMMs over the pixels on the warp-level tensor cores (mma.sync m16n8k16),
 // reduced by persistent blocks and added to the fp32 gradient once per block.
 #include <cuda.h>
@@ -50,113 +50,94 @@ __device__ __forceinline__ void mma16816(float *c, const uint32_t *a, const uint
 
 enum { kHidden = 0, kLast = 1, kBackData = 2 };
 
-// The one-channel ends of the network carry 32x fewer flops than the hidden
-// layers and are bound by their 64-byte-per-pixel activations, so they run on
-// the CUDA cores: one thread per pixel of an 8 x 32 tile, the halo and the
-// fp32 weights in shared memory.
+// The first layer (and the last layer's backward-data pass) has one input
+// channel, below the K = 16 of a tensor-core MMA, and is bound by its
+// 64-byte-per-pixel output, so it runs on the CUDA cores: a block of 256
+// threads covers 16 x 32 pixels, two pixels per thread (rows ty and ty + 8),
+// the halo and the fp32 weights in shared memory; each weight float4 is read
+// once for both pixels and applied with packed fp32x2 FMAs (each lane
+// correctly rounded, the same sequence per channel as scalar FMAs).
 // 1 -> 32 channels (first layer forward; last layer's backward-data pass):
 //   wt [tap][32] (bf16);  MODE kHidden: relu(conv + bias);  kBackData: conv * (mask > 0)
+constexpr int TH1 = 16;  // rows per block of the one-channel kernel
 template <int MODE>
 __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
                                                     __nv_bfloat16 *__restrict__ out, int H, int W) {
-  __shared__ float s_w[9 * 32];
-  __shared__ float s_b[32];
-  __shared__ float s_in[(TH + 2) * (TW + 2)];
+  __shared__ __align__(16) float s_w[9 * 32];
+  __shared__ __align__(16) float s_b[32];
+  __shared__ float s_in[(TH1 + 2) * (TW + 2)];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int img = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
+  const int img = blockIdx.z, y0 = blockIdx.y * TH1, x0 = blockIdx.x * TW;
   const long long ibase = (long long)img * H * W;
   for (int i = tid; i < 9 * 32; i += 256) s_w[i] = __bfloat162float(wt[i]);
   if (MODE == kHidden && tid < 32) s_b[tid] = bias[tid];
-  for (int i = tid; i < (TH + 2) * (TW + 2); i += 256) {
+  for (int i = tid; i < (TH1 + 2) * (TW + 2); i += 256) {
     const int yy = y0 + i / (TW + 2) - 1, xx = x0 + i % (TW + 2) - 1;
     s_in[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __bfloat162float(in[ibase + (long long)yy * W + xx]) : 0.f;
   }
   __syncthreads();
-  const int yy = y0 + ty, xx = x0 + tx;
-  if (yy >= H || xx >= W) return;
-  float acc[32];
+  const int xx = x0 + tx;
+  float2 acc[2][16];  // [pixel][channel pair]
 #pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+  for (int p = 0; p < 2; ++p)
 #pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    const float v = s_in[(ty + t / 3) * (TW + 2) + tx + t % 3];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = fmaf(v, s_w[t * 32 + c], acc[c]);
-  }
-  const long long HWp = (long long)H * W, pix = (long long)yy * W + xx;
-  if (MODE == kHidden) {
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = fmaxf(acc[c] + s_b[c], 0.f);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 m4 = reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp + pix];
-      const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 mf = __bfloat1622float2(m2[e]);
-        if (!(mf.x > 0.f)) acc[q * 8 + 2 * e] = 0.f;
-        if (!(mf.y > 0.f)) acc[q * 8 + 2 * e + 1] = 0.f;
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint4 pk;
-    __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(acc[q * 8 + 2 * e], acc[q * 8 + 2 * e + 1]);
-    reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
-  }
-}
-
-// 32 -> 1 channel, the last layer: y = x + conv(in) + bias (fp32 out).
-//   wt [tap][32] (bf16, the single output channel's weights)
-__global__ void __launch_bounds__(256) k_conv_32to1(const __nv_bfloat16 *__restrict__ in,
-                                                    const __nv_bfloat16 *__restrict__ wt,
-                                                    const float *__restrict__ bias,
-                                                    const float *__restrict__ resid, float *__restrict__ out,
-                                                    int H, int W) {
-  __shared__ float s_w[9 * 32];
-  __shared__ __align__(16) __nv_bfloat16 s_h[(TH + 2) * (TW + 2) * 32];
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int img = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
-  const long long ibase = (long long)img * H * W, HWp = (long long)H * W;
-  for (int i = tid; i < 9 * 32; i += 256) s_w[i] = __bfloat162float(wt[i]);
-  // halo as four channel-group planes [group][pixel] of 16-byte chunks
-  constexpr int HP = (TH + 2) * (TW + 2);
-  for (int i = tid; i < HP * 4; i += 256) {
-    const int q = i / HP, hp = i % HP;
-    const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-      v = reinterpret_cast<const uint4 *>(in)[((long long)img * 4 + q) * HWp + (long long)yy * W + xx];
-    reinterpret_cast<uint4 *>(s_h)[i] = v;
-  }
-  __syncthreads();
-  const int yy = y0 + ty, xx = x0 + tx;
-  if (yy >= H || xx >= W) return;
-  float acc = 0.f;
+    for (int c = 0; c < 16; ++c) acc[p][c] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
-    const int hp = (ty + t / 3) * (TW + 2) + tx + t % 3;
+    const float v0 = s_in[(ty + t / 3) * (TW + 2) + tx + t % 3];
+    const float v1 = s_in[(ty + 8 + t / 3) * (TW + 2) + tx + t % 3];
+    const float2 a0 = make_float2(v0, v0), a1 = make_float2(v1, v1);
+    const float4 *w4 = reinterpret_cast<const float4 *>(s_w + t * 32);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 v4 = reinterpret_cast<const uint4 *>(s_h)[q * HP + hp];
-      const __nv_bfloat162 *v2 = reinterpret_cast<const __nv_bfloat162 *>(&v4);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(v2[e]);
-        acc = fmaf(f.x, s_w[t * 32 + q * 8 + 2 * e], acc);
-        acc = fmaf(f.y, s_w[t * 32 + q * 8 + 2 * e + 1], acc);
-      }
+    for (int c4 = 0; c4 < 8; ++c4) {
+      const float4 w = w4[c4];
+      const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
+      acc[0][2 * c4] = __ffma2_rn(a0, wl, acc[0][2 * c4]);
+      acc[0][2 * c4 + 1] = __ffma2_rn(a0, wh, acc[0][2 * c4 + 1]);
+      acc[1][2 * c4] = __ffma2_rn(a1, wl, acc[1][2 * c4]);
+      acc[1][2 * c4 + 1] = __ffma2_rn(a1, wh, acc[1][2 * c4 + 1]);
     }
   }
-  const long long p = ibase + (long long)yy * W + xx;
-  out[p] = resid[p] + acc + bias[0];
+  const long long HWp = (long long)H * W;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int yy = y0 + ty + 8 * p;
+    if (yy >= H || xx >= W) continue;
+    const long long pix = (long long)yy * W + xx;
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      v[2 * c] = acc[p][c].x;
+      v[2 * c + 1] = acc[p][c].y;
+    }
+    if (MODE == kHidden) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + s_b[c], 0.f);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 m4 = reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp + pix];
+        const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 mf = __bfloat1622float2(m2[e]);
+          if (!(mf.x > 0.f)) v[q * 8 + 2 * e] = 0.f;
+          if (!(mf.y > 0.f)) v[q * 8 + 2 * e + 1] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 pk;
+      __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
+      reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -208,11 +189,7 @@ constexpr int kTcPlane = (kTcRows + 2) * kTcHW * 16;         // 12480 B per chan
 constexpr int kTcStage = 4 * kTcPlane;                       // halo stage (one TMA box)
 constexpr int kTcStages = 4;                                 // halo ring depth
 constexpr int kTcWBytes = 9 * 4 * 32 * 16;                   // weights, 18432 B
-constexpr int kTcWdx = 3 * 4 * 32 * 16;                      // weight bytes per dx: 6144
-constexpr int kTcWcg = 3 * 32 * 16;                          // per (dx, channel group): 1536
-constexpr int kTcBuf = kTcRows * 32;                         // accumulator columns per tile buffer
-constexpr int kTcTmemCols = 2 * kTcBuf <= 256 ? 256 : 512;   // two buffers (a power of two >= 32)
-static_assert(2 * kTcBuf <= 512, "two accumulator buffers must fit in tensor memory");
+static_assert(2 * kTcRows * 32 <= 512, "two accumulator buffers must fit in tensor memory");
 constexpr long long kTcWaitCycles = 4000000000LL;            // about two seconds
 constexpr int kTcSmem = kTcWBytes + kTcStages * kTcStage + 256;
 
@@ -292,14 +269,38 @@ __device__ __forceinline__ void tc_tma5(uint32_t dst, const CUtensorMap *tm, int
       : "memory");
 }
 
-//   MODE kHidden:   out = relu(conv(in) + bias)
+// Tensor-memory columns to allocate for c columns (a power of two >= 32).
+constexpr int tmem_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
+
+__device__ __forceinline__ float tmem_ld1(uint32_t ta) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void tmem_zero1(uint32_t ta) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(ta), "r"(0u) : "memory");
+}
+
+//   MODE kHidden:   out = relu(conv(in) + bias)                        (32 -> 32)
 //   MODE kBackData: out = conv(in) * (mask > 0)   (weights mirrored and transposed)
+//   MODE kLast:     out_f = resid + conv(in) + bias                    (32 -> 1)
+// The last layer's single output channel is padded to N = 16 per output row
+// (the smallest N of an M = 128 MMA); the 15 padding channels have zero
+// weights, so their accumulators stay zero and only channel 0 is read out.
 template <int MODE>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
-                                                    __nv_bfloat16 *__restrict__ out, int nimg, int H, int W, int *err) {
+                                                    __nv_bfloat16 *__restrict__ out, float *__restrict__ out_f,
+                                                    const float *__restrict__ resid, int nimg, int H, int W,
+                                                    int *err) {
+  constexpr int NCO = MODE == kLast ? 16 : 32;  // output channels per row accumulator
+  constexpr int WCG = 3 * NCO * 16;              // weight bytes per (dx, channel group)
+  constexpr int WDX = 4 * WCG;                   // weight bytes per dx
+  constexpr int BUF = kTcRows * NCO;             // accumulator columns per tile buffer
+  constexpr int TCOLS = tmem_cols(2 * BUF);
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t s_w = (uint32_t)__cvta_generic_to_shared(smem);
@@ -316,11 +317,24 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   auto tfull = [&](int i) { return b0 + 8u * (2 * kTcStages + i); };
   auto tempty = [&](int i) { return b0 + 8u * (2 * kTcStages + 2 + i); };
   // weights [tap][co][ci] (tap = 3 dy + dx) -> [dx][ci / 8][dy][co][8]
-  for (int i = tid; i < 9 * 32 * 4; i += blockDim.x) {
-    const int j = i & 3, co = (i >> 2) & 31, t = i >> 7, dy = t / 3, dx = t % 3;
-    cp_async16(s_w + dx * kTcWdx + j * kTcWcg + dy * 512 + co * 16, wt + (t * 32 + co) * 32 + j * 8, true);
+  if (MODE == kLast) {
+    for (int i = tid; i < 9 * 4 * (NCO - 1); i += blockDim.x) {  // padding channels 1..15: zero
+      const int co = 1 + i % (NCO - 1), r = i / (NCO - 1), j = r & 3, t = r >> 2;
+      *reinterpret_cast<uint4 *>(smem + (t % 3) * WDX + j * WCG + (t / 3) * NCO * 16 + co * 16) =
+          make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int i = tid; i < 9 * 4; i += blockDim.x) {
+      const int j = i & 3, t = i >> 2;
+      cp_async16(s_w + (t % 3) * WDX + j * WCG + (t / 3) * NCO * 16, wt + t * 32 + j * 8, true);
+    }
+  } else {
+    for (int i = tid; i < 9 * 32 * 4; i += blockDim.x) {
+      const int j = i & 3, co = (i >> 2) & 31, t = i >> 7, dy = t / 3, dx = t % 3;
+      cp_async16(s_w + dx * WDX + j * WCG + dy * NCO * 16 + co * 16, wt + (t * 32 + co) * 32 + j * 8, true);
+    }
   }
   if (MODE == kHidden && tid < 32) s_bias[tid] = bias[tid];
+  if (MODE == kLast && tid == 0) s_bias[0] = bias[0];
   if (tid == 0) {
     *abort_blk = 0;
     for (int i = 0; i < kTcStages; ++i) {
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   }
   if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-        (uint32_t)__cvta_generic_to_shared(tslot)), "r"(kTcTmemCols));
+        (uint32_t)__cvta_generic_to_shared(tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
@@ -346,7 +360,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   const uint32_t tmem = *tslot;
   if (warp < 4) {  // every MMA accumulates: both accumulator buffers start at zero
 #pragma unroll 1
-    for (int c = 0; c < 2 * kTcBuf; c += 32) tmem_zero32(tmem + ((uint32_t)(warp * 32) << 16) + c);
+    for (int c = 0; c < 2 * BUF; c += 32) tmem_zero32(tmem + ((uint32_t)(warp * 32) << 16) + c);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -392,20 +406,20 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         // descriptors differ only in their start-address field: one add per MMA
         // (fully unrolled, the offsets are constants; a single thread issues
         // all of them, so per-MMA arithmetic would bound the tile)
-        const uint64_t a0 = umma_desc(s_h + s * kTcStage, kTcPlane, 128), b0d = umma_desc(s_w, kTcWcg, 128);
-        const uint32_t d0 = tmem + b * kTcBuf;
+        const uint64_t a0 = umma_desc(s_h + s * kTcStage, kTcPlane, 128), b0d = umma_desc(s_w, WCG, 128);
+        const uint32_t d0 = tmem + b * BUF;
 #pragma unroll
         for (int h = 0; h < kTcRows + 2; ++h) {
           // output rows h - j for j in [j0, j1] (those inside the tile)
           const int j0 = h > kTcRows - 1 ? h - (kTcRows - 1) : 0, j1 = h < 2 ? h : 2;
-          const uint32_t idesc = tc_idesc(32 * (j1 - j0 + 1));
-          const uint32_t d = d0 + (uint32_t)((kTcRows - 1 - h + j0) * 32);
+          const uint32_t idesc = tc_idesc(NCO * (j1 - j0 + 1));
+          const uint32_t d = d0 + (uint32_t)((kTcRows - 1 - h + j0) * NCO);
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
               const uint64_t ad = a0 + (uint64_t)((2 * ks * kTcPlane + (h * kTcHW + dx) * 16) >> 4);
-              const uint64_t bd = b0d + (uint64_t)((dx * kTcWdx + 2 * ks * kTcWcg + j0 * 512) >> 4);
+              const uint64_t bd = b0d + (uint64_t)((dx * WDX + 2 * ks * WCG + j0 * NCO * 16) >> 4);
               asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d), "l"(ad),
                            "l"(bd), "r"(idesc), "r"(1u));
@@ -440,10 +454,27 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       const bool ok = tc_wait(tfull(b), ub & 1, abort_blk);
       if (__any_sync(0xffffffffu, !ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (MODE == kLast) {
+#pragma unroll
+        for (int rr = 0; rr < kTcRows; ++rr) {
+          const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + b * BUF + (kTcRows - 1 - rr) * NCO;
+          const float v0 = tmem_ld1(ta);
+          tmem_zero1(ta);  // channel 0 only: the padding channels never leave zero
+          const int yy = y0 + rr;
+          if (yy < H && xx < W) {
+            const long long p = (long long)img * HWp + (long long)yy * W + xx;
+            out_f[p] = resid[p] + v0 + s_bias[0];
+          }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        tc_arrive(tempty(b));
+        continue;
+      }
 #pragma unroll 1
       for (int rr = 0; rr < kTcRows; ++rr) {
         float v[32];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + b * kTcBuf + (kTcRows - 1 - rr) * 32;
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + b * BUF + (kTcRows - 1 - rr) * NCO;
         tmem_ld32(ta, v);
         tmem_zero32(ta);  // the next tile in this buffer accumulates from zero
         const int yy = y0 + rr;
@@ -483,7 +514,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   __syncthreads();
   if (tid == 0 && *abort_blk) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
+  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // Weight and bias gradients of a convolution layer:
@@ -709,6 +740,7 @@ void set_attrs() {
   if (done) return;
   cudaFuncSetAttribute(k_conv_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   cudaFuncSetAttribute(k_conv_tc<kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kLast>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -781,14 +813,15 @@ bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, i
 
 template <int MODE>
 bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, const __nv_bfloat16 *mask,
-                    __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s) {
+                    __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s, float *out_f = nullptr,
+                    const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcRows - 1) / kTcRows) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
   if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcRows + 2)) return false;
-  k_conv_tc<MODE><<<grid, 192, kTcSmem, s>>>(tin, wt, bias, mask, out, nimg, H, W, tc_err_dev);
+  k_conv_tc<MODE><<<grid, 192, kTcSmem, s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
   return true;
 }
 
@@ -811,13 +844,14 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
-  const dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, nimg);
+  const dim3 grid((W + TW - 1) / TW, (H + TH1 - 1) / TH1, nimg);
   k_conv_1to32<kHidden><<<grid, 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], H, W);
   bool ok_tc = true;
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
-  k_conv_32to1<<<grid, 256, 0, s>>>(w.act[3], w.wf + kW5, params_dev + kB5, x_dev, y_dev, H, W);
+  ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
+                                         y_dev, x_dev);
   if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: tensor map encoding failed");
   rbc::add_launches(7);
   cudaError_t e = cudaGetLastError();
@@ -834,7 +868,7 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   cudaStream_t s = (cudaStream_t)stream;
   const long long npx = (long long)nimg * H * W;
   Ws w = carve(ws_dev, npx);  // activations from the preceding rbc_cnn_forward
-  const dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, nimg);
+  const dim3 grid((W + TW - 1) / TW, (H + TH1 - 1) / TH1, nimg);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const int pg = 2 * sms;

@@ -276,30 +276,30 @@ __global__ void __launch_bounds__(32 * NW, MB) k_rev2d_tile(const RevArgs A) {
 // ------------------------------------------------------------ launchers ----
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
-// 2-D kernel shapes: 0 = register-queue kernels (k_fwd2d / k_rev2d); 1..5 =
-// shared-memory tiles (rows per warp x warps, resident blocks per SM asked
-// of the compiler): 1 = 2 x 4 (7), 2 = 2 x 8 (3), 3 = 4 x 4 (4), 4 = 1 x 8
-// (4), 5 = 2 x 4 (no register cap).  RBC_TILE2D="fwd,rev" overrides the
-// default (read once per process).
+// 2-D kernel shapes: 0 = register-queue kernels (k_fwd2d 4 warps x 2 rows,
+// k_rev2d 8 warps x 2 rows); 1 = shared-memory tiles of 4 warps x 2 rows,
+// 7 resident blocks per SM asked of the compiler (k_fwd2d_tile /
+// k_rev2d_tile).  Measured on the survey grid (2421 x 871, warm L2, per
+// launch): forward 5.78 us (shape 0) vs 6.32 us (1); reverse 15.25 us (0) vs
+// 13.54 us (1); other tile shapes (2 x 8, 4 x 4, 1 x 8, no register cap) lost
+// to both.  Default: forward 0, reverse 1; RBC_TILE2D="fwd,rev" overrides it
+// (read once per process).
 struct Shape2d { int fwd, rev; };
 static Shape2d shape2d() {
   static Shape2d sh = [] {
-    Shape2d v{1, 1};
+    Shape2d v{0, 1};
     const char *e = getenv("RBC_TILE2D");
     if (e) {
       int f = -1, r = -1;
-      if (sscanf(e, "%d,%d", &f, &r) == 2 && f >= 0 && f <= 5 && r >= 0 && r <= 5) v = Shape2d{f, r};
+      if (sscanf(e, "%d,%d", &f, &r) == 2 && f >= 0 && f <= 1 && r >= 0 && r <= 1) v = Shape2d{f, r};
     }
     return v;
   }();
   return sh;
 }
 static int tile_rows_2d(int k, bool fwd) {
-  switch (k) {
-  case 1: case 4: case 5: return 8;
-  case 2: case 3: return 16;
-  default: return fwd ? k2dWarpsF * k2dRowsF : k2dWarpsR * k2dRowsR;
-  }
+  if (k == 1) return 8;
+  return fwd ? k2dWarpsF * k2dRowsF : k2dWarpsR * k2dRowsR;
 }
 
 bool launch_fwd(const StepArgs &A, cudaStream_t s) {
@@ -307,14 +307,10 @@ bool launch_fwd(const StepArgs &A, cudaStream_t s) {
   if (L.ndim == 3) return launch_fwd3d(A, s);
   const int k = shape2d().fwd;
   dim3 grid(cdiv(L.NX, kTileX), cdiv(L.NZ, tile_rows_2d(k, true)));
-  switch (k) {
-  case 1: launch_pdl(k_fwd2d_tile<2, 4, 7>, grid, dim3(32, 4), 0, s, A); break;
-  case 2: launch_pdl(k_fwd2d_tile<2, 8, 3>, grid, dim3(32, 8), 0, s, A); break;
-  case 3: launch_pdl(k_fwd2d_tile<4, 4, 4>, grid, dim3(32, 4), 0, s, A); break;
-  case 4: launch_pdl(k_fwd2d_tile<1, 8, 4>, grid, dim3(32, 8), 0, s, A); break;
-  case 5: launch_pdl(k_fwd2d_tile<2, 4, 1>, grid, dim3(32, 4), 0, s, A); break;
-  default: launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarpsF), 0, s, A); break;
-  }
+  if (k == 1)
+    launch_pdl(k_fwd2d_tile<2, 4, 7>, grid, dim3(32, 4), 0, s, A);
+  else
+    launch_pdl(k_fwd2d<k2dRowsF>, grid, dim3(32, k2dWarpsF), 0, s, A);
   return true;
 }
 
@@ -338,16 +334,10 @@ bool launch_rev(const RevArgs &A, cudaStream_t s) {
   rev_tiling(A.L, A.zc, &gx, &gy, &gz, &t);
   const dim3 grid(gx, gy);
   const bool g = A.mode == 1;
-  switch (shape2d().rev) {
-  case 1: launch_pdl(g ? k_rev2d_tile<2, 4, 7, true> : k_rev2d_tile<2, 4, 7, false>, grid, dim3(32, 4), 0, s, A); break;
-  case 2: launch_pdl(g ? k_rev2d_tile<2, 8, 3, true> : k_rev2d_tile<2, 8, 3, false>, grid, dim3(32, 8), 0, s, A); break;
-  case 3: launch_pdl(g ? k_rev2d_tile<4, 4, 4, true> : k_rev2d_tile<4, 4, 4, false>, grid, dim3(32, 4), 0, s, A); break;
-  case 4: launch_pdl(g ? k_rev2d_tile<1, 8, 4, true> : k_rev2d_tile<1, 8, 4, false>, grid, dim3(32, 8), 0, s, A); break;
-  case 5: launch_pdl(g ? k_rev2d_tile<2, 4, 1, true> : k_rev2d_tile<2, 4, 1, false>, grid, dim3(32, 4), 0, s, A); break;
-  default:
+  if (shape2d().rev == 1)
+    launch_pdl(g ? k_rev2d_tile<2, 4, 7, true> : k_rev2d_tile<2, 4, 7, false>, grid, dim3(32, 4), 0, s, A);
+  else
     launch_pdl(g ? k_rev2d<k2dRowsR, true> : k_rev2d<k2dRowsR, false>, grid, dim3(32, k2dWarpsR), 0, s, A);
-    break;
-  }
   return true;
 }
 
