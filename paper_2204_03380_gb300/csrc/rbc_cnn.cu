@@ -18,8 +18,6 @@
 // memory).  The one-channel first layer runs on the CUDA cores.  Weight gradients are per-tap
 // GEMMs over the pixels on the warp-level tensor cores (mma.sync m16n8k16),
 // reduced by persistent blocks and added to the fp32 gradient once per block.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -53,19 +51,23 @@ enum { kHidden = 0, kLast = 1, kBackData = 2 };
 // The first layer (and the last layer's backward-data pass) has one input
 // channel, below the K = 16 of a tensor-core MMA, and is bound by its
 // 64-byte-per-pixel output, so it runs on the CUDA cores: a block of 256
-// threads covers 16 x 32 pixels, two pixels per thread (rows ty and ty + 8),
-// the halo and the fp32 weights in shared memory; each weight float4 is read
-// once for both pixels and applied with packed fp32x2 FMAs (each lane
-// correctly rounded, the same sequence per channel as scalar FMAs).
+// threads covers (8 x PPT) x 32 pixels, PPT pixels per thread (rows ty,
+// ty + 8, ...), the halo and the fp32 weights in shared memory; each weight
+// float4 is read once for the thread's pixels and applied with packed fp32x2
+// FMAs (each lane correctly rounded, the same sequence per channel as scalar
+// FMAs).
 // 1 -> 32 channels (first layer forward; last layer's backward-data pass):
 //   wt [tap][32] (bf16);  MODE kHidden: relu(conv + bias);  kBackData: conv * (mask > 0)
-constexpr int TH1 = 16;  // rows per block of the one-channel kernel
+// PPT pixels per thread (rows ty, ty + 8, ...): 2 for the forward layer, 1
+// for the backward-data pass, whose mask loads want the occupancy.
+template <int MODE> constexpr int ppt_1to32() { return MODE == kHidden ? 2 : 1; }
 template <int MODE>
 __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
                                                     __nv_bfloat16 *__restrict__ out, int H, int W) {
+  constexpr int P = ppt_1to32<MODE>(), TH1 = 8 * P;
   __shared__ __align__(16) float s_w[9 * 32];
   __shared__ __align__(16) float s_b[32];
   __shared__ float s_in[(TH1 + 2) * (TW + 2)];
@@ -80,30 +82,34 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
   }
   __syncthreads();
   const int xx = x0 + tx;
-  float2 acc[2][16];  // [pixel][channel pair]
+  float2 acc[P][16];  // [pixel][channel pair]
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < P; ++p)
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[p][c] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
-    const float v0 = s_in[(ty + t / 3) * (TW + 2) + tx + t % 3];
-    const float v1 = s_in[(ty + 8 + t / 3) * (TW + 2) + tx + t % 3];
-    const float2 a0 = make_float2(v0, v0), a1 = make_float2(v1, v1);
+    float2 a[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float v = s_in[(ty + 8 * p + t / 3) * (TW + 2) + tx + t % 3];
+      a[p] = make_float2(v, v);
+    }
     const float4 *w4 = reinterpret_cast<const float4 *>(s_w + t * 32);
 #pragma unroll
     for (int c4 = 0; c4 < 8; ++c4) {
       const float4 w = w4[c4];
       const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
-      acc[0][2 * c4] = __ffma2_rn(a0, wl, acc[0][2 * c4]);
-      acc[0][2 * c4 + 1] = __ffma2_rn(a0, wh, acc[0][2 * c4 + 1]);
-      acc[1][2 * c4] = __ffma2_rn(a1, wl, acc[1][2 * c4]);
-      acc[1][2 * c4 + 1] = __ffma2_rn(a1, wh, acc[1][2 * c4 + 1]);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        acc[p][2 * c4] = __ffma2_rn(a[p], wl, acc[p][2 * c4]);
+        acc[p][2 * c4 + 1] = __ffma2_rn(a[p], wh, acc[p][2 * c4 + 1]);
+      }
     }
   }
   const long long HWp = (long long)H * W;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < P; ++p) {
     const int yy = y0 + ty + 8 * p;
     if (yy >= H || xx >= W) continue;
     const long long pix = (long long)yy * W + xx;
@@ -162,9 +168,10 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // Both operands sit in shared memory in the no-swizzle K-major layout: a
 // "core matrix" is 8 rows of 16 bytes (8 channels) stored contiguously.  The
 // activations are kept channel-group planar in memory ([image][group of 8
-// channels][row][column][8]), so one 5-D TMA copy lands a tile's halo as four
-// planes (one per channel group) of halo pixels in row-major order at 16
-// bytes each: 8 consecutive pixels of any halo row are one core matrix, and
+// channels][row][column][8]), so a tile's halo lands as four planes (one per
+// channel group) of halo pixels in row-major order at 16 bytes each, one
+// contiguous bulk copy per (group, row): 8 consecutive pixels of any halo row
+// are one core matrix, and
 // the operand of a shifted tap is the same planes with the start address
 // moved by (h * 130 + dx) * 16 bytes (stride between 8-pixel groups 128
 // bytes, between channel groups one plane).  Weights in shared memory:
@@ -172,9 +179,9 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // consecutive core matrices (stride 128 bytes) and the two channel groups of a
 // K = 16 slice are 1536 bytes apart.
 //
-// Per block (one per SM, persistent over tiles), three roles: warp 4 streams
-// each tile's halo (zero-filled outside the image) into a 4-stage shared-
-// memory ring; warp 5 issues the 72 MMAs of a tile into one of two
+// Per block (one per SM, persistent over a contiguous range of tiles), three
+// roles: warp 4 streams each tile's halo (zero-filled outside the image) into
+// a 4-stage shared-memory ring; warp 5 issues the 72 MMAs of a tile into one of two
 // tensor-memory accumulators and commits them to the ring's "empty" and the
 // accumulator's "full" barrier; warps 0-3 (tensor-memory lanes 0-127, one
 // pixel each) drain the other accumulator with tcgen05.ld, apply the epilogue
@@ -260,14 +267,6 @@ __device__ __forceinline__ bool tc_wait(uint32_t b, uint32_t parity, volatile in
   }
   return true;
 }
-__device__ __forceinline__ void tc_tma5(uint32_t dst, const CUtensorMap *tm, int c1, int c2, int c4, uint32_t bar) {
-  // coordinates (channel 0, x, y, group 0, image)
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-      "%6}], [%7];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(c1), "r"(c2), "r"(0), "r"(c4), "r"(bar)
-      : "memory");
-}
 
 // Tensor-memory columns to allocate for c columns (a power of two >= 32).
 constexpr int tmem_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
@@ -289,7 +288,7 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
 template <int MODE>
-__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
+__global__ void __launch_bounds__(192, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
@@ -368,29 +367,72 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int ntx = (W + kTcW - 1) / kTcW, nty = (H + kTcRows - 1) / kTcRows;
   const long long ntiles = (long long)ntx * nty * nimg;
+  // Each block takes a contiguous range of tiles, ordered down the image
+  // columns (y fastest): a tile's two halo rows are rows of the block's
+  // previous tile, fetched a moment earlier and still in L2, so DRAM reads
+  // each activation row about once instead of 1.5 times.
+  const long long t_beg = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
   auto tile_xy = [&](long long t, int &img, int &y0, int &x0) {
     img = (int)(t / ((long long)ntx * nty));
     const int rem = (int)(t % ((long long)ntx * nty));
-    y0 = (rem / ntx) * kTcRows;
-    x0 = (rem % ntx) * kTcW;
+    y0 = (rem % nty) * kTcRows;
+    x0 = (rem / nty) * kTcW;
   };
   if (warp == 4) {
-    // ---- producer: one TMA copy of the halo per tile ----
-    if (lane == 0) {
-      int issued = 0;
-      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
-        const int s = issued % kTcStages, u = issued / kTcStages;
-        if (u > 0 && !tc_wait(empty(s), (u - 1) & 1, abort_blk)) break;
-        int img, y0, x0;
-        tile_xy(t, img, y0, x0);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTcStage) : "memory");
-        tc_tma5(s_h + s * kTcStage, &tm_in, x0 - 1, y0 - 1, img, full(s));
+    // ---- producer: the tile's halo, one bulk copy per (channel group, row) ----
+    // A halo row of one channel group is 130 contiguous 16-byte pixels in
+    // global memory and in the stage; it is copied as one 2 KB bulk copy
+    // (cp.async.bulk) rather than as a tensor box whose innermost dimension
+    // (one pixel's 8 channels) is only 16 bytes.  Parts outside the image
+    // (rows above / below it, the pixel left of x = 0, columns at or beyond W)
+    // are written as zeros by the warp and fenced for the tensor cores.
+    const long long HWp = (long long)H * W;
+    const uint32_t zero_ok = 1;
+    int issued = 0;
+    for (long long t = t_beg; t < t_end; ++t, ++issued) {
+      const int s = issued % kTcStages, u = issued / kTcStages;
+      uint32_t ok = zero_ok;
+      if (u > 0 && lane == 0) ok = tc_wait(empty(s), (u - 1) & 1, abort_blk) ? 1u : 0u;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      int img, y0, x0;
+      tile_xy(t, img, y0, x0);
+      const int xa = x0 - 1 < 0 ? 0 : x0 - 1, xb = x0 + kTcW + 1 < W ? x0 + kTcW + 1 : W;
+      const int lead = xa - (x0 - 1), ncopy = xb - xa;  // zero pixels before, pixels copied
+      unsigned char *stage = smem + kTcWBytes + s * kTcStage;
+      for (int gr = 0; gr < 4 * (kTcRows + 2); ++gr) {
+        const int g = gr / (kTcRows + 2), r = gr % (kTcRows + 2), yy = y0 - 1 + r;
+        uint4 *row = reinterpret_cast<uint4 *>(stage + g * kTcPlane + r * kTcHW * 16);
+        if (yy < 0 || yy >= H) {
+          for (int px = lane; px < kTcHW; px += 32) row[px] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+          for (int px = lane; px < lead; px += 32) row[px] = make_uint4(0u, 0u, 0u, 0u);
+          for (int px = lead + ncopy + lane; px < kTcHW; px += 32) row[px] = make_uint4(0u, 0u, 0u, 0u);
+        }
       }
-      if (*abort_blk) {  // let the copies in flight land before the block exits
-        for (int k = (issued > kTcStages ? issued - kTcStages : 0); k < issued; ++k) {
-          const long long t0 = clock64();
-          while (!tc_try(full(k % kTcStages), (k / kTcStages) & 1) && clock64() - t0 < kTcWaitCycles) {
-          }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        int rows_in = 0;
+        for (int r = 0; r < kTcRows + 2; ++r) rows_in += (y0 - 1 + r >= 0 && y0 - 1 + r < H) ? 1 : 0;
+        const uint32_t bytes = (uint32_t)(4 * rows_in * ncopy * 16);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(bytes) : "memory");
+        const uint32_t sb = s_h + s * kTcStage;
+        for (int gr = 0; gr < 4 * (kTcRows + 2); ++gr) {
+          const int g = gr / (kTcRows + 2), r = gr % (kTcRows + 2), yy = y0 - 1 + r;
+          if (yy < 0 || yy >= H) continue;
+          const __nv_bfloat16 *src = in + (((long long)img * 4 + g) * HWp + (long long)yy * W + xa) * 8;
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           sb + g * kTcPlane + r * kTcHW * 16 + lead * 16),
+                       "l"(src), "r"((uint32_t)(ncopy * 16)), "r"(full(s))
+                       : "memory");
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0 && *abort_blk) {  // let the copies in flight land before the block exits
+      for (int k = (issued > kTcStages ? issued - kTcStages : 0); k < issued; ++k) {
+        const long long t0 = clock64();
+        while (!tc_try(full(k % kTcStages), (k / kTcStages) & 1) && clock64() - t0 < kTcWaitCycles) {
         }
       }
     }
@@ -398,7 +440,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     // ---- MMA issuer ----
     if (lane == 0) {
       int k = 0;
-      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      for (long long t = t_beg; t < t_end; ++t, ++k) {
         const int s = k % kTcStages, u = k / kTcStages, b = k & 1, ub = k >> 1;
         if (!tc_wait(full(s), u & 1, abort_blk)) break;
         if (ub > 0 && !tc_wait(tempty(b), (ub - 1) & 1, abort_blk)) break;
@@ -435,7 +477,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     // ---- epilogue: warps 0-3, one accumulator row (pixel) per thread ----
     const long long HWp = (long long)H * W;
     int k = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    for (long long t = t_beg; t < t_end; ++t, ++k) {
       const int b = k & 1, ub = k >> 1;
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
@@ -454,7 +496,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       const bool ok = tc_wait(tfull(b), ub & 1, abort_blk);
       if (__any_sync(0xffffffffu, !ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (MODE == kLast) {
+      if constexpr (MODE == kLast) {
 #pragma unroll
         for (int rr = 0; rr < kTcRows; ++rr) {
           const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + b * BUF + (kTcRows - 1 - rr) * NCO;
@@ -466,11 +508,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
             out_f[p] = resid[p] + v0 + s_bias[0];
           }
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        tc_arrive(tempty(b));
-        continue;
-      }
+      } else {
 #pragma unroll 1
       for (int rr = 0; rr < kTcRows; ++rr) {
         float v[32];
@@ -505,6 +543,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
             reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
           }
         }
+      }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -797,20 +836,6 @@ int tc_err() {
   return RBC_OK;
 }
 
-// 5-D tensor map over a channel-group planar bf16 activation buffer (32
-// channels): dims (channel in group, x, y, group, image); box (8, bx, by, 4, 1).
-bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, int bx, int by) {
-  auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(rbc::tmap_encode_fn());
-  if (!fn) return false;
-  cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)nimg};
-  cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)W * H * 64};
-  cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, 4, 1};
-  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(buf), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int MODE>
 bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, const __nv_bfloat16 *mask,
                     __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s, float *out_f = nullptr,
@@ -819,9 +844,7 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcRows - 1) / kTcRows) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
-  CUtensorMap tin;
-  if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcRows + 2)) return false;
-  k_conv_tc<MODE><<<grid, 192, kTcSmem, s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
+  k_conv_tc<MODE><<<grid, 192, kTcSmem, s>>>(in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
   return true;
 }
 
@@ -844,7 +867,8 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
-  const dim3 grid((W + TW - 1) / TW, (H + TH1 - 1) / TH1, nimg);
+  const int th1 = 8 * ppt_1to32<kHidden>();
+  const dim3 grid((W + TW - 1) / TW, (H + th1 - 1) / th1, nimg);
   k_conv_1to32<kHidden><<<grid, 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], H, W);
   bool ok_tc = true;
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
@@ -852,7 +876,7 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
                                          y_dev, x_dev);
-  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: tensor map encoding failed");
+  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: launch failed");
   rbc::add_launches(7);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
@@ -868,7 +892,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   cudaStream_t s = (cudaStream_t)stream;
   const long long npx = (long long)nimg * H * W;
   Ws w = carve(ws_dev, npx);  // activations from the preceding rbc_cnn_forward
-  const dim3 grid((W + TW - 1) / TW, (H + TH1 - 1) / TH1, nimg);
+  const int th1 = 8 * ppt_1to32<kBackData>();
+  const dim3 grid((W + TW - 1) / TW, (H + th1 - 1) / th1, nimg);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const int pg = 2 * sms;
@@ -892,7 +917,7 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   // layer 1
   k_expand_c0<__nv_bfloat16><<<grid_of(npx), 256, 0, s>>>(w.x0, w.dz[1 - cur], (long long)H * W, nimg);
   k_conv_wgrad32<1, C><<<pg, 288, kWgSmem, s>>>(w.dz[1 - cur], w.dz[cur], grad_dev + kW1, grad_dev + kB1, nimg, H, W);
-  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_backward: tensor map encoding failed");
+  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_backward: launch failed");
   rbc::add_launches(12);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
