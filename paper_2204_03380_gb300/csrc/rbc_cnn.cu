@@ -18,8 +18,11 @@
 // memory).  The one-channel first layer runs on the CUDA cores.  Weight gradients are per-tap
 // GEMMs over the pixels on the warp-level tensor cores (mma.sync m16n8k16),
 // reduced by persistent blocks and added to the fp32 gradient once per block.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <cstdlib>
 
 #include "../../include/rbc.h"
 #include "rbc_internal.cuh"
@@ -268,6 +271,15 @@ __device__ __forceinline__ bool tc_wait(uint32_t b, uint32_t parity, volatile in
   return true;
 }
 
+__device__ __forceinline__ void tc_tma5(uint32_t dst, const CUtensorMap *tm, int c1, int c2, int c4, uint32_t bar) {
+  // coordinates (channel 0, x, y, group 0, image)
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(c1), "r"(c2), "r"(0), "r"(c4), "r"(bar)
+      : "memory");
+}
+
 // Tensor-memory columns to allocate for c columns (a power of two >= 32).
 constexpr int tmem_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
 
@@ -287,8 +299,12 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // The last layer's single output channel is padded to N = 16 per output row
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
-template <int MODE>
-__global__ void __launch_bounds__(192, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
+// V (tuning sweep): bit 0 = tile order (0: strided over the blocks, 1:
+// contiguous y-fastest range per block); bit 1 = halo copy (0: one 5-D
+// tensor copy, 1: one bulk copy per channel group and row).
+template <int MODE, int V>
+__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
+                                                    const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
@@ -371,12 +387,20 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __nv_bfloat16 *__restr
   // columns (y fastest): a tile's two halo rows are rows of the block's
   // previous tile, fetched a moment earlier and still in L2, so DRAM reads
   // each activation row about once instead of 1.5 times.
-  const long long t_beg = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  constexpr bool kContig = (V & 1) != 0, kBulk = (V & 2) != 0;
+  const long long t_beg = kContig ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
+  const long long t_end = kContig ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
+  const long long t_step = kContig ? 1 : gridDim.x;
   auto tile_xy = [&](long long t, int &img, int &y0, int &x0) {
     img = (int)(t / ((long long)ntx * nty));
     const int rem = (int)(t % ((long long)ntx * nty));
-    y0 = (rem % nty) * kTcRows;
-    x0 = (rem / nty) * kTcW;
+    if (kContig) {
+      y0 = (rem % nty) * kTcRows;
+      x0 = (rem / nty) * kTcW;
+    } else {
+      y0 = (rem / ntx) * kTcRows;
+      x0 = (rem % ntx) * kTcW;
+    }
   };
   if (warp == 4) {
     // ---- producer: the tile's halo, one bulk copy per (channel group, row) ----
@@ -389,13 +413,22 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __nv_bfloat16 *__restr
     const long long HWp = (long long)H * W;
     const uint32_t zero_ok = 1;
     int issued = 0;
-    for (long long t = t_beg; t < t_end; ++t, ++issued) {
+    for (long long t = t_beg; t < t_end; t += t_step, ++issued) {
       const int s = issued % kTcStages, u = issued / kTcStages;
       uint32_t ok = zero_ok;
       if (u > 0 && lane == 0) ok = tc_wait(empty(s), (u - 1) & 1, abort_blk) ? 1u : 0u;
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
+      if (!kBulk) {
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTcStage)
+                       : "memory");
+          tc_tma5(s_h + s * kTcStage, &tm_in, x0 - 1, y0 - 1, img, full(s));
+        }
+        __syncwarp();
+        continue;
+      }
       const int xa = x0 - 1 < 0 ? 0 : x0 - 1, xb = x0 + kTcW + 1 < W ? x0 + kTcW + 1 : W;
       const int lead = xa - (x0 - 1), ncopy = xb - xa;  // zero pixels before, pixels copied
       unsigned char *stage = smem + kTcWBytes + s * kTcStage;
@@ -440,7 +473,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __nv_bfloat16 *__restr
     // ---- MMA issuer ----
     if (lane == 0) {
       int k = 0;
-      for (long long t = t_beg; t < t_end; ++t, ++k) {
+      for (long long t = t_beg; t < t_end; t += t_step, ++k) {
         const int s = k % kTcStages, u = k / kTcStages, b = k & 1, ub = k >> 1;
         if (!tc_wait(full(s), u & 1, abort_blk)) break;
         if (ub > 0 && !tc_wait(tempty(b), (ub - 1) & 1, abort_blk)) break;
@@ -477,7 +510,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __nv_bfloat16 *__restr
     // ---- epilogue: warps 0-3, one accumulator row (pixel) per thread ----
     const long long HWp = (long long)H * W;
     int k = 0;
-    for (long long t = t_beg; t < t_end; ++t, ++k) {
+    for (long long t = t_beg; t < t_end; t += t_step, ++k) {
       const int b = k & 1, ub = k >> 1;
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
@@ -777,9 +810,12 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 void set_attrs() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_conv_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kLast>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+#define RBC_TC_ATTR(V)                                                                          \
+  cudaFuncSetAttribute(k_conv_tc<kHidden, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);   \
+  cudaFuncSetAttribute(k_conv_tc<kBackData, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem); \
+  cudaFuncSetAttribute(k_conv_tc<kLast, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  RBC_TC_ATTR(0) RBC_TC_ATTR(1) RBC_TC_ATTR(2) RBC_TC_ATTR(3)
+#undef RBC_TC_ATTR
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -836,6 +872,20 @@ int tc_err() {
   return RBC_OK;
 }
 
+// 5-D tensor map over a channel-group planar bf16 activation buffer (32
+// channels): dims (channel in group, x, y, group, image); box (8, bx, by, 4, 1).
+bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, int bx, int by) {
+  auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(rbc::tmap_encode_fn());
+  if (!fn) return false;
+  cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)nimg};
+  cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)W * H * 64};
+  cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, 4, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(buf), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int MODE>
 bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, const __nv_bfloat16 *mask,
                     __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s, float *out_f = nullptr,
@@ -844,7 +894,19 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcRows - 1) / kTcRows) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
-  k_conv_tc<MODE><<<grid, 192, kTcSmem, s>>>(in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
+  CUtensorMap tin;
+  if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcRows + 2)) return false;
+  static int variant = [] {
+    const char *e = getenv("RBC_TC_VARIANT");
+    const int v = e ? atoi(e) : 0;
+    return v >= 0 && v <= 3 ? v : 0;
+  }();
+  switch (variant) {
+  case 1: k_conv_tc<MODE, 1><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
+  case 2: k_conv_tc<MODE, 2><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
+  case 3: k_conv_tc<MODE, 3><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
+  default: k_conv_tc<MODE, 0><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
+  }
   return true;
 }
 

@@ -202,10 +202,25 @@ __global__ void __launch_bounds__(32 * NW, MB) k_fwd2d_tile(const StepArgs A) {
   griddep_launch();
 }
 
+// The tile's own rows of one pitched buffer (T rows x 128 columns) into `s`
+// (rows beyond the zero halo below the grid are zero-filled).
+template <int T>
+__device__ __forceinline__ void stage_own(const Lay &L, const float *__restrict__ f, float *s, int X0, int Z0,
+                                          int tid, int nthr) {
+  constexpr int kCh = kTileX / 4;
+  for (int i = tid; i < T * kCh; i += nthr) {
+    const int r = i / kCh, c = i - r * kCh;
+    const int z = Z0 + r;
+    const bool ok = z < L.NZ + kHaloR;
+    cp_async16z(s + r * kTileX + 4 * c, f + (ok ? L.origin + z * L.pitch + X0 + 4 * c : 0), ok);
+  }
+}
+
 template <int RZ, int NW, int MB, bool kGrad>
 __global__ void __launch_bounds__(32 * NW, MB) k_rev2d_tile(const RevArgs A) {
   constexpr int T = NW * RZ;
   __shared__ __align__(16) float s_r[(T + 8) * kStRow], s_b[(T + 8) * kStRow];
+  __shared__ __align__(16) float s_num[T * kTileX], s_den[kGrad ? 4 : T * kTileX];
   const Lay &L = A.L;
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
   const int X0 = blockIdx.x * kTileX, Z0 = blockIdx.y * T;
@@ -214,6 +229,13 @@ __global__ void __launch_bounds__(32 * NW, MB) k_rev2d_tile(const RevArgs A) {
   griddep_wait();
   stage_rows<T>(L, A.rc, s_r, X0, Z0, tid, 32 * NW);
   stage_rows<T>(L, A.bc, s_b, X0, Z0, tid, 32 * NW);
+  // the imaging accumulators' rows: read-modify-written below, so their loads
+  // fly with the fields' instead of stalling the update loop
+  const bool img_tile = Z0 < A.iz1 && Z0 + T > A.iz0 && X0 < A.ix1 && X0 + kTileX > A.ix0;
+  if (img_tile) {
+    stage_own<T>(L, A.num, s_num, X0, Z0, tid, 32 * NW);
+    if (!kGrad) stage_own<T>(L, A.den, s_den, X0, Z0, tid, 32 * NW);
+  }
   asm volatile("cp.async.commit_group;" ::: "memory");
   float4 av[RZ], pr[RZ], pb[RZ];
 #pragma unroll
@@ -259,13 +281,14 @@ __global__ void __launch_bounds__(32 * NW, MB) k_rev2d_tile(const RevArgs A) {
       st4(A.bn + o, leap_staged(s_b, rr, lane, pb[j], av[j], &cb));
     }
     if (img && z >= A.iz0 && z < A.iz1) {
+      const int so = (w * RZ + j) * kTileX + 4 * lane;
       if (kGrad) {
         // FWI: num += mu^m (p^m - 2 p^{m-1} + p^{m-2}) on the interior
-        if (A.do_r) st4(A.num + o, add4(ld4(A.num + o), masked_prod(cb, inc, x0, A.ix0, A.ix1)));
+        if (A.do_r) st4(A.num + o, add4(ld4(s_num + so), masked_prod(cb, inc, x0, A.ix0, A.ix1)));
       } else {
         // Eq. 3: the two time integrals, interior only
-        st4(A.num + o, add4(ld4(A.num + o), masked_prod(cr, cb, x0, A.ix0, A.ix1)));
-        st4(A.den + o, add4(ld4(A.den + o), masked_prod(cr, cr, x0, A.ix0, A.ix1)));
+        st4(A.num + o, add4(ld4(s_num + so), masked_prod(cr, cb, x0, A.ix0, A.ix1)));
+        st4(A.den + o, add4(ld4(s_den + so), masked_prod(cr, cr, x0, A.ix0, A.ix1)));
       }
     }
   }
