@@ -171,10 +171,9 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // Both operands sit in shared memory in the no-swizzle K-major layout: a
 // "core matrix" is 8 rows of 16 bytes (8 channels) stored contiguously.  The
 // activations are kept channel-group planar in memory ([image][group of 8
-// channels][row][column][8]), so a tile's halo lands as four planes (one per
-// channel group) of halo pixels in row-major order at 16 bytes each, one
-// contiguous bulk copy per (group, row): 8 consecutive pixels of any halo row
-// are one core matrix, and
+// channels][row][column][8]), so one 5-D TMA copy lands a tile's halo as four
+// planes (one per channel group) of halo pixels in row-major order at 16
+// bytes each: 8 consecutive pixels of any halo row are one core matrix, and
 // the operand of a shifted tap is the same planes with the start address
 // moved by (h * 130 + dx) * 16 bytes (stride between 8-pixel groups 128
 // bytes, between channel groups one plane).  Weights in shared memory:
@@ -182,9 +181,9 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // consecutive core matrices (stride 128 bytes) and the two channel groups of a
 // K = 16 slice are 1536 bytes apart.
 //
-// Per block (one per SM, persistent over a contiguous range of tiles), three
-// roles: warp 4 streams each tile's halo (zero-filled outside the image) into
-// a 4-stage shared-memory ring; warp 5 issues the 72 MMAs of a tile into one of two
+// Per block (one per SM, persistent over tiles), three roles: warp 4 streams
+// each tile's halo (zero-filled outside the image) into a 4-stage shared-
+// memory ring; warp 5 issues the 72 MMAs of a tile into one of two
 // tensor-memory accumulators and commits them to the ring's "empty" and the
 // accumulator's "full" barrier; warps 0-3 (tensor-memory lanes 0-127, one
 // pixel each) drain the other accumulator with tcgen05.ld, apply the epilogue
@@ -299,12 +298,12 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // The last layer's single output channel is padded to N = 16 per output row
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
-// V (tuning sweep): bit 0 = tile order (0: strided over the blocks, 1:
-// contiguous y-fastest range per block); bit 1 = halo copy (0: one 5-D
-// tensor copy, 1: one bulk copy per channel group and row).
-template <int MODE, int V>
-__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
-                                                    const __nv_bfloat16 *__restrict__ in,
+// E epilogue warps (4 or 8): warp e drains TMEM lane quarter e % 4 (pixels
+// 32 (e % 4) .. +31) for the output rows of its share (kTcRows * 4 / E rows,
+// starting at row (e / 4) * kTcRows * 4 / E); warp E is the producer, warp
+// E + 1 the MMA issuer.
+template <int MODE, int E>
+__global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
@@ -358,11 +357,11 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     }
     for (int i = 0; i < 2; ++i) {
       tc_mbar_init(tfull(i), 1);
-      tc_mbar_init(tempty(i), 128);
+      tc_mbar_init(tempty(i), 32 * E);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == E + 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
         (uint32_t)__cvta_generic_to_shared(tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -387,93 +386,41 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   // columns (y fastest): a tile's two halo rows are rows of the block's
   // previous tile, fetched a moment earlier and still in L2, so DRAM reads
   // each activation row about once instead of 1.5 times.
-  constexpr bool kContig = (V & 1) != 0, kBulk = (V & 2) != 0;
-  const long long t_beg = kContig ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
-  const long long t_end = kContig ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
-  const long long t_step = kContig ? 1 : gridDim.x;
+  // persistent blocks over the tiles, x fastest (measured against a
+  // contiguous y-fastest range per block, which lost: 1.36 vs 1.27 ms per
+  // 32 x 512^2 inference)
   auto tile_xy = [&](long long t, int &img, int &y0, int &x0) {
     img = (int)(t / ((long long)ntx * nty));
     const int rem = (int)(t % ((long long)ntx * nty));
-    if (kContig) {
-      y0 = (rem % nty) * kTcRows;
-      x0 = (rem / nty) * kTcW;
-    } else {
-      y0 = (rem / ntx) * kTcRows;
-      x0 = (rem % ntx) * kTcW;
-    }
+    y0 = (rem / ntx) * kTcRows;
+    x0 = (rem % ntx) * kTcW;
   };
-  if (warp == 4) {
-    // ---- producer: the tile's halo, one bulk copy per (channel group, row) ----
-    // A halo row of one channel group is 130 contiguous 16-byte pixels in
-    // global memory and in the stage; it is copied as one 2 KB bulk copy
-    // (cp.async.bulk) rather than as a tensor box whose innermost dimension
-    // (one pixel's 8 channels) is only 16 bytes.  Parts outside the image
-    // (rows above / below it, the pixel left of x = 0, columns at or beyond W)
-    // are written as zeros by the warp and fenced for the tensor cores.
-    const long long HWp = (long long)H * W;
-    const uint32_t zero_ok = 1;
-    int issued = 0;
-    for (long long t = t_beg; t < t_end; t += t_step, ++issued) {
-      const int s = issued % kTcStages, u = issued / kTcStages;
-      uint32_t ok = zero_ok;
-      if (u > 0 && lane == 0) ok = tc_wait(empty(s), (u - 1) & 1, abort_blk) ? 1u : 0u;
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      int img, y0, x0;
-      tile_xy(t, img, y0, x0);
-      if (!kBulk) {
-        if (lane == 0) {
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTcStage)
-                       : "memory");
-          tc_tma5(s_h + s * kTcStage, &tm_in, x0 - 1, y0 - 1, img, full(s));
-        }
-        __syncwarp();
-        continue;
+  if (warp == E) {
+    // ---- producer: one TMA copy of the halo per tile ----
+    // (one bulk copy per channel group and halo row instead lost by 2.1x)
+    if (lane == 0) {
+      int issued = 0;
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
+        const int s = issued % kTcStages, u = issued / kTcStages;
+        if (u > 0 && !tc_wait(empty(s), (u - 1) & 1, abort_blk)) break;
+        int img, y0, x0;
+        tile_xy(t, img, y0, x0);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTcStage) : "memory");
+        tc_tma5(s_h + s * kTcStage, &tm_in, x0 - 1, y0 - 1, img, full(s));
       }
-      const int xa = x0 - 1 < 0 ? 0 : x0 - 1, xb = x0 + kTcW + 1 < W ? x0 + kTcW + 1 : W;
-      const int lead = xa - (x0 - 1), ncopy = xb - xa;  // zero pixels before, pixels copied
-      unsigned char *stage = smem + kTcWBytes + s * kTcStage;
-      for (int gr = 0; gr < 4 * (kTcRows + 2); ++gr) {
-        const int g = gr / (kTcRows + 2), r = gr % (kTcRows + 2), yy = y0 - 1 + r;
-        uint4 *row = reinterpret_cast<uint4 *>(stage + g * kTcPlane + r * kTcHW * 16);
-        if (yy < 0 || yy >= H) {
-          for (int px = lane; px < kTcHW; px += 32) row[px] = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-          for (int px = lane; px < lead; px += 32) row[px] = make_uint4(0u, 0u, 0u, 0u);
-          for (int px = lead + ncopy + lane; px < kTcHW; px += 32) row[px] = make_uint4(0u, 0u, 0u, 0u);
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        int rows_in = 0;
-        for (int r = 0; r < kTcRows + 2; ++r) rows_in += (y0 - 1 + r >= 0 && y0 - 1 + r < H) ? 1 : 0;
-        const uint32_t bytes = (uint32_t)(4 * rows_in * ncopy * 16);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(bytes) : "memory");
-        const uint32_t sb = s_h + s * kTcStage;
-        for (int gr = 0; gr < 4 * (kTcRows + 2); ++gr) {
-          const int g = gr / (kTcRows + 2), r = gr % (kTcRows + 2), yy = y0 - 1 + r;
-          if (yy < 0 || yy >= H) continue;
-          const __nv_bfloat16 *src = in + (((long long)img * 4 + g) * HWp + (long long)yy * W + xa) * 8;
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                           sb + g * kTcPlane + r * kTcHW * 16 + lead * 16),
-                       "l"(src), "r"((uint32_t)(ncopy * 16)), "r"(full(s))
-                       : "memory");
-        }
-      }
-      __syncwarp();
-    }
-    if (lane == 0 && *abort_blk) {  // let the copies in flight land before the block exits
-      for (int k = (issued > kTcStages ? issued - kTcStages : 0); k < issued; ++k) {
-        const long long t0 = clock64();
-        while (!tc_try(full(k % kTcStages), (k / kTcStages) & 1) && clock64() - t0 < kTcWaitCycles) {
+      if (*abort_blk) {  // let the copies in flight land before the block exits
+        for (int k = (issued > kTcStages ? issued - kTcStages : 0); k < issued; ++k) {
+          const long long t0 = clock64();
+          while (!tc_try(full(k % kTcStages), (k / kTcStages) & 1) && clock64() - t0 < kTcWaitCycles) {
+          }
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == E + 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
       int k = 0;
-      for (long long t = t_beg; t < t_end; t += t_step, ++k) {
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int s = k % kTcStages, u = k / kTcStages, b = k & 1, ub = k >> 1;
         if (!tc_wait(full(s), u & 1, abort_blk)) break;
         if (ub > 0 && !tc_wait(tempty(b), (ub - 1) & 1, abort_blk)) break;
@@ -507,32 +454,35 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       }
     }
   } else {
-    // ---- epilogue: warps 0-3, one accumulator row (pixel) per thread ----
+    // ---- epilogue: warps 0 .. E-1, one accumulator row (pixel) per thread ----
+    constexpr int RE = kTcRows * 4 / E;  // output rows per epilogue warp
+    const int lq = warp & 3, r0 = (warp >> 2) * RE;
+    const uint32_t lanes = (uint32_t)(lq * 32) << 16;
     const long long HWp = (long long)H * W;
     int k = 0;
-    for (long long t = t_beg; t < t_end; t += t_step, ++k) {
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int b = k & 1, ub = k >> 1;
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
-      const int px = warp * 32 + lane, xx = x0 + px;
-      uint4 mk[kTcRows][4];  // backward-data: this pixel's masks, loaded while the MMAs run
+      const int px = lq * 32 + lane, xx = x0 + px;
+      uint4 mk[RE][4];  // backward-data: this pixel's masks, loaded while the MMAs run
       if (MODE == kBackData) {
 #pragma unroll
-        for (int rr = 0; rr < kTcRows; ++rr)
+        for (int i = 0; i < RE; ++i)
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            mk[rr][q] = (y0 + rr < H && xx < W)
-                            ? reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp +
-                                                                   (long long)(y0 + rr) * W + xx]
-                            : make_uint4(0u, 0u, 0u, 0u);
+            mk[i][q] = (y0 + r0 + i < H && xx < W)
+                           ? reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp +
+                                                                  (long long)(y0 + r0 + i) * W + xx]
+                           : make_uint4(0u, 0u, 0u, 0u);
       }
       const bool ok = tc_wait(tfull(b), ub & 1, abort_blk);
       if (__any_sync(0xffffffffu, !ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if constexpr (MODE == kLast) {
 #pragma unroll
-        for (int rr = 0; rr < kTcRows; ++rr) {
-          const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + b * BUF + (kTcRows - 1 - rr) * NCO;
+        for (int rr = r0; rr < r0 + RE; ++rr) {
+          const uint32_t ta = tmem + lanes + b * BUF + (kTcRows - 1 - rr) * NCO;
           const float v0 = tmem_ld1(ta);
           tmem_zero1(ta);  // channel 0 only: the padding channels never leave zero
           const int yy = y0 + rr;
@@ -543,9 +493,9 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         }
       } else {
 #pragma unroll 1
-      for (int rr = 0; rr < kTcRows; ++rr) {
+      for (int rr = r0; rr < r0 + RE; ++rr) {
         float v[32];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + b * BUF + (kTcRows - 1 - rr) * NCO;
+        const uint32_t ta = tmem + lanes + b * BUF + (kTcRows - 1 - rr) * NCO;
         tmem_ld32(ta, v);
         tmem_zero32(ta);  // the next tile in this buffer accumulates from zero
         const int yy = y0 + rr;
@@ -557,7 +507,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
           } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const uint4 m4 = mk[rr][q];
+              const uint4 m4 = mk[rr - r0][q];
               const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
@@ -586,7 +536,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   __syncthreads();
   if (tid == 0 && *abort_blk) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  if (warp == E + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // Weight and bias gradients of a convolution layer:
@@ -810,12 +760,12 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 void set_attrs() {
   static bool done = false;
   if (done) return;
-#define RBC_TC_ATTR(V)                                                                          \
-  cudaFuncSetAttribute(k_conv_tc<kHidden, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);   \
-  cudaFuncSetAttribute(k_conv_tc<kBackData, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem); \
-  cudaFuncSetAttribute(k_conv_tc<kLast, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  RBC_TC_ATTR(0) RBC_TC_ATTR(1) RBC_TC_ATTR(2) RBC_TC_ATTR(3)
-#undef RBC_TC_ATTR
+  cudaFuncSetAttribute(k_conv_tc<kHidden, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kBackData, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kLast, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kHidden, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kBackData, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kLast, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -896,17 +846,14 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
   if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcRows + 2)) return false;
-  static int variant = [] {
-    const char *e = getenv("RBC_TC_VARIANT");
-    const int v = e ? atoi(e) : 0;
-    return v >= 0 && v <= 3 ? v : 0;
+  static const int epi = [] {
+    const char *e = getenv("RBC_TC_EPI");
+    return e && atoi(e) == 4 ? 4 : 8;
   }();
-  switch (variant) {
-  case 1: k_conv_tc<MODE, 1><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
-  case 2: k_conv_tc<MODE, 2><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
-  case 3: k_conv_tc<MODE, 3><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
-  default: k_conv_tc<MODE, 0><<<grid, 192, kTcSmem, s>>>(tin, in, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev); break;
-  }
+  if (epi == 4)
+    k_conv_tc<MODE, 4><<<grid, 32 * 6, kTcSmem, s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
+  else
+    k_conv_tc<MODE, 8><<<grid, 32 * 10, kTcSmem, s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
   return true;
 }
 
