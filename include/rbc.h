@@ -308,12 +308,14 @@ int rbc_batch_rtm(rbc_batch *b, const rbc_shot *shots, const float *wavelet_dev,
  * whole batch. */
 int rbc_batch_timing(rbc_batch *b, int enable, double *out);
 
-/* rbc_batch_info -- out[0..13]: forward and reverse rows per warp chosen by
- * the autotuner (0 = the streaming kernels), work items of both kernels,
- * their grids, then the measured per-launch time in microseconds of every
- * candidate on the first shot group: forward streaming / 1 / 2 / 4 rows,
- * reverse 1 / 2 rows / streaming (0 where a candidate was not timed), then
- * the number of shot groups.  Host only. */
+/* rbc_batch_info -- out[0..14]: forward and reverse kernels chosen by the
+ * autotuner (forward: rows per warp, 0 = the streaming kernel; reverse: 1 or
+ * 2 rows per warp, 0 = the streaming kernel, 3 = shared-memory tiles of
+ * 8 rows), work items of both kernels, their grids, then the measured
+ * per-launch time in microseconds of every candidate on the first shot
+ * group: forward streaming / 1 / 2 / 4 rows, reverse 1 / 2 rows / streaming /
+ * tiles (0 where a candidate was not timed), then the number of shot groups.
+ * Host only. */
 int rbc_batch_info(const rbc_batch *b, int *out);
 
 /* ------------------------------------------------------------------------

@@ -335,12 +335,13 @@ def rbc_batch_timing(batch, enable):
 
 
 def rbc_batch_info(batch):
-    out = (C.c_int * 14)()
+    out = (C.c_int * 15)()
     _check(_lib.rbc_batch_info(C.c_void_p(batch), out))
     return dict(rows_fwd=out[0], rows_rev=out[1], items_fwd=out[2], items_rev=out[3], grid_fwd=out[4],
                 grid_rev=out[5], tune_us={"fwd_stream": out[6], "fwd_1": out[7], "fwd_2": out[8], "fwd_4": out[9],
-                                          "rev_1": out[10], "rev_2": out[11], "rev_stream": out[12]},
-                groups=out[13])
+                                          "rev_1": out[10], "rev_2": out[11], "rev_stream": out[12],
+                                          "rev_tile": out[13]},
+                groups=out[14])
 
 
 def rbc_cnn_param_count() -> int:

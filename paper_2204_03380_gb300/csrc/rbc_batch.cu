@@ -137,6 +137,93 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
   griddep_launch();
 }
 
+// Tiled form of the fused reverse step: one block of 4 warps per work item of
+// 128 columns x 8 rows (2 per warp), non-persistent (a grid of the group's
+// items), with the current levels of both fields over the item and its halo
+// and the item's imaging accumulators staged in shared memory by cp.async
+// before a single barrier, as in the single-shot k_rev2d_tile.
+constexpr int kBTileW = 4, kBTileRZ = 2, kBTileT = kBTileW * kBTileRZ;
+__global__ void __launch_bounds__(32 * kBTileW, 7) k_rev2d_batch_tile(const BShot *__restrict__ shots,
+                                                                      const int *__restrict__ item_shot, int item0,
+                                                                      int n, int nt, const float *__restrict__ wav,
+                                                                      float src_scale, float rec_scale) {
+  constexpr int T = kBTileT, RZ = kBTileRZ;
+  __shared__ __align__(16) float s_r[(T + 8) * kStRow], s_b[(T + 8) * kStRow];
+  __shared__ __align__(16) float s_num[T * kTileX], s_den[T * kTileX];
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+  const bool do_r = n < nt && n > 0, do_b = n > 0;
+  const int t = item0 + blockIdx.x;
+  griddep_wait();
+  const BShot &S = shots[__ldg(item_shot + t)];
+  const Lay &L = S.L;
+  const int loc = t - S.tbase_r;
+  const int X0 = (loc % S.gx) * kTileX, Z0 = (loc / S.gx) * T;
+  const int x0 = X0 + lane * 4, zb = Z0 + w * RZ;
+  const bool xok = x0 < L.NX4;
+  // p^R_n in p[n & 1], pbar_n in q[n & 1]
+  const float *rc = (n & 1) ? S.p1 : S.p0;
+  float *rn = (n & 1) ? S.p0 : S.p1;
+  const float *bc = (n & 1) ? S.q1 : S.q0;
+  float *bn = (n & 1) ? S.q0 : S.q1;
+  stage_rows<T>(L, rc, s_r, X0, Z0, tid, 32 * kBTileW);
+  stage_rows<T>(L, bc, s_b, X0, Z0, tid, 32 * kBTileW);
+  const bool img_tile = Z0 < S.iz1 && Z0 + T > S.iz0 && X0 < S.ix1 && X0 + kTileX > S.ix0;
+  if (img_tile) {
+    stage_own<T>(L, S.num, s_num, X0, Z0, tid, 32 * kBTileW);
+    stage_own<T>(L, S.den, s_den, X0, Z0, tid, 32 * kBTileW);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  float4 av[RZ], pr[RZ], pb[RZ];
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int o = L.origin + x0 + (zb + j) * L.pitch;
+    const bool ok = xok && zb + j < L.NZ;
+    av[j] = ok ? ldg4(S.a + o) : zero4();
+    pr[j] = ok && do_r ? ld4(rn + o) : zero4();
+    pb[j] = ok && do_b ? ld4(bn + o) : zero4();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int src = S.src_off;
+  const float fsrc = do_r ? wav[n] * src_scale : 0.f;  // f[nt] does not exist
+  const bool img = xok && x0 + 3 >= S.ix0 && x0 < S.ix1;
+#pragma unroll
+  for (int j = 0; j < RZ; ++j) {
+    const int z = zb + j, rr = w * RZ + j + kHaloR;
+    if (!(xok && z < L.NZ)) continue;
+    const int o = L.origin + x0 + z * L.pitch;
+    float4 cr = staged_c(s_r, rr, lane), cb = staged_c(s_b, rr, lane);
+    if (do_r) {
+      // Eq. 6: reconstruction (exact inverse of the forward step)
+      float4 r = leap_staged(s_r, rr, lane, pr[j], av[j], &cr);
+      const int d = src - o;
+      if ((unsigned)d < 4u) point_sub(r, d, cmp(av[j], d) * fsrc);
+      st4(rn + o, r);
+    }
+    // Eq. 2: the record is added below, after the block's stores
+    if (do_b) st4(bn + o, leap_staged(s_b, rr, lane, pb[j], av[j], &cb));
+    if (img && z >= S.iz0 && z < S.iz1) {
+      const int so = (w * RZ + j) * kTileX + 4 * lane;
+      st4(S.num + o, add4(ld4(s_num + so), masked_prod(cr, cb, x0, S.ix0, S.ix1)));
+      st4(S.den + o, add4(ld4(s_den + so), masked_prod(cr, cr, x0, S.ix0, S.ix1)));
+    }
+  }
+  // Eq. 2 source term at this item's receivers, after the block's stores
+  if (do_b) {
+    const int beg = S.tile_ptr[loc], end = S.tile_ptr[loc + 1];
+    if (end > beg) {
+      __threadfence();
+      __syncthreads();
+      for (int k = beg + tid; k < end; k += 32 * kBTileW) {
+        const int r = S.tile_rec[k];
+        const int o = S.rec_off[r];
+        atomicAdd(bn + o, rec_scale * S.a[o] * S.seis_t[(long long)n * S.nrec + r]);
+      }
+    }
+  }
+  griddep_launch();
+}
+
 // Streaming form of the forward step for DRAM-bound batches: every warp owns
 // a 128-column strip of kSZ rows of one shot and keeps its own rings in
 // shared memory -- kSR rows of p^n (with the 4-column halo, 544 bytes each)
@@ -484,7 +571,7 @@ struct rbc_batch {
   int nitems_f = 0, nitems_r = 0;
   int rzf = 4, rzr = 2;  // rows per warp (rzf == 0: the streaming forward kernel)
   int *err_host = nullptr, *err_dev = nullptr;  // bounded waits that gave up (mapped)
-  float tune_ms[7] = {};  // per-launch ms of the candidates: forward 0/1/2/4 rows, reverse 1/2/0
+  float tune_ms[8] = {};  // per-launch ms of the candidates: forward 0/1/2/4 rows, reverse 1/2/0/3
   int grid_f = 0, grid_r = 0;
   int rec_cap = 0, tile_cap = 0;
   int *d_rec_off = nullptr, *d_tile_ptr = nullptr, *d_tile_rec = nullptr;
@@ -504,7 +591,7 @@ struct rbc_batch {
 namespace {
 
 // z rows of a reverse work item (rzr == 0: the streaming kernel's warp task)
-int rev_tile_rows(const rbc_batch *b) { return b->rzr ? k2dWarps * b->rzr : kSZ; }
+int rev_tile_rows(const rbc_batch *b) { return b->rzr == 3 ? kBTileT : b->rzr ? k2dWarps * b->rzr : kSZ; }
 
 int bfail(int code, const char *fmt, ...) {
   char buf[512];
@@ -611,6 +698,11 @@ bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s, int i0 = 0, int i1 = -1) 
     launch_pdl(k_rev2d_batch<1>, dim3(std::min(b->grid_r, items)), blk, 0, s, (const BShot *)b->ds,
                (const int *)b->d_item_r, i0, i1, n, nt, (const float *)b->d_wav, 1.f, 1.f);
     break;
+  case 3:
+    if (items > 0)
+      launch_pdl(k_rev2d_batch_tile, dim3(items), dim3(32, kBTileW), 0, s, (const BShot *)b->ds,
+                 (const int *)b->d_item_r, i0, n, nt, (const float *)b->d_wav, 1.f, 1.f);
+    break;
   default:
     launch_pdl(k_rev2d_batch<2>, dim3(std::min(b->grid_r, items)), blk, 0, s, (const BShot *)b->ds,
                (const int *)b->d_item_r, i0, i1, n, nt, (const float *)b->d_wav, 1.f, 1.f);
@@ -629,6 +721,7 @@ void set_grids(rbc_batch *b) {
   switch (b->rzr) {
   case 0: b->grid_r = resident_grid(k_rev2d_stream, cdiv(b->nitems_r, k2dWarps), kStreamSmemR); break;
   case 1: b->grid_r = resident_grid(k_rev2d_batch<1>, b->nitems_r); break;
+  case 3: b->grid_r = b->nitems_r; break;  // one block per item
   default: b->grid_r = resident_grid(k_rev2d_batch<2>, b->nitems_r); break;
   }
 }
@@ -665,7 +758,7 @@ int autotune(rbc_batch *b) {
   // RBC_BATCH_TILES="f,r" restricts the candidates (a tuning and test knob)
   int force_f = -1, force_r = -1;
   if (const char *env = getenv("RBC_BATCH_TILES")) sscanf(env, "%d,%d", &force_f, &force_r);
-  const int cf[4] = {0, 1, 2, 4}, cr[3] = {1, 2, 0};
+  const int cf[4] = {0, 1, 2, 4}, cr[4] = {1, 2, 0, 3};
   for (int i = 0; i < 4; ++i) {
     if (force_f >= 0 && cf[i] != force_f) continue;
     b->rzf = cf[i];
@@ -677,7 +770,7 @@ int autotune(rbc_batch *b) {
     if (t < tf) tf = t, best_f = cf[i];
   }
   b->rzf = best_f;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (force_r >= 0 && cr[i] != force_r) continue;
     b->rzr = cr[i];
     int rc = build_items(b);
@@ -1065,8 +1158,8 @@ int rbc_batch_info(const rbc_batch *b, int *out) {
   out[3] = b->nitems_r;
   out[4] = b->grid_f;
   out[5] = b->grid_r;
-  for (int i = 0; i < 7; ++i) out[6 + i] = (int)(b->tune_ms[i] * 1000.0f + 0.5f);  // microseconds
-  out[13] = (int)b->grp.size() - 1;
+  for (int i = 0; i < 8; ++i) out[6 + i] = (int)(b->tune_ms[i] * 1000.0f + 0.5f);  // microseconds
+  out[14] = (int)b->grp.size() - 1;
   return RBC_OK;
 }
 

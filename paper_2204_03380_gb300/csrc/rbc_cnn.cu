@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // ---------------------------------------------------------------------------
 // 32 -> 32 channel layers on the 5th-generation tensor cores (tcgen05).
 //
-// A tile is kTcRows output rows x 128 columns of one image.  The accumulator
+// A tile is R output rows x 128 columns of one image.  The accumulator
 // of output row rr is a 128 (pixels) x 32 (channels) fp32 matrix in tensor
 // memory:
 //   D_rr[px][co] = sum_(dy, dx) sum_ci halo[rr + dy][px + dx][ci] * w[dy][dx][co][ci].
@@ -162,11 +162,11 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // channels) with M = 128 pixels, K = 16 channels and N = 32 x (number of
 // output rows h reaches): B stacks the weights of those dy values, and the
 // output rows' accumulators sit in tensor memory in descending row order
-// (row rr at column (kTcRows - 1 - rr) * 32), so the N columns of one MMA are
+// (row rr at column (R - 1 - rr) * 32), so the N columns of one MMA are
 // exactly the accumulators it feeds.  Against one N = 32 MMA per (row, tap,
 // half) this reads each shifted halo operand once instead of up to three
-// times: 6 (kTcRows + 2) MMAs per tile instead of 18 kTcRows, and 40 % less
-// shared-memory operand traffic at kTcRows = 4.  Every MMA accumulates; the
+// times: 6 (R + 2) MMAs per tile instead of 18 R, and 40 % less
+// shared-memory operand traffic at R = 4.  Every MMA accumulates; the
 // epilogue clears each accumulator after reading it.
 // Both operands sit in shared memory in the no-swizzle K-major layout: a
 // "core matrix" is 8 rows of 16 bytes (8 channels) stored contiguously.  The
@@ -191,16 +191,18 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // before the accumulator wait) and store.  Copies of tiles k+1 .. k+3, MMAs
 // of tile k and the epilogue of tile k-1 overlap.  Every wait is bounded; a
 // block that gives up flags the error word and stops.
-constexpr int kTcRows = 4;                                   // output rows per tile
 constexpr int kTcW = 128;                                    // output columns per tile (M)
 constexpr int kTcHW = kTcW + 2;                              // halo row width (pixels)
-constexpr int kTcPlane = (kTcRows + 2) * kTcHW * 16;         // 12480 B per channel-group plane
-constexpr int kTcStage = 4 * kTcPlane;                       // halo stage (one TMA box)
-constexpr int kTcStages = 4;                                 // halo ring depth
 constexpr int kTcWBytes = 9 * 4 * 32 * 16;                   // weights, 18432 B
-static_assert(2 * kTcRows * 32 <= 512, "two accumulator buffers must fit in tensor memory");
 constexpr long long kTcWaitCycles = 4000000000LL;            // about two seconds
-constexpr int kTcSmem = kTcWBytes + kTcStages * kTcStage + 256;
+constexpr int kTcEpi = 8;                                    // epilogue warps (4 measured slower)
+// Tiles of R output rows: halo planes of R + 2 rows per channel group, a
+// ring of 4 stages for R = 4 and 3 for R = 6 (what fits in 227 KB).
+constexpr int tc_plane(int R) { return (R + 2) * kTcHW * 16; }
+constexpr int tc_stages(int R) { return R <= 4 ? 4 : 3; }
+constexpr int tc_smem(int R) { return kTcWBytes + tc_stages(R) * 4 * tc_plane(R) + 256; }
+static_assert(tc_smem(6) <= 227 * 1024, "the R = 6 ring must fit in shared memory");
+static_assert(2 * 6 * 32 <= 512, "two accumulator buffers must fit in tensor memory");
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   // no swizzle; start, leading (K) and stride (M/N) byte offsets in 16-byte
@@ -298,12 +300,12 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // The last layer's single output channel is padded to N = 16 per output row
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
-// E epilogue warps (4 or 8): warp e drains TMEM lane quarter e % 4 (pixels
-// 32 (e % 4) .. +31) for the output rows of its share (kTcRows * 4 / E rows,
-// starting at row (e / 4) * kTcRows * 4 / E); warp E is the producer, warp
-// E + 1 the MMA issuer.
-template <int MODE, int E>
-__global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
+// kTcEpi epilogue warps: warp e drains TMEM lane quarter e % 4 (pixels
+// 32 (e % 4) .. +31) for the output rows of its share (R * 4 / kTcEpi rows,
+// starting at row (e / 4) * R * 4 / kTcEpi); warp kTcEpi is the producer,
+// warp kTcEpi + 1 the MMA issuer.
+template <int MODE, int R>
+__global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
@@ -313,23 +315,24 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
   constexpr int NCO = MODE == kLast ? 16 : 32;  // output channels per row accumulator
   constexpr int WCG = 3 * NCO * 16;              // weight bytes per (dx, channel group)
   constexpr int WDX = 4 * WCG;                   // weight bytes per dx
-  constexpr int BUF = kTcRows * NCO;             // accumulator columns per tile buffer
+  constexpr int BUF = R * NCO;             // accumulator columns per tile buffer
   constexpr int TCOLS = tmem_cols(2 * BUF);
+  constexpr int PLANE = tc_plane(R), STAGES = tc_stages(R), STAGE = 4 * PLANE;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t s_w = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t s_h = s_w + kTcWBytes;  // halo ring
-  unsigned char *tail = smem + kTcWBytes + kTcStages * kTcStage;
+  unsigned char *tail = smem + kTcWBytes + STAGES * STAGE;
   float *s_bias = reinterpret_cast<float *>(tail);
-  // barriers: full[kTcStages], empty[kTcStages], tfull[2], tempty[2]
+  // barriers: full[STAGES], empty[STAGES], tfull[2], tempty[2]
   uint64_t *bars = reinterpret_cast<uint64_t *>(tail + 128);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kTcStages + 4);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
   volatile int *abort_blk = reinterpret_cast<volatile int *>(tslot + 1);
   const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(bars);
   auto full = [&](int i) { return b0 + 8u * i; };
-  auto empty = [&](int i) { return b0 + 8u * (kTcStages + i); };
-  auto tfull = [&](int i) { return b0 + 8u * (2 * kTcStages + i); };
-  auto tempty = [&](int i) { return b0 + 8u * (2 * kTcStages + 2 + i); };
+  auto empty = [&](int i) { return b0 + 8u * (STAGES + i); };
+  auto tfull = [&](int i) { return b0 + 8u * (2 * STAGES + i); };
+  auto tempty = [&](int i) { return b0 + 8u * (2 * STAGES + 2 + i); };
   // weights [tap][co][ci] (tap = 3 dy + dx) -> [dx][ci / 8][dy][co][8]
   if (MODE == kLast) {
     for (int i = tid; i < 9 * 4 * (NCO - 1); i += blockDim.x) {  // padding channels 1..15: zero
@@ -351,17 +354,17 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
   if (MODE == kLast && tid == 0) s_bias[0] = bias[0];
   if (tid == 0) {
     *abort_blk = 0;
-    for (int i = 0; i < kTcStages; ++i) {
+    for (int i = 0; i < STAGES; ++i) {
       tc_mbar_init(full(i), 1);
       tc_mbar_init(empty(i), 1);
     }
     for (int i = 0; i < 2; ++i) {
       tc_mbar_init(tfull(i), 1);
-      tc_mbar_init(tempty(i), 32 * E);
+      tc_mbar_init(tempty(i), 32 * kTcEpi);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == E + 1) {
+  if (warp == kTcEpi + 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
         (uint32_t)__cvta_generic_to_shared(tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int ntx = (W + kTcW - 1) / kTcW, nty = (H + kTcRows - 1) / kTcRows;
+  const int ntx = (W + kTcW - 1) / kTcW, nty = (H + R - 1) / R;
   const long long ntiles = (long long)ntx * nty * nimg;
   // Each block takes a contiguous range of tiles, ordered down the image
   // columns (y fastest): a tile's two halo rows are rows of the block's
@@ -392,55 +395,55 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
   auto tile_xy = [&](long long t, int &img, int &y0, int &x0) {
     img = (int)(t / ((long long)ntx * nty));
     const int rem = (int)(t % ((long long)ntx * nty));
-    y0 = (rem / ntx) * kTcRows;
+    y0 = (rem / ntx) * R;
     x0 = (rem % ntx) * kTcW;
   };
-  if (warp == E) {
+  if (warp == kTcEpi) {
     // ---- producer: one TMA copy of the halo per tile ----
     // (one bulk copy per channel group and halo row instead lost by 2.1x)
     if (lane == 0) {
       int issued = 0;
       for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
-        const int s = issued % kTcStages, u = issued / kTcStages;
+        const int s = issued % STAGES, u = issued / STAGES;
         if (u > 0 && !tc_wait(empty(s), (u - 1) & 1, abort_blk)) break;
         int img, y0, x0;
         tile_xy(t, img, y0, x0);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTcStage) : "memory");
-        tc_tma5(s_h + s * kTcStage, &tm_in, x0 - 1, y0 - 1, img, full(s));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(STAGE) : "memory");
+        tc_tma5(s_h + s * STAGE, &tm_in, x0 - 1, y0 - 1, img, full(s));
       }
       if (*abort_blk) {  // let the copies in flight land before the block exits
-        for (int k = (issued > kTcStages ? issued - kTcStages : 0); k < issued; ++k) {
+        for (int k = (issued > STAGES ? issued - STAGES : 0); k < issued; ++k) {
           const long long t0 = clock64();
-          while (!tc_try(full(k % kTcStages), (k / kTcStages) & 1) && clock64() - t0 < kTcWaitCycles) {
+          while (!tc_try(full(k % STAGES), (k / STAGES) & 1) && clock64() - t0 < kTcWaitCycles) {
           }
         }
       }
     }
-  } else if (warp == E + 1) {
+  } else if (warp == kTcEpi + 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
       int k = 0;
       for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-        const int s = k % kTcStages, u = k / kTcStages, b = k & 1, ub = k >> 1;
+        const int s = k % STAGES, u = k / STAGES, b = k & 1, ub = k >> 1;
         if (!tc_wait(full(s), u & 1, abort_blk)) break;
         if (ub > 0 && !tc_wait(tempty(b), (ub - 1) & 1, abort_blk)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // descriptors differ only in their start-address field: one add per MMA
         // (fully unrolled, the offsets are constants; a single thread issues
         // all of them, so per-MMA arithmetic would bound the tile)
-        const uint64_t a0 = umma_desc(s_h + s * kTcStage, kTcPlane, 128), b0d = umma_desc(s_w, WCG, 128);
+        const uint64_t a0 = umma_desc(s_h + s * STAGE, PLANE, 128), b0d = umma_desc(s_w, WCG, 128);
         const uint32_t d0 = tmem + b * BUF;
 #pragma unroll
-        for (int h = 0; h < kTcRows + 2; ++h) {
+        for (int h = 0; h < R + 2; ++h) {
           // output rows h - j for j in [j0, j1] (those inside the tile)
-          const int j0 = h > kTcRows - 1 ? h - (kTcRows - 1) : 0, j1 = h < 2 ? h : 2;
+          const int j0 = h > R - 1 ? h - (R - 1) : 0, j1 = h < 2 ? h : 2;
           const uint32_t idesc = tc_idesc(NCO * (j1 - j0 + 1));
-          const uint32_t d = d0 + (uint32_t)((kTcRows - 1 - h + j0) * NCO);
+          const uint32_t d = d0 + (uint32_t)((R - 1 - h + j0) * NCO);
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-              const uint64_t ad = a0 + (uint64_t)((2 * ks * kTcPlane + (h * kTcHW + dx) * 16) >> 4);
+              const uint64_t ad = a0 + (uint64_t)((2 * ks * PLANE + (h * kTcHW + dx) * 16) >> 4);
               const uint64_t bd = b0d + (uint64_t)((dx * WDX + 2 * ks * WCG + j0 * NCO * 16) >> 4);
               asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d), "l"(ad),
@@ -454,8 +457,8 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
       }
     }
   } else {
-    // ---- epilogue: warps 0 .. E-1, one accumulator row (pixel) per thread ----
-    constexpr int RE = kTcRows * 4 / E;  // output rows per epilogue warp
+    // ---- epilogue: warps 0 .. kTcEpi-1, one accumulator row (pixel) per thread ----
+    constexpr int RE = R * 4 / kTcEpi;  // output rows per epilogue warp
     const int lq = warp & 3, r0 = (warp >> 2) * RE;
     const uint32_t lanes = (uint32_t)(lq * 32) << 16;
     const long long HWp = (long long)H * W;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
       if constexpr (MODE == kLast) {
 #pragma unroll
         for (int rr = r0; rr < r0 + RE; ++rr) {
-          const uint32_t ta = tmem + lanes + b * BUF + (kTcRows - 1 - rr) * NCO;
+          const uint32_t ta = tmem + lanes + b * BUF + (R - 1 - rr) * NCO;
           const float v0 = tmem_ld1(ta);
           tmem_zero1(ta);  // channel 0 only: the padding channels never leave zero
           const int yy = y0 + rr;
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
 #pragma unroll 1
       for (int rr = r0; rr < r0 + RE; ++rr) {
         float v[32];
-        const uint32_t ta = tmem + lanes + b * BUF + (kTcRows - 1 - rr) * NCO;
+        const uint32_t ta = tmem + lanes + b * BUF + (R - 1 - rr) * NCO;
         tmem_ld32(ta, v);
         tmem_zero32(ta);  // the next tile in this buffer accumulates from zero
         const int yy = y0 + rr;
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(32 * (E + 2), 1) k_conv_tc(const __grid_consta
   __syncthreads();
   if (tid == 0 && *abort_blk) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == E + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  if (warp == kTcEpi + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // Weight and bias gradients of a convolution layer:
@@ -760,12 +763,12 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 void set_attrs() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_conv_tc<kHidden, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kBackData, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kLast, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kHidden, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kBackData, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(k_conv_tc<kLast, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(k_conv_tc<kHidden, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4));
+  cudaFuncSetAttribute(k_conv_tc<kBackData, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4));
+  cudaFuncSetAttribute(k_conv_tc<kLast, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4));
+  cudaFuncSetAttribute(k_conv_tc<kHidden, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6));
+  cudaFuncSetAttribute(k_conv_tc<kBackData, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6));
+  cudaFuncSetAttribute(k_conv_tc<kLast, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6));
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -842,18 +845,21 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
                     const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcRows - 1) / kTcRows) * nimg;
+  // rows per tile: RBC_TC_ROWS=4 or 6 (a tuning knob, read once)
+  static const int rows = [] {
+    const char *e = getenv("RBC_TC_ROWS");
+    return e && atoi(e) == 6 ? 6 : 4;
+  }();
+  const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + rows - 1) / rows) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
-  if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcRows + 2)) return false;
-  static const int epi = [] {
-    const char *e = getenv("RBC_TC_EPI");
-    return e && atoi(e) == 4 ? 4 : 8;
-  }();
-  if (epi == 4)
-    k_conv_tc<MODE, 4><<<grid, 32 * 6, kTcSmem, s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
+  if (!act_map(&tin, in, nimg, H, W, kTcHW, rows + 2)) return false;
+  if (rows == 6)
+    k_conv_tc<MODE, 6><<<grid, 32 * (kTcEpi + 2), tc_smem(6), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H,
+                                                                   W, tc_err_dev);
   else
-    k_conv_tc<MODE, 8><<<grid, 32 * 10, kTcSmem, s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
+    k_conv_tc<MODE, 4><<<grid, 32 * (kTcEpi + 2), tc_smem(4), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H,
+                                                                   W, tc_err_dev);
   return true;
 }
 

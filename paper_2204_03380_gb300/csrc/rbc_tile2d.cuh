@@ -150,4 +150,67 @@ __device__ __forceinline__ void rev_field2d(const Lay &L, const float *__restric
   }
 }
 
+// ---- shared-memory tiles (single-shot and batched reverse kernels) ----
+// A block of NW warps covers 128 columns x T = NW * RZ rows.  The current
+// level(s) over the tile and its 4-node halo (T + 8 rows x 136 columns) are
+// staged in shared memory by 16-byte cp.async copies of the whole block (each
+// row crosses L2 once per tile instead of (RZ + 8) / RZ times through a
+// per-warp register queue, and no register holds a copy in flight), while
+// every lane loads its own a and p^{n-1} float4s into registers; one barrier,
+// then each warp updates its RZ rows with x and z neighbours from shared
+// memory.  Rows beyond the zero halo below the grid are zero-filled.
+__device__ __forceinline__ void cp_async16z(float *dst, const float *src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+constexpr int kStRow = kTileX + 2 * kHaloR;  // staged floats per row: x0 - 4 .. x0 + 131
+
+// Stage rows Z0 - 4 .. Z0 + T + 3 of `f` (columns X0 - 4 .. X0 + 131) into `s`.
+template <int T>
+__device__ __forceinline__ void stage_rows(const Lay &L, const float *__restrict__ f, float *s, int X0, int Z0,
+                                           int tid, int nthr) {
+  constexpr int kCh = kStRow / 4;  // 16-byte chunks per row
+  for (int i = tid; i < (T + 8) * kCh; i += nthr) {
+    const int r = i / kCh, c = i - r * kCh;
+    const int z = Z0 - kHaloR + r;
+    const bool ok = z < L.NZ + kHaloR;  // rows -4 .. NZ + 3 exist (zero halo); z >= -4 always
+    const float *src = f + (ok ? L.origin + z * L.pitch + X0 - kHaloR + 4 * c : 0);
+    cp_async16z(s + r * kStRow + 4 * c, src, ok);
+  }
+}
+
+// The leapfrog of Eq. 1 for the float4 of lane `lane` in staged row rr
+// (rr = 4 + local row) of `s`.
+__device__ __forceinline__ float4 leap_staged(const float *s, int rr, int lane, const float4 po, const float4 av,
+                                              float4 *cen) {
+  const float *row = s + rr * kStRow + 4 * lane;
+  const float4 lf = *reinterpret_cast<const float4 *>(row);
+  const float4 c = *reinterpret_cast<const float4 *>(row + 4);
+  const float4 rt = *reinterpret_cast<const float4 *>(row + 8);
+  float4 zq[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) zq[k] = *reinterpret_cast<const float4 *>(row + (k - 4) * kStRow + 4);
+  *cen = c;
+  return leap4_2d(lf, c, rt, zq, po, av);
+}
+
+__device__ __forceinline__ float4 staged_c(const float *s, int rr, int lane) {
+  return *reinterpret_cast<const float4 *>(s + rr * kStRow + 4 * lane + 4);
+}
+
+// The tile's own rows of one pitched buffer (T rows x 128 columns) into `s`
+// (rows beyond the zero halo below the grid are zero-filled).
+template <int T>
+__device__ __forceinline__ void stage_own(const Lay &L, const float *__restrict__ f, float *s, int X0, int Z0,
+                                          int tid, int nthr) {
+  constexpr int kCh = kTileX / 4;
+  for (int i = tid; i < T * kCh; i += nthr) {
+    const int r = i / kCh, c = i - r * kCh;
+    const int z = Z0 + r;
+    const bool ok = z < L.NZ + kHaloR;
+    cp_async16z(s + r * kTileX + 4 * c, f + (ok ? L.origin + z * L.pitch + X0 + 4 * c : 0), ok);
+  }
+}
+
 } // namespace rbc

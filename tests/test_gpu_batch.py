@@ -27,11 +27,13 @@ def _window(v, off, width):
 
 
 # every forward kernel the autotuner can pick (0 = the streaming kernel) and
-# both reverse shapes, forced one pair at a time, and the tuner's own choice;
+# every reverse kernel (1 or 2 rows per warp, 0 = streaming, 3 = shared-memory
+# tiles), forced one pair at a time, and the tuner's own choice;
 # one group of all shots, one shot per group (0.3 MB) and groups of two or
 # three shots (1.5 MB)
 @pytest.mark.parametrize("tiles,l2mb,groups", [(None, None, 1), ("0,0", None, 1), ("4,2", None, 1),
-                                               (None, "0.3", 5), ("0,0", "1.5", None), ("1,1", "0", 1)])
+                                               (None, "0.3", 5), ("0,0", "1.5", None), ("1,1", "0", 1),
+                                               ("2,3", None, 1), ("2,3", "0.3", 5)])
 def test_batch_matches_single_shots_and_oracle(tiles, l2mb, groups, monkeypatch):
     import paper_2204_03380_gb300 as R
     if tiles is not None:
@@ -57,7 +59,7 @@ def test_batch_matches_single_shots_and_oracle(tiles, l2mb, groups, monkeypatch)
     # batched path
     b = R.rbc_batch_create(_shot_grid(R, w, 1), [sh["width"] for sh in inp["shots"]], a_mig)
     info = R.rbc_batch_info(b)
-    assert info["rows_fwd"] in (0, 1, 2, 4) and info["rows_rev"] in (0, 1, 2)
+    assert info["rows_fwd"] in (0, 1, 2, 4) and info["rows_rev"] in (0, 1, 2, 3)
     if tiles is not None:
         assert [info["rows_fwd"], info["rows_rev"]] == [int(v) for v in tiles.split(",")]
     if groups is not None:
