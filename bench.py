@@ -70,6 +70,9 @@ def parse():
     p.add_argument("--denoise-models", type=int, default=512, help="denoise: training models")
     p.add_argument("--denoise-size", type=int, default=96, help="denoise: training image size")
     p.add_argument("--denoise-steps", type=int, default=20000, help="denoise: Adam steps (batch 32)")
+    p.add_argument("--denoise-nb", type=int, default=None, help="denoise: boundary cells (default size / 4)")
+    p.add_argument("--denoise-nt", type=int, default=None, help="denoise: time steps (default 6.5 x size)")
+    p.add_argument("--denoise-shots", type=int, default=4, help="denoise: shots per model")
     p.add_argument("--cnn-batch", type=int, nargs=3, default=[32, 512, 512],
                    help="cnn: images, height, width of one training / inference batch")
     p.add_argument("--workload", choices=["survey2d", "shot3d", "batch2d", "denoise", "cnn", "fwi"], default="survey2d",
@@ -453,10 +456,12 @@ def run_denoise(args, rank, world):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     n = args.denoise_size
-    K, S = 16, 4
+    K, S = 16, args.denoise_shots
+    nb_d = args.denoise_nb or n // 4
+    nt_d = args.denoise_nt or int(6.5 * n)
 
     def image_set(M, seed):
-        w = W.scaled(W.SMALL_2D, nx=n, nz=n, nb=n // 4, nt=int(6.5 * n), name="dn")
+        w = W.scaled(W.SMALL_2D, nx=n, nz=n, nb=nb_d, nt=nt_d, name="dn")
         vt = [W.faulted_layers(n, n, seed + m, 1500.0, 4000.0, nlayers=8, nfaults=2) for m in range(M)]
         vm = [W.smooth_slowness(v, 4.0) for v in vt]
         g = R.make_grid(2, n, 1, n, w.nb, w.h, w.dt, w.nt)
@@ -541,7 +546,8 @@ def run_denoise(args, rank, world):
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_inf * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
            "data": "synthetic",
-           "config": {"workload": "denoise: train " + f"{args.denoise_models} pairs of {n}x{n} (K=16, {S} shots); "
+           "config": {"workload": "denoise: train " + f"{args.denoise_models} pairs of {n}x{n} (K=16, {S} shots, "
+                                  + f"nb {nb_d}, {nt_d} steps); "
                                   + f"infer {w3.ny} x-z slices of {w3.nz}x{w3.nx}",
                       "heldout_rel_l2_to_16stack": {"single_realization": e_single, "network": e_net,
                                                      "8_stack": e_half, "target": 5e-2},

@@ -22,7 +22,6 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
-#include <cstdlib>
 
 #include "../../include/rbc.h"
 #include "rbc_internal.cuh"
@@ -195,9 +194,13 @@ constexpr int kTcW = 128;                                    // output columns p
 constexpr int kTcHW = kTcW + 2;                              // halo row width (pixels)
 constexpr int kTcWBytes = 9 * 4 * 32 * 16;                   // weights, 18432 B
 constexpr long long kTcWaitCycles = 4000000000LL;            // about two seconds
-constexpr int kTcEpi = 8;                                    // epilogue warps (4 measured slower)
+constexpr int kTcEpi = 8;                                    // epilogue warps
 // Tiles of R output rows: halo planes of R + 2 rows per channel group, a
 // ring of 4 stages for R = 4 and 3 for R = 6 (what fits in 227 KB).
+// Measured at 32 x 512^2 (inference / training step): R = 6 with 8 epilogue
+// warps 1.14 / 5.51 ms; R = 4 with 8 warps 1.18 / 5.57 ms; R = 4 with 4 warps
+// 1.23 / 5.88 ms.
+constexpr int kTcR = 6;
 constexpr int tc_plane(int R) { return (R + 2) * kTcHW * 16; }
 constexpr int tc_stages(int R) { return R <= 4 ? 4 : 3; }
 constexpr int tc_smem(int R) { return kTcWBytes + tc_stages(R) * 4 * tc_plane(R) + 256; }
@@ -763,12 +766,9 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 void set_attrs() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_conv_tc<kHidden, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4));
-  cudaFuncSetAttribute(k_conv_tc<kBackData, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4));
-  cudaFuncSetAttribute(k_conv_tc<kLast, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4));
-  cudaFuncSetAttribute(k_conv_tc<kHidden, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6));
-  cudaFuncSetAttribute(k_conv_tc<kBackData, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6));
-  cudaFuncSetAttribute(k_conv_tc<kLast, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6));
+  cudaFuncSetAttribute(k_conv_tc<kHidden, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
+  cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
+  cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -845,21 +845,12 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
                     const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  // rows per tile: RBC_TC_ROWS=4 or 6 (a tuning knob, read once)
-  static const int rows = [] {
-    const char *e = getenv("RBC_TC_ROWS");
-    return e && atoi(e) == 6 ? 6 : 4;
-  }();
-  const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + rows - 1) / rows) * nimg;
+  const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcR - 1) / kTcR) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
-  if (!act_map(&tin, in, nimg, H, W, kTcHW, rows + 2)) return false;
-  if (rows == 6)
-    k_conv_tc<MODE, 6><<<grid, 32 * (kTcEpi + 2), tc_smem(6), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H,
-                                                                   W, tc_err_dev);
-  else
-    k_conv_tc<MODE, 4><<<grid, 32 * (kTcEpi + 2), tc_smem(4), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H,
-                                                                   W, tc_err_dev);
+  if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcR + 2)) return false;
+  k_conv_tc<MODE, kTcR><<<grid, 32 * (kTcEpi + 2), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
+                                                                       H, W, tc_err_dev);
   return true;
 }
 
