@@ -115,6 +115,7 @@ struct rbc_ctx {
   std::vector<cudaEvent_t> ev;  // three events per timed shot
   std::vector<cudaEvent_t> ev_free;
   bool use_graph = true;
+  int levels_per_launch = 1;  // 2: the 2-D forward phases advance two levels per launch (RBC_TEMPORAL=2)
   int zc = k3dZC, zc_r = k3dZC;  // z planes per tile of the 3-D forward / reverse kernels
   // snapshots
   std::vector<int> snap;
@@ -230,7 +231,73 @@ long long field_elems(const rbc_ctx *c) { return (long long)c->L.NX * c->L.NY * 
 
 // Algorithm 1 time loop: p^n lives in p[n & 1]; step n overwrites p^{n-1}
 // with p^{n+1}.
+// Two levels per launch (2-D, no snapshots): level m lives in buffer m mod 4
+// of (p0, p1, q0, q1) -- the q fields are free until the reverse phase, which
+// clears them -- so a launch never writes a buffer that a neighbouring block
+// still reads; an odd nt ends with one single-level step, and the last two
+// levels are left in p[(nt - 1) & 1] and p[nt & 1] as the single-level loop
+// leaves them.
+int enqueue_forward2(rbc_ctx *c, cudaStream_t s, int sample) {
+  const Lay &L = c->L;
+  const size_t bytes = sizeof(float) * (size_t)L.total;
+  float *B[4] = {c->p[0], c->p[1], c->q[0], c->q[1]};
+  CK(cudaMemsetAsync(B[0], 0, bytes, s));  // level 0
+  CK(cudaMemsetAsync(B[3], 0, bytes, s));  // level -1
+  StepArgs A{};
+  A.L = L;
+  A.a = c->a;
+  A.info = c->info;
+  A.wav = c->wav;
+  A.rec_off = c->rec_off;
+  A.seis_t = c->seis_t;
+  A.sample = sample;
+  A.zc = c->zc;
+  A.err = c->err_dev;
+  const int nt = c->g.nt;
+  float *loc_prev = B[3], *loc_cur = B[0];  // buffers of levels n - 1 and n
+  int n = 0;
+  for (; n + 2 <= nt; n += 2) {
+    A.cur = loc_cur;
+    A.n = n;
+    if (!launch_fwd2_2d(A, loc_prev, B[(n + 1) & 3], B[(n + 2) & 3], c->tile_ptr, c->tile_rec, s))
+      return fail(RBC_ECUDA, "launch failed");
+    ++g_launches;
+    loc_prev = B[(n + 1) & 3];
+    loc_cur = B[(n + 2) & 3];
+  }
+  if (n < nt) {  // one single-level step: p^{n+1} overwrites p^{n-1} in place
+    A.cur = loc_cur;
+    A.nxt = loc_prev;
+    A.n = n;
+    if (!launch_fwd(A, s)) return fail(RBC_ECUDA, "launch failed");
+    ++g_launches;
+    float *t = loc_prev;
+    loc_prev = loc_cur;
+    loc_cur = t;
+  }
+  // the panels where the reverse phase, rbc_get_panels and the last sample
+  // expect them; a copy never overwrites a panel that is still to be copied
+  float *want_prev = c->p[(nt - 1) & 1], *want_cur = c->p[nt & 1];
+  auto copy = [&](float *dst, const float *src) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+  };
+  if (loc_cur == want_prev && loc_prev == want_cur) {  // swapped: through a q buffer
+    CK(copy(c->q[0], loc_cur));
+    CK(copy(want_prev, loc_prev));
+    CK(copy(want_cur, c->q[0]));
+  } else if (loc_prev == want_cur) {
+    CK(copy(want_prev, loc_prev));
+    if (loc_cur != want_cur) CK(copy(want_cur, loc_cur));
+  } else {
+    if (loc_cur != want_cur) CK(copy(want_cur, loc_cur));
+    if (loc_prev != want_prev) CK(copy(want_prev, loc_prev));
+  }
+  CKL();
+  return RBC_OK;
+}
+
 int enqueue_forward(rbc_ctx *c, cudaStream_t s, int sample) {
+  if (c->levels_per_launch == 2 && c->snap.empty() && c->g.nt >= 2) return enqueue_forward2(c, s, sample);
   const Lay &L = c->L;
   const size_t bytes = sizeof(float) * (size_t)L.total;
   CK(cudaMemsetAsync(c->p[0], 0, bytes, s));
@@ -563,6 +630,14 @@ int rbc_create(const rbc_grid *g, const float *a_dev, rbc_ctx **out) {
   cudaGetDevice(&c->dev);
   const char *env = getenv("RBC_GRAPH");
   c->use_graph = !(env && env[0] == '0');
+  // temporal blocking of the 2-D forward phases; it uses the receiver lists of
+  // the 2-D reverse tiling, so it needs that tiling's 8-row tiles
+  const char *tenv = getenv("RBC_TEMPORAL");
+  if (tenv && atoi(tenv) == 2 && L.ndim == 2) {
+    int gx, gy, gz, t;
+    rev_tiling(L, c->zc_r, &gx, &gy, &gz, &t);
+    if (t == fwd2_tile_rows()) c->levels_per_launch = 2;
+  }
   const char *zenv = getenv("RBC_ZC");  // tuning knob: z planes per 3-D block
   if (L.ndim == 3) {
     c->zc = zc_for_3d(L, true);

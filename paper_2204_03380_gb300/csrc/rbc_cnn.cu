@@ -63,88 +63,127 @@ enum { kHidden = 0, kLast = 1, kBackData = 2 };
 // PPT pixels per thread (rows ty, ty + 8, ...): 2 for the forward layer, 1
 // for the backward-data pass, whose mask loads want the occupancy.
 template <int MODE> constexpr int ppt_1to32() { return MODE == kHidden ? 2 : 1; }
+// Persistent blocks walk the tiles (x fastest, then rows, then images); the
+// weights are converted once per block, and the next tile's input halo is
+// loaded into registers while the current tile is computed and stored, then
+// parked in the other half of a double-buffered shared-memory halo.
+constexpr int kHalo1 = 3;  // halo values per thread: ceil(18 x 34 / 256) for P = 2
 template <int MODE>
 __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
-                                                    __nv_bfloat16 *__restrict__ out, int H, int W) {
-  constexpr int P = ppt_1to32<MODE>(), TH1 = 8 * P;
+                                                    __nv_bfloat16 *__restrict__ out, int nimg, int H, int W) {
+  constexpr int P = ppt_1to32<MODE>(), TH1 = 8 * P, HP = (TH1 + 2) * (TW + 2);
+  static_assert(HP <= kHalo1 * 256, "the halo must fit in kHalo1 values per thread");
   __shared__ __align__(16) float s_w[9 * 32];
   __shared__ __align__(16) float s_b[32];
-  __shared__ float s_in[(TH1 + 2) * (TW + 2)];
+  __shared__ float s_in[2][HP];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int img = blockIdx.z, y0 = blockIdx.y * TH1, x0 = blockIdx.x * TW;
-  const long long ibase = (long long)img * H * W;
+  const int ntx = (W + TW - 1) / TW, nty = (H + TH1 - 1) / TH1;
+  const long long ntiles = (long long)ntx * nty * nimg, HWp = (long long)H * W;
   for (int i = tid; i < 9 * 32; i += 256) s_w[i] = __bfloat162float(wt[i]);
   if (MODE == kHidden && tid < 32) s_b[tid] = bias[tid];
-  for (int i = tid; i < (TH1 + 2) * (TW + 2); i += 256) {
-    const int yy = y0 + i / (TW + 2) - 1, xx = x0 + i % (TW + 2) - 1;
-    s_in[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __bfloat162float(in[ibase + (long long)yy * W + xx]) : 0.f;
-  }
-  __syncthreads();
-  const int xx = x0 + tx;
-  float2 acc[P][16];  // [pixel][channel pair]
+  auto origin = [&](long long t, int &img, int &y0, int &x0) {
+    img = (int)(t / ((long long)ntx * nty));
+    const int rem = (int)(t % ((long long)ntx * nty));
+    y0 = (rem / ntx) * TH1;
+    x0 = (rem % ntx) * TW;
+  };
+  // this thread's share of a tile's halo (zero outside the image)
+  auto fetch = [&](long long t, float *v) {
+    int img, y0, x0;
+    origin(t, img, y0, x0);
 #pragma unroll
-  for (int p = 0; p < P; ++p)
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc[p][c] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    float2 a[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const float v = s_in[(ty + 8 * p + t / 3) * (TW + 2) + tx + t % 3];
-      a[p] = make_float2(v, v);
+    for (int k = 0; k < kHalo1; ++k) {
+      const int i = tid + 256 * k;
+      const int yy = y0 + i / (TW + 2) - 1, xx = x0 + i % (TW + 2) - 1;
+      v[k] = (i < HP && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                 ? __bfloat162float(in[(long long)img * HWp + (long long)yy * W + xx])
+                 : 0.f;
     }
-    const float4 *w4 = reinterpret_cast<const float4 *>(s_w + t * 32);
+  };
+  auto park = [&](const float *v, int b) {
 #pragma unroll
-    for (int c4 = 0; c4 < 8; ++c4) {
-      const float4 w = w4[c4];
-      const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
+    for (int k = 0; k < kHalo1; ++k)
+      if (tid + 256 * k < HP) s_in[b][tid + 256 * k] = v[k];
+  };
+  float v[kHalo1];
+  if ((long long)blockIdx.x < ntiles) {
+    fetch(blockIdx.x, v);
+    park(v, 0);
+  }
+  int b = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, b ^= 1) {
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) fetch(tn, v);  // in flight during this tile
+    __syncthreads();                // s_in[b] holds tile t
+    int img, y0, x0;
+    origin(t, img, y0, x0);
+    const int xx = x0 + tx;
+    const float *sb = s_in[b];
+    float2 acc[P][16];  // [pixel][channel pair]
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[p][c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int tp = 0; tp < 9; ++tp) {
+      float2 a[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        acc[p][2 * c4] = __ffma2_rn(a[p], wl, acc[p][2 * c4]);
-        acc[p][2 * c4 + 1] = __ffma2_rn(a[p], wh, acc[p][2 * c4 + 1]);
+        const float x = sb[(ty + 8 * p + tp / 3) * (TW + 2) + tx + tp % 3];
+        a[p] = make_float2(x, x);
       }
-    }
-  }
-  const long long HWp = (long long)H * W;
+      const float4 *w4 = reinterpret_cast<const float4 *>(s_w + tp * 32);
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
-    const int yy = y0 + ty + 8 * p;
-    if (yy >= H || xx >= W) continue;
-    const long long pix = (long long)yy * W + xx;
-    float v[32];
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 w = w4[c4];
+        const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      v[2 * c] = acc[p][c].x;
-      v[2 * c + 1] = acc[p][c].y;
-    }
-    if (MODE == kHidden) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + s_b[c], 0.f);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 m4 = reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp + pix];
-        const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 mf = __bfloat1622float2(m2[e]);
-          if (!(mf.x > 0.f)) v[q * 8 + 2 * e] = 0.f;
-          if (!(mf.y > 0.f)) v[q * 8 + 2 * e + 1] = 0.f;
+        for (int p = 0; p < P; ++p) {
+          acc[p][2 * c4] = __ffma2_rn(a[p], wl, acc[p][2 * c4]);
+          acc[p][2 * c4 + 1] = __ffma2_rn(a[p], wh, acc[p][2 * c4 + 1]);
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint4 pk;
-      __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+    for (int p = 0; p < P; ++p) {
+      const int yy = y0 + ty + 8 * p;
+      if (yy >= H || xx >= W) continue;
+      const long long pix = (long long)yy * W + xx;
+      float o[32];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
-      reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
+      for (int c = 0; c < 16; ++c) {
+        o[2 * c] = acc[p][c].x;
+        o[2 * c + 1] = acc[p][c].y;
+      }
+      if (MODE == kHidden) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) o[c] = fmaxf(o[c] + s_b[c], 0.f);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 m4 = reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp + pix];
+          const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 mf = __bfloat1622float2(m2[e]);
+            if (!(mf.x > 0.f)) o[q * 8 + 2 * e] = 0.f;
+            if (!(mf.y > 0.f)) o[q * 8 + 2 * e + 1] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint4 pk;
+        __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(o[q * 8 + 2 * e], o[q * 8 + 2 * e + 1]);
+        reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
+      }
     }
+    if (tn < ntiles) park(v, b ^ 1);  // read two tiles on, after the next barrier
   }
 }
 
@@ -775,6 +814,21 @@ void set_attrs() {
   done = true;
 }
 
+// Persistent grid of the one-channel kernel: its resident blocks, at most one per tile.
+template <int MODE>
+int grid_1to32(int nimg, int H, int W) {
+  static int slots = 0;
+  if (!slots) {
+    int sms = 152, per = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32<MODE>, 256, 0);
+    slots = sms * (per > 0 ? per : 1);
+  }
+  const int th1 = 8 * ppt_1to32<MODE>();
+  const long long tiles = (long long)((W + TW - 1) / TW) * ((H + th1 - 1) / th1) * nimg;
+  return (int)(tiles < slots ? tiles : slots);
+}
+
 int grid_of(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
@@ -873,9 +927,8 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
-  const int th1 = 8 * ppt_1to32<kHidden>();
-  const dim3 grid((W + TW - 1) / TW, (H + th1 - 1) / th1, nimg);
-  k_conv_1to32<kHidden><<<grid, 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], H, W);
+  k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr,
+                                                                          w.act[0], nimg, H, W);
   bool ok_tc = true;
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
@@ -898,8 +951,7 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   cudaStream_t s = (cudaStream_t)stream;
   const long long npx = (long long)nimg * H * W;
   Ws w = carve(ws_dev, npx);  // activations from the preceding rbc_cnn_forward
-  const int th1 = 8 * ppt_1to32<kBackData>();
-  const dim3 grid((W + TW - 1) / TW, (H + th1 - 1) / th1, nimg);
+
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const int pg = 2 * sms;
@@ -908,7 +960,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   k_conv_wgrad32<C, 1><<<pg, 288, kWgSmem, s>>>(w.act[3], w.dz[1], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
-  k_conv_1to32<kBackData><<<grid, 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3], w.dz[0], H, W);
+  k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3],
+                                                                              w.dz[0], nimg, H, W);
   // layers 4, 3, 2: dW from dz; dz below = conv^T(dz) masked
   int cur = 0;
   bool ok_tc = true;

@@ -163,6 +163,12 @@ inline bool lay_make(int ndim, long long NX, long long NY, long long NZ, Lay *ou
 // kernel launchers (rbc_kernels.cu)
 namespace rbc {
 bool launch_fwd(const StepArgs &A, cudaStream_t s);
+// Two forward levels per launch (2-D): (prev = p^{n-1}, A.cur = p^n) ->
+// (out1 = p^{n+1}, out2 = p^{n+2}); tiles of 128 x fwd2_tile_rows() with the
+// receivers of each tile in (tile_ptr, tile_rec).
+bool launch_fwd2_2d(const StepArgs &A, const float *prev, float *out1, float *out2, const int *tile_ptr,
+                    const int *tile_rec, cudaStream_t s);
+int fwd2_tile_rows();
 bool launch_rev(const RevArgs &A, cudaStream_t s);
 // rbc_kernels3d.cu (TMA-fed 3-D kernels)
 bool launch_fwd3d(const StepArgs &A, cudaStream_t s);

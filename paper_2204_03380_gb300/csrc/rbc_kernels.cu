@@ -235,6 +235,122 @@ __global__ void __launch_bounds__(32 * NW, MB) k_rev2d_tile(const RevArgs A) {
   griddep_launch();
 }
 
+// ------------------------------------------ 2-D, two levels per launch ----
+// Temporal blocking of the forward step: one launch advances (p^{n-1}, p^n)
+// to (p^{n+1}, p^{n+2}).  A block of 4 warps owns a tile of 128 columns x 8
+// rows.  It stages p^n over the tile and an 8-node apron (24 x 144 floats),
+// p^{n-1} and a over a 4-node apron (16 x 136 each), computes p^{n+1} over the
+// 4-node apron into shared memory (the source term with f[n]), then p^{n+2}
+// over the tile (f[n+1]), and writes both levels of its tile.  Level m lives
+// in buffer m mod 4 of a four-buffer rotation, so no launch writes a buffer
+// that a neighbouring block still reads.  The receivers of the tile (the
+// reverse kernel's per-tile lists, same 128 x 8 tiling) record levels n and
+// n + 1 from shared memory.
+constexpr int kT2 = 8;                          // rows per tile
+constexpr int kP2W = kTileX + 4 * kHaloR;        // 144: p^n row, x0 - 8 .. x0 + 135
+constexpr int kQ2W = kTileX + 2 * kHaloR;        // 136: apron rows, x0 - 4 .. x0 + 131
+
+// Rows z0 .. z0 + rows - 1, columns x0 .. x0 + 4 chunks - 1 of `f` into `s`
+// (row stride `stride` floats); rows outside -4 .. NZ + 3 are zero-filled.
+__device__ __forceinline__ void stage_box(const Lay &L, const float *__restrict__ f, float *s, int x0, int z0,
+                                          int rows, int chunks, int stride, int tid, int nthr) {
+  for (int i = tid; i < rows * chunks; i += nthr) {
+    const int r = i / chunks, c = i - r * chunks;
+    const int z = z0 + r;
+    const bool ok = z >= -kHaloR && z < L.NZ + kHaloR;
+    cp_async16z(s + r * stride + 4 * c, f + (ok ? L.origin + z * L.pitch + x0 + 4 * c : 0), ok);
+  }
+}
+
+__global__ void __launch_bounds__(128, 5) k_fwd2d_2lev(const StepArgs A, const float *__restrict__ prev,
+                                                       float *__restrict__ out1, float *__restrict__ out2,
+                                                       const int *__restrict__ tile_ptr,
+                                                       const int *__restrict__ tile_rec) {
+  __shared__ __align__(16) float s_c[(kT2 + 16) * kP2W];  // p^n
+  __shared__ __align__(16) float s_p[(kT2 + 8) * kQ2W];   // p^{n-1}
+  __shared__ __align__(16) float s_a[(kT2 + 8) * kQ2W];   // a
+  __shared__ __align__(16) float s_q[(kT2 + 8) * kQ2W];   // p^{n+1}
+  const Lay &L = A.L;
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+  const int X0 = blockIdx.x * kTileX, Z0 = blockIdx.y * kT2;
+  griddep_wait();
+  stage_box(L, A.cur, s_c, X0 - 2 * kHaloR, Z0 - 2 * kHaloR, kT2 + 16, kP2W / 4, kP2W, tid, 128);
+  stage_box(L, prev, s_p, X0 - kHaloR, Z0 - kHaloR, kT2 + 8, kQ2W / 4, kQ2W, tid, 128);
+  stage_box(L, A.a, s_a, X0 - kHaloR, Z0 - kHaloR, kT2 + 8, kQ2W / 4, kQ2W, tid, 128);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int src = A.info->src_off;
+  const float f0 = A.wav[A.n] * A.info->src_fwd, f1 = A.wav[A.n + 1] * A.info->src_fwd;
+  // p^{n+1} over the apron: rows Z0 - 4 .. Z0 + 11, columns X0 - 4 .. X0 + 131
+  // (34 float4 per row: lane k and, for lanes 0 and 1, float4 32 + lane);
+  // outside the grid every staged value is zero, so the update is zero there
+  for (int r = w * 4; r < w * 4 + 4; ++r) {
+    const int z = Z0 - kHaloR + r;
+    for (int c4 = lane; c4 < kQ2W / 4; c4 += 32) {
+      const float *row = s_c + (r + kHaloR) * kP2W + 4 * c4;  // p^n at x = X0 - 8 + 4 c4 ..
+      const float4 lf = *reinterpret_cast<const float4 *>(row), c = *reinterpret_cast<const float4 *>(row + 4),
+                   rt = *reinterpret_cast<const float4 *>(row + 8);
+      float4 zq[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) zq[k] = *reinterpret_cast<const float4 *>(row + (k - 4) * kP2W + 4);
+      const float4 av = *reinterpret_cast<const float4 *>(s_a + r * kQ2W + 4 * c4);
+      const float4 po = *reinterpret_cast<const float4 *>(s_p + r * kQ2W + 4 * c4);
+      float4 v = leap4_2d(lf, c, rt, zq, po, av);
+      const int d = src - (L.origin + z * L.pitch + X0 - kHaloR + 4 * c4);
+      if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * f0);
+      *reinterpret_cast<float4 *>(s_q + r * kQ2W + 4 * c4) = v;
+    }
+  }
+  __syncthreads();
+  // p^{n+2} over the tile; both levels of the tile to their buffers
+  const int x0 = X0 + lane * 4;
+  const bool xok = x0 < L.NX4;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int rl = w * 2 + j, z = Z0 + rl;
+    if (!(xok && z < L.NZ)) continue;
+    const float *row = s_q + (rl + kHaloR) * kQ2W + 4 * lane;  // p^{n+1} at x = x0 - 4 ..
+    const float4 lf = *reinterpret_cast<const float4 *>(row), c = *reinterpret_cast<const float4 *>(row + 4),
+                 rt = *reinterpret_cast<const float4 *>(row + 8);
+    float4 zq[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) zq[k] = *reinterpret_cast<const float4 *>(row + (k - 4) * kQ2W + 4);
+    const float4 av = *reinterpret_cast<const float4 *>(s_a + (rl + kHaloR) * kQ2W + 4 * lane + 4);
+    const float4 po = *reinterpret_cast<const float4 *>(s_c + (rl + 2 * kHaloR) * kP2W + 4 * lane + 8);
+    float4 v = leap4_2d(lf, c, rt, zq, po, av);
+    const int o = L.origin + z * L.pitch + x0;
+    const int d = src - o;
+    if ((unsigned)d < 4u) point_sub(v, d, cmp(av, d) * f1);
+    st4(out1 + o, c);
+    st4(out2 + o, v);
+  }
+  // record levels n and n + 1 at this tile's receivers
+  if (A.sample) {
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const int nrec = A.info->nrec;
+    for (int k = tile_ptr[bid] + tid; k < tile_ptr[bid + 1]; k += 128) {
+      const int r = tile_rec[k];
+      const int off = A.rec_off[r] - L.origin;
+      const int z = off / L.pitch, x = off - z * L.pitch;
+      A.seis_t[(long long)A.n * nrec + r] = s_c[(z - Z0 + 2 * kHaloR) * kP2W + x - X0 + 2 * kHaloR];
+      A.seis_t[(long long)(A.n + 1) * nrec + r] = s_q[(z - Z0 + kHaloR) * kQ2W + x - X0 + kHaloR];
+    }
+  }
+  griddep_launch();
+}
+
+bool launch_fwd2_2d(const StepArgs &A, const float *prev, float *out1, float *out2, const int *tile_ptr,
+                    const int *tile_rec, cudaStream_t s) {
+  const Lay &L = A.L;
+  if (L.ndim != 2) return false;
+  const dim3 grid((L.NX + kTileX - 1) / kTileX, (L.NZ + kT2 - 1) / kT2);
+  launch_pdl(k_fwd2d_2lev, grid, dim3(32, 4), 0, s, A, prev, out1, out2, tile_ptr, tile_rec);
+  return true;
+}
+
+int fwd2_tile_rows() { return kT2; }
+
 // ------------------------------------------------------------ launchers ----
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
