@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // ---------------------------------------------------------------------------
 // 32 -> 32 channel layers on the 5th-generation tensor cores (tcgen05).
 //
-// A tile is R output rows x 128 columns of one image.  The accumulator
+// A tile is R output rows x 126 columns of one image.  The accumulator
 // of output row rr is a 128 (pixels) x 32 (channels) fp32 matrix in tensor
 // memory:
 //   D_rr[px][co] = sum_(dy, dx) sum_ci halo[rr + dy][px + dx][ci] * w[dy][dx][co][ci].
@@ -209,28 +209,37 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // Both operands sit in shared memory in the no-swizzle K-major layout: a
 // "core matrix" is 8 rows of 16 bytes (8 channels) stored contiguously.  The
 // activations are kept channel-group planar in memory ([image][group of 8
-// channels][row][column][8]), so one 5-D TMA copy lands a tile's halo as four
-// planes (one per channel group) of halo pixels in row-major order at 16
-// bytes each: 8 consecutive pixels of any halo row are one core matrix, and
+// channels][row][column][8]), so one 4-D TMA copy (rows of 8-byte elements)
+// lands a tile's halo as four planes (one per channel group) of halo pixels
+// in row-major order at 16 bytes each: 8 consecutive pixels of any halo row
+// are one core matrix, and
 // the operand of a shifted tap is the same planes with the start address
-// moved by (h * 130 + dx) * 16 bytes (stride between 8-pixel groups 128
+// moved by (h * 128 + dx) * 16 bytes (stride between 8-pixel groups 128
 // bytes, between channel groups one plane).  Weights in shared memory:
 // [dx][ci / 8][dy][co][8], so the 96 (dy, co) rows of one (dx, ci group) are
 // consecutive core matrices (stride 128 bytes) and the two channel groups of a
 // K = 16 slice are 1536 bytes apart.
 //
-// Per block (one per SM, persistent over tiles), three roles: warp 4 streams
-// each tile's halo (zero-filled outside the image) into a 4-stage shared-
-// memory ring; warp 5 issues the 72 MMAs of a tile into one of two
-// tensor-memory accumulators and commits them to the ring's "empty" and the
-// accumulator's "full" barrier; warps 0-3 (tensor-memory lanes 0-127, one
-// pixel each) drain the other accumulator with tcgen05.ld, apply the epilogue
-// (the backward-data pass reads its ReLU mask from global memory, issued
-// before the accumulator wait) and store.  Copies of tiles k+1 .. k+3, MMAs
-// of tile k and the epilogue of tile k-1 overlap.  Every wait is bounded; a
+// Per block (one per SM, persistent over tiles), three roles: warp kTcEpi
+// streams each tile's halo (zero-filled outside the image) into a shared-
+// memory ring of tc_stages(R) stages; warp kTcEpi + 1 issues the 6 (R + 2)
+// MMAs of a tile into one of two tensor-memory accumulators and commits them
+// to the ring's "empty" and the accumulator's "full" barrier; warps 0 ..
+// kTcEpi - 1 (two per tensor-memory lane quarter, one pixel per thread, half
+// of the rows each) drain the other accumulator with tcgen05.ld, apply the
+// epilogue (the backward-data pass reads its ReLU mask from global memory,
+// issued before the accumulator wait) and store.  Copies of the next tiles,
+// MMAs of tile k and the epilogue of tile k-1 overlap.  Every wait is bounded; a
 // block that gives up flags the error word and stops.
-constexpr int kTcW = 128;                                    // output columns per tile (M)
-constexpr int kTcHW = kTcW + 2;                              // halo row width (pixels)
+// A tile is kTcOut = 126 output columns: its halo row is then 128 pixels of
+// 16 bytes, 2 KB, which one tensor copy moves as 256 8-byte elements (the
+// box limit), against a box whose innermost dimension is one pixel's 16
+// bytes; measured on GB300 streaming such halos on every SM: 9.2 TB/s for
+// the 2 KB rows, 4.4 TB/s for the 16-byte rows.  The MMAs keep M = 128:
+// rows 126 and 127 of a shifted operand run into the next halo row and
+// their outputs are discarded.
+constexpr int kTcOut = 126;                                  // output columns per tile
+constexpr int kTcHW = 128;                                   // halo row width (pixels)
 constexpr int kTcWBytes = 9 * 4 * 32 * 16;                   // weights, 18432 B
 constexpr long long kTcWaitCycles = 4000000000LL;            // about two seconds
 constexpr int kTcEpi = 8;                                    // epilogue warps
@@ -314,12 +323,12 @@ __device__ __forceinline__ bool tc_wait(uint32_t b, uint32_t parity, volatile in
   return true;
 }
 
-__device__ __forceinline__ void tc_tma5(uint32_t dst, const CUtensorMap *tm, int c1, int c2, int c4, uint32_t bar) {
-  // coordinates (channel 0, x, y, group 0, image)
+__device__ __forceinline__ void tc_tma4(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c3, uint32_t bar) {
+  // coordinates (8-byte element along the row, y, group 0, image)
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-      "%6}], [%7];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(c1), "r"(c2), "r"(0), "r"(c4), "r"(bar)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(0), "r"(c3), "r"(bar)
       : "memory");
 }
 
@@ -425,7 +434,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int ntx = (W + kTcW - 1) / kTcW, nty = (H + R - 1) / R;
+  const int ntx = (W + kTcOut - 1) / kTcOut, nty = (H + R - 1) / R;
   const long long ntiles = (long long)ntx * nty * nimg;
   // Each block takes a contiguous range of tiles, ordered down the image
   // columns (y fastest): a tile's two halo rows are rows of the block's
@@ -438,7 +447,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
     img = (int)(t / ((long long)ntx * nty));
     const int rem = (int)(t % ((long long)ntx * nty));
     y0 = (rem / ntx) * R;
-    x0 = (rem % ntx) * kTcW;
+    x0 = (rem % ntx) * kTcOut;
   };
   if (warp == kTcEpi) {
     // ---- producer: one TMA copy of the halo per tile ----
@@ -451,7 +460,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
         int img, y0, x0;
         tile_xy(t, img, y0, x0);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(STAGE) : "memory");
-        tc_tma5(s_h + s * STAGE, &tm_in, x0 - 1, y0 - 1, img, full(s));
+        tc_tma4(s_h + s * STAGE, &tm_in, 2 * (x0 - 1), y0 - 1, img, full(s));
       }
       if (*abort_blk) {  // let the copies in flight land before the block exits
         for (int k = (issued > STAGES ? issued - STAGES : 0); k < issued; ++k) {
@@ -509,7 +518,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
       const int b = k & 1, ub = k >> 1;
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
-      const int px = lq * 32 + lane, xx = x0 + px;
+      const int px = lq * 32 + lane, xx = px < kTcOut ? x0 + px : W;  // MMA rows 126, 127: no pixel
       uint4 mk[RE][4];  // backward-data: this pixel's masks, loaded while the MMAs run
       if (MODE == kBackData) {
 #pragma unroll
@@ -879,16 +888,17 @@ int tc_err() {
   return RBC_OK;
 }
 
-// 5-D tensor map over a channel-group planar bf16 activation buffer (32
-// channels): dims (channel in group, x, y, group, image); box (8, bx, by, 4, 1).
-bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, int bx, int by) {
+// 4-D tensor map over a channel-group planar bf16 activation buffer (32
+// channels) seen as 8-byte elements: dims (2 W elements of a row -- two per
+// pixel --, y, group, image); box (256 = 128 pixels, by rows, 4 groups, 1).
+bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, int by) {
   auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(rbc::tmap_encode_fn());
   if (!fn) return false;
-  cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)nimg};
-  cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)W * H * 64};
-  cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, 4, 1};
-  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(buf), dims, strides, box, estr,
+  cuuint64_t dims[4] = {2 * (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)nimg};
+  cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)W * H * 64};
+  cuuint32_t box[4] = {2 * kTcHW, (cuuint32_t)by, 4, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<__nv_bfloat16 *>(buf), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -899,10 +909,10 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
                     const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const long long tiles = (long long)((W + kTcW - 1) / kTcW) * ((H + kTcR - 1) / kTcR) * nimg;
+  const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + kTcR - 1) / kTcR) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
-  if (!act_map(&tin, in, nimg, H, W, kTcHW, kTcR + 2)) return false;
+  if (!act_map(&tin, in, nimg, H, W, kTcR + 2)) return false;
   k_conv_tc<MODE, kTcR><<<grid, 32 * (kTcEpi + 2), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
                                                                        H, W, tc_err_dev);
   return true;
