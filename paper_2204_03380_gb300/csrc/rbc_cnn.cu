@@ -519,6 +519,12 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
       const int px = lq * 32 + lane, xx = px < kTcOut ? x0 + px : W;  // MMA rows 126, 127: no pixel
+      float rs[RE];     // last layer: this pixel's residual input, loaded while the MMAs run
+      if (MODE == kLast) {
+#pragma unroll
+        for (int i = 0; i < RE; ++i)
+          rs[i] = (y0 + r0 + i < H && xx < W) ? resid[(long long)img * HWp + (long long)(y0 + r0 + i) * W + xx] : 0.f;
+      }
       uint4 mk[RE][4];  // backward-data: this pixel's masks, loaded while the MMAs run
       if (MODE == kBackData) {
 #pragma unroll
@@ -540,10 +546,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
           const float v0 = tmem_ld1(ta);
           tmem_zero1(ta);  // channel 0 only: the padding channels never leave zero
           const int yy = y0 + rr;
-          if (yy < H && xx < W) {
-            const long long p = (long long)img * HWp + (long long)yy * W + xx;
-            out_f[p] = resid[p] + v0 + s_bias[0];
-          }
+          if (yy < H && xx < W) out_f[(long long)img * HWp + (long long)yy * W + xx] = rs[rr - r0] + v0 + s_bias[0];
         }
       } else {
 #pragma unroll 1
