@@ -22,7 +22,6 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
-#include <cstdlib>
 
 #include "../../include/rbc.h"
 #include "rbc_internal.cuh"
@@ -245,11 +244,13 @@ constexpr int kTcWBytes = 9 * 4 * 32 * 16;                   // weights, 18432 B
 constexpr long long kTcWaitCycles = 4000000000LL;            // about two seconds
 constexpr int kTcEpi = 8;                                    // epilogue warps
 // Tiles of R output rows: halo planes of R + 2 rows per channel group, a
-// ring of 4 stages for R = 4 and 3 for R = 6 (what fits in 227 KB).
-// Measured at 32 x 512^2 (inference / training step): R = 6 with 8 epilogue
-// warps 1.14 / 5.51 ms; R = 4 with 8 warps 1.18 / 5.57 ms; R = 4 with 4 warps
-// 1.23 / 5.88 ms.
-constexpr int kTcR = 6;
+// ring of 4 stages for R = 4, 3 for R = 6 and 2 for R = 8 (what fits in
+// 227 KB); R = 8 fills tensor memory with the two accumulator buffers.
+// Measured at 32 x 512^2 with 126-column tiles (inference / training step):
+// R = 8 0.951 / 5.20 ms, R = 6 0.969 / 5.37 ms, R = 4 1.071 / 5.49 ms; with
+// 128-column tiles and the 16-byte-row halo copy: R = 6 1.14 / 5.51 ms, R = 4
+// 1.18 / 5.57 ms, R = 4 with 4 epilogue warps 1.23 / 5.88 ms.
+constexpr int kTcR = 8;
 constexpr int tc_plane(int R) { return (R + 2) * kTcHW * 16; }
 constexpr int tc_stages(int R) { return R <= 4 ? 4 : R <= 6 ? 3 : 2; }
 constexpr int tc_smem(int R) { return kTcWBytes + tc_stages(R) * 4 * tc_plane(R) + 256; }
@@ -819,12 +820,9 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 void set_attrs() {
   static bool done = false;
   if (done) return;
-#define RBC_TC_ATTR(R)                                                                                      \
-  cudaFuncSetAttribute(k_conv_tc<kHidden, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(R));   \
-  cudaFuncSetAttribute(k_conv_tc<kBackData, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(R)); \
-  cudaFuncSetAttribute(k_conv_tc<kLast, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(R));
-  RBC_TC_ATTR(4) RBC_TC_ATTR(6) RBC_TC_ATTR(8)
-#undef RBC_TC_ATTR
+  cudaFuncSetAttribute(k_conv_tc<kHidden, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
+  cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
+  cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
@@ -917,22 +915,12 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
                     const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  static const int rows = [] {  // tuning knob for the sweep (RBC_TC_ROWS = 4, 6 or 8)
-    const char *e = getenv("RBC_TC_ROWS");
-    const int r = e ? atoi(e) : kTcR;
-    return r == 4 || r == 6 || r == 8 ? r : kTcR;
-  }();
-  const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + rows - 1) / rows) * nimg;
+  const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + kTcR - 1) / kTcR) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
-  if (!act_map(&tin, in, nimg, H, W, rows + 2)) return false;
-  const dim3 blk(32 * (kTcEpi + 2));
-  if (rows == 4)
-    k_conv_tc<MODE, 4><<<grid, blk, tc_smem(4), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
-  else if (rows == 8)
-    k_conv_tc<MODE, 8><<<grid, blk, tc_smem(8), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
-  else
-    k_conv_tc<MODE, 6><<<grid, blk, tc_smem(6), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev);
+  if (!act_map(&tin, in, nimg, H, W, kTcR + 2)) return false;
+  k_conv_tc<MODE, kTcR><<<grid, 32 * (kTcEpi + 2), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
+                                                                       H, W, tc_err_dev);
   return true;
 }
 
