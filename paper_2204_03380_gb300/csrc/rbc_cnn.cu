@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <cstdlib>
 
 #include "../../include/rbc.h"
 #include "rbc_internal.cuh"
@@ -181,6 +182,127 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 #pragma unroll
         for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(o[q * 8 + 2 * e], o[q * 8 + 2 * e + 1]);
         reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
+      }
+    }
+    if (tn < ntiles) park(v, b ^ 1);  // read two tiles on, after the next barrier
+  }
+}
+
+// The same 1 -> 32 layer on the warp-level tensor cores: per 16 pixels of a
+// row, one m16n8k16 MMA per group of 8 output channels with K = the 9 taps
+// (padded to 16, zero weights): the im2col operand A[pixel][tap] is gathered
+// from the staged halo straight into the A fragments, the weights are the B
+// fragments, held in registers for the whole kernel.  A block of 8 warps
+// covers 8 rows x 128 pixels (one warp per row); persistent blocks prefetch
+// the next tile's halo into registers.  The output fragment of lane (g, t)
+// holds channels 8n + 2t, 8n + 2t + 1 of pixels g and g + 8: 4-byte pieces of
+// the pixels' 16-byte channel groups, stored 128 contiguous bytes per warp
+// and group.
+constexpr int kM1R = 8, kM1C = 128, kM1HP = (kM1R + 2) * (kM1C + 2);  // tile rows, columns, halo values
+constexpr int kM1Pre = (kM1HP + 255) / 256;                          // halo values per thread
+__device__ __forceinline__ uint32_t pack_bf16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_conv_1to32_mma(const __nv_bfloat16 *__restrict__ in,
+                                                        const __nv_bfloat16 *__restrict__ wt,
+                                                        const float *__restrict__ bias,
+                                                        const __nv_bfloat16 *__restrict__ mask,
+                                                        __nv_bfloat16 *__restrict__ out, int nimg, int H, int W) {
+  __shared__ uint16_t s_x[2][kM1HP];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+  const int ntx = (W + kM1C - 1) / kM1C, nty = (H + kM1R - 1) / kM1R;
+  const long long ntiles = (long long)ntx * nty * nimg, HWp = (long long)H * W;
+  const uint16_t *win = reinterpret_cast<const uint16_t *>(wt);
+  // B fragments: B[k][co] = w[tap k][co] for k < 9, zero above
+  uint32_t bf[4][2];
+  float2 bs[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int co = 8 * n + g;
+    bf[n][0] = pack_bf16(win[(2 * t) * 32 + co], win[(2 * t + 1) * 32 + co]);
+    bf[n][1] = t == 0 ? pack_bf16(win[8 * 32 + co], 0) : 0u;
+    bs[n] = MODE == kHidden ? make_float2(bias[8 * n + 2 * t], bias[8 * n + 2 * t + 1]) : make_float2(0.f, 0.f);
+  }
+  // halo taps of this lane: k0 = 2t, k1 = 2t + 1 (and tap 8 for t = 0)
+  const int o0 = ((2 * t) / 3) * (kM1C + 2) + (2 * t) % 3, o1 = ((2 * t + 1) / 3) * (kM1C + 2) + (2 * t + 1) % 3;
+  const int o8 = 2 * (kM1C + 2) + 2;
+  auto origin = [&](long long tt, int &img, int &y0, int &x0) {
+    img = (int)(tt / ((long long)ntx * nty));
+    const int rem = (int)(tt % ((long long)ntx * nty));
+    y0 = (rem / ntx) * kM1R;
+    x0 = (rem % ntx) * kM1C;
+  };
+  const uint16_t *xin = reinterpret_cast<const uint16_t *>(in);
+  auto fetch = [&](long long tt, uint16_t *v) {
+    int img, y0, x0;
+    origin(tt, img, y0, x0);
+#pragma unroll
+    for (int k = 0; k < kM1Pre; ++k) {
+      const int i = tid + 256 * k;
+      const int yy = y0 + i / (kM1C + 2) - 1, xx = x0 + i % (kM1C + 2) - 1;
+      v[k] = (i < kM1HP && yy >= 0 && yy < H && xx >= 0 && xx < W) ? xin[(long long)img * HWp + (long long)yy * W + xx]
+                                                                      : (uint16_t)0;
+    }
+  };
+  auto park = [&](const uint16_t *v, int b) {
+#pragma unroll
+    for (int k = 0; k < kM1Pre; ++k)
+      if (tid + 256 * k < kM1HP) s_x[b][tid + 256 * k] = v[k];
+  };
+  uint16_t v[kM1Pre];
+  if ((long long)blockIdx.x < ntiles) {
+    fetch(blockIdx.x, v);
+    park(v, 0);
+  }
+  uint32_t *o32 = reinterpret_cast<uint32_t *>(out);
+  const uint32_t *m32 = reinterpret_cast<const uint32_t *>(mask);
+  int b = 0;
+  for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x, b ^= 1) {
+    const long long tn = tt + gridDim.x;
+    if (tn < ntiles) fetch(tn, v);  // in flight during this tile
+    __syncthreads();                // s_x[b] holds tile tt
+    int img, y0, x0;
+    origin(tt, img, y0, x0);
+    const int y = y0 + warp;
+    if (y < H) {
+      const uint16_t *sr = s_x[b] + warp * (kM1C + 2);
+#pragma unroll 2
+      for (int sx = 0; sx < kM1C; sx += 16) {
+        if (x0 + sx >= W) break;
+        const uint16_t *p0 = sr + sx + g, *p1 = p0 + 8;
+        uint32_t a[4];
+        a[0] = pack_bf16(p0[o0], p0[o1]);
+        a[1] = pack_bf16(p1[o0], p1[o1]);
+        a[2] = t == 0 ? pack_bf16(p0[o8], 0) : 0u;
+        a[3] = t == 0 ? pack_bf16(p1[o8], 0) : 0u;
+        float d[4][4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          d[n][0] = d[n][1] = d[n][2] = d[n][3] = 0.f;
+          mma16816(d[n], a, bf[n]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // pixels g (h = 0) and g + 8
+          const int x = x0 + sx + g + 8 * h;
+          if (x >= W) continue;
+          const long long pix = (long long)y * W + x;
+#pragma unroll
+          for (int n = 0; n < 4; ++n) {
+            float v0 = d[n][2 * h], v1 = d[n][2 * h + 1];
+            const long long idx = (((long long)img * 4 + n) * HWp + pix) * 4 + t;
+            if (MODE == kHidden) {
+              v0 = fmaxf(v0 + bs[n].x, 0.f);
+              v1 = fmaxf(v1 + bs[n].y, 0.f);
+            } else {
+              const uint32_t mk = m32[idx];
+              const float2 mf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&mk));
+              if (!(mf.x > 0.f)) v0 = 0.f;
+              if (!(mf.y > 0.f)) v1 = 0.f;
+            }
+            const __nv_bfloat162 pk = __floats2bfloat162_rn(v0, v1);
+            o32[idx] = *reinterpret_cast<const uint32_t *>(&pk);
+          }
+        }
       }
     }
     if (tn < ntiles) park(v, b ^ 1);  // read two tiles on, after the next barrier
@@ -829,6 +951,29 @@ void set_attrs() {
   done = true;
 }
 
+// Persistent grid of the mma one-channel kernel: its resident blocks, at most one per tile.
+template <int MODE>
+int grid_1to32_mma(int nimg, int H, int W) {
+  static int slots = 0;
+  if (!slots) {
+    int sms = 152, per = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32_mma<MODE>, 256, 0);
+    slots = sms * (per > 0 ? per : 1);
+  }
+  const long long tiles = (long long)((W + kM1C - 1) / kM1C) * ((H + kM1R - 1) / kM1R) * nimg;
+  return (int)(tiles < slots ? tiles : slots);
+}
+
+// RBC_CONV1=0 selects the CUDA-core first layer (a sweep knob, read once).
+bool conv1_mma() {
+  static const bool on = [] {
+    const char *e = getenv("RBC_CONV1");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 // Persistent grid of the one-channel kernel: its resident blocks, at most one per tile.
 template <int MODE>
 int grid_1to32(int nimg, int H, int W) {
@@ -943,7 +1088,11 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
-  k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr,
+  if (conv1_mma())
+    k_conv_1to32_mma<kHidden><<<grid_1to32_mma<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1,
+                                                                                  nullptr, w.act[0], nimg, H, W);
+  else
+    k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr,
                                                                           w.act[0], nimg, H, W);
   bool ok_tc = true;
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
@@ -976,7 +1125,11 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   k_conv_wgrad32<C, 1><<<pg, 288, kWgSmem, s>>>(w.act[3], w.dz[1], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
-  k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3],
+  if (conv1_mma())
+    k_conv_1to32_mma<kBackData><<<grid_1to32_mma<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr,
+                                                                                      w.act[3], w.dz[0], nimg, H, W);
+  else
+    k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3],
                                                                               w.dz[0], nimg, H, W);
   // layers 4, 3, 2: dW from dz; dz below = conv^T(dz) masked
   int cur = 0;
