@@ -192,26 +192,52 @@ __global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restr
 // row, one m16n8k16 MMA per group of 8 output channels with K = the 9 taps
 // (padded to 16, zero weights): the im2col operand A[pixel][tap] is gathered
 // from the staged halo straight into the A fragments, the weights are the B
-// fragments, held in registers for the whole kernel.  A block of 8 warps
-// covers 8 rows x 128 pixels (one warp per row); persistent blocks prefetch
-// the next tile's halo into registers.  The output fragment of lane (g, t)
-// holds channels 8n + 2t, 8n + 2t + 1 of pixels g and g + 8: 4-byte pieces of
-// the pixels' 16-byte channel groups, stored 128 contiguous bytes per warp
-// and group.
-constexpr int kM1R = 8, kM1C = 128, kM1HP = (kM1R + 2) * (kM1C + 2);  // tile rows, columns, halo values
-constexpr int kM1Pre = (kM1HP + 255) / 256;                          // halo values per thread
-__device__ __forceinline__ uint32_t pack_bf16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+// fragments, held in registers for the whole kernel (the bias is the
+// accumulator's initial value).  A block of 8 warps covers 8 rows x 128
+// pixels (one warp per row); persistent blocks prefetch the next tile's halo
+// into registers.  The output fragment of lane (g, t) holds channels
+// 8n + 2t, 8n + 2t + 1 of pixels g and g + 8: 4-byte pieces of the pixels'
+// 16-byte channel groups, stored 128 contiguous bytes per warp and group
+// (rounded and clamped at zero by one conversion for the forward layer;
+// masked by a packed compare of the layer's activation for the
+// backward-data pass).  The backward-data pass stages each warp's mask row
+// (8 KB) in shared memory by 16-byte cp.async copies issued before the
+// tile's barrier, so that the copies of the blocks on an SM keep enough bytes
+// in flight without holding registers.
+// Tile counts are ints: a tile holds 1024 pixels of 64-byte activations.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+constexpr int kM1R = 8, kM1C = 128;               // tile rows, columns
+constexpr int kM1HW = kM1C + 2, kM1HP = (kM1R + 2) * kM1HW;  // halo columns, halo values
+// halo row pitch in shared memory (2-byte values): 72 words, 8 banks apart,
+// so the A-fragment gathers of a warp (three halo rows) are conflict-free
+constexpr int kM1P = 144;
+constexpr int kM1Pre = (kM1HP + 255) / 256;       // halo values per thread
+constexpr int kM1MaskWords = 4 * kM1C * 4;        // a warp's staged mask row: [group][pixel][4 words]
+template <int MODE> constexpr int smem_1to32_mma() { return MODE == kBackData ? 8 * kM1MaskWords * 4 : 0; }
+__device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+// {lo, hi} rounded to bf16 (and clamped at zero for kRelu) in one 4-byte word
+template <bool kRelu>
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
+  uint32_t r;
+  if (kRelu) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_conv_1to32_mma(const __nv_bfloat16 *__restrict__ in,
+__global__ void __launch_bounds__(256, 3) k_conv_1to32_mma(const __nv_bfloat16 *__restrict__ in,
                                                         const __nv_bfloat16 *__restrict__ wt,
                                                         const float *__restrict__ bias,
                                                         const __nv_bfloat16 *__restrict__ mask,
                                                         __nv_bfloat16 *__restrict__ out, int nimg, int H, int W) {
-  __shared__ uint16_t s_x[2][kM1HP];
+  __shared__ __align__(16) uint16_t s_x[2][(kM1R + 2) * kM1P];
+  extern __shared__ __align__(16) uint32_t s_m[];  // kBackData: the warps' mask rows
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-  const int ntx = (W + kM1C - 1) / kM1C, nty = (H + kM1R - 1) / kM1R;
-  const long long ntiles = (long long)ntx * nty * nimg, HWp = (long long)H * W;
+  const int ntx = (W + kM1C - 1) / kM1C, tpi = ntx * ((H + kM1R - 1) / kM1R), ntiles = tpi * nimg;
+  const long long HWp = (long long)H * W;
   const uint16_t *win = reinterpret_cast<const uint16_t *>(wt);
   // B fragments: B[k][co] = w[tap k][co] for k < 9, zero above
   uint32_t bf[4][2];
@@ -219,93 +245,118 @@ __global__ void __launch_bounds__(256) k_conv_1to32_mma(const __nv_bfloat16 *__r
 #pragma unroll
   for (int n = 0; n < 4; ++n) {
     const int co = 8 * n + g;
-    bf[n][0] = pack_bf16(win[(2 * t) * 32 + co], win[(2 * t + 1) * 32 + co]);
-    bf[n][1] = t == 0 ? pack_bf16(win[8 * 32 + co], 0) : 0u;
+    bf[n][0] = pack_u16(win[(2 * t) * 32 + co], win[(2 * t + 1) * 32 + co]);
+    bf[n][1] = t == 0 ? pack_u16(win[8 * 32 + co], 0) : 0u;
     bs[n] = MODE == kHidden ? make_float2(bias[8 * n + 2 * t], bias[8 * n + 2 * t + 1]) : make_float2(0.f, 0.f);
   }
-  // halo taps of this lane: k0 = 2t, k1 = 2t + 1 (and tap 8 for t = 0)
-  const int o0 = ((2 * t) / 3) * (kM1C + 2) + (2 * t) % 3, o1 = ((2 * t + 1) / 3) * (kM1C + 2) + (2 * t + 1) % 3;
-  const int o8 = 2 * (kM1C + 2) + 2;
-  auto origin = [&](long long tt, int &img, int &y0, int &x0) {
-    img = (int)(tt / ((long long)ntx * nty));
-    const int rem = (int)(tt % ((long long)ntx * nty));
-    y0 = (rem / ntx) * kM1R;
-    x0 = (rem % ntx) * kM1C;
+  // halo offsets of this lane's taps: 2t, 2t + 1 (and 8 for t = 0), tap = 3 dy + dx
+  const int o0 = ((2 * t) / 3) * kM1P + (2 * t) % 3, o1 = ((2 * t + 1) / 3) * kM1P + (2 * t + 1) % 3;
+  constexpr int o8 = 2 * kM1P + 2;
+  auto origin = [&](int tt, int &img, int &y0, int &x0) {
+    img = tt / tpi;
+    const int rem = tt - img * tpi, ty = rem / ntx;
+    y0 = ty * kM1R;
+    x0 = (rem - ty * ntx) * kM1C;
   };
   const uint16_t *xin = reinterpret_cast<const uint16_t *>(in);
-  auto fetch = [&](long long tt, uint16_t *v) {
-    int img, y0, x0;
-    origin(tt, img, y0, x0);
+  auto fetch = [&](int img, int y0, int x0, uint16_t *v) {
+    const uint16_t *src = xin + (long long)img * HWp;
 #pragma unroll
     for (int k = 0; k < kM1Pre; ++k) {
-      const int i = tid + 256 * k;
-      const int yy = y0 + i / (kM1C + 2) - 1, xx = x0 + i % (kM1C + 2) - 1;
-      v[k] = (i < kM1HP && yy >= 0 && yy < H && xx >= 0 && xx < W) ? xin[(long long)img * HWp + (long long)yy * W + xx]
-                                                                      : (uint16_t)0;
+      const int i = tid + 256 * k, r = i / kM1HW;
+      const int yy = y0 + r - 1, xx = x0 + (i - r * kM1HW) - 1;
+      v[k] = (i < kM1HP && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W) ? src[(long long)yy * W + xx]
+                                                                                      : (uint16_t)0;
     }
   };
   auto park = [&](const uint16_t *v, int b) {
 #pragma unroll
-    for (int k = 0; k < kM1Pre; ++k)
-      if (tid + 256 * k < kM1HP) s_x[b][tid + 256 * k] = v[k];
+    for (int k = 0; k < kM1Pre; ++k) {
+      const int i = tid + 256 * k, r = i / kM1HW;
+      if (i < kM1HP) s_x[b][r * kM1P + (i - r * kM1HW)] = v[k];
+    }
   };
   uint16_t v[kM1Pre];
-  if ((long long)blockIdx.x < ntiles) {
-    fetch(blockIdx.x, v);
+  int img = 0, y0 = 0, x0 = 0;
+  if ((int)blockIdx.x < ntiles) {
+    origin(blockIdx.x, img, y0, x0);
+    fetch(img, y0, x0, v);
     park(v, 0);
   }
   uint32_t *o32 = reinterpret_cast<uint32_t *>(out);
-  const uint32_t *m32 = reinterpret_cast<const uint32_t *>(mask);
   int b = 0;
-  for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x, b ^= 1) {
-    const long long tn = tt + gridDim.x;
-    if (tn < ntiles) fetch(tn, v);  // in flight during this tile
-    __syncthreads();                // s_x[b] holds tile tt
-    int img, y0, x0;
-    origin(tt, img, y0, x0);
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x, b ^= 1) {
+    const int tn = tt + gridDim.x;
+    int img_n = 0, y0_n = 0, x0_n = 0;
+    if (tn < ntiles) {  // in flight during this tile
+      origin(tn, img_n, y0_n, x0_n);
+      fetch(img_n, y0_n, x0_n, v);
+    }
     const int y = y0 + warp;
+    const int nx = min(kM1C, W - x0);  // columns of the tile inside the image
+    uint32_t *sm = s_m + warp * kM1MaskWords;
+    if (MODE == kBackData && y < H) {
+      __syncwarp();  // the warp's reads of its previous mask row are done
+      const uint4 *m16 = reinterpret_cast<const uint4 *>(mask) + ((long long)img * 4 * HWp + (long long)y * W + x0);
+#pragma unroll
+      for (int k = 0; k < 4 * kM1C / 32; ++k) {
+        const int c = lane + 32 * k, n = c / kM1C, px = c % kM1C;
+        if (px < nx) cp_async16((uint32_t)__cvta_generic_to_shared(sm + 4 * c), m16 + n * HWp + px, true);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    __syncthreads();  // s_x[b] holds tile tt
     if (y < H) {
-      const uint16_t *sr = s_x[b] + warp * (kM1C + 2);
-#pragma unroll 2
-      for (int sx = 0; sx < kM1C; sx += 16) {
-        if (x0 + sx >= W) break;
-        const uint16_t *p0 = sr + sx + g, *p1 = p0 + 8;
+      if (MODE == kBackData) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+      }
+      const uint16_t *sr = s_x[b] + warp * kM1P + g;
+      // 4-byte piece t of pixel (y, x0 + g) in each channel group
+      uint32_t *orow[4];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) orow[n] = o32 + (((long long)img * 4 + n) * HWp + (long long)y * W + x0 + g) * 4 + t;
+#pragma unroll
+      for (int sg = 0; sg < kM1C / 16; ++sg) {
+        if (16 * sg >= nx) break;
+        const uint16_t *p0 = sr + 16 * sg, *p1 = p0 + 8;
         uint32_t a[4];
-        a[0] = pack_bf16(p0[o0], p0[o1]);
-        a[1] = pack_bf16(p1[o0], p1[o1]);
-        a[2] = t == 0 ? pack_bf16(p0[o8], 0) : 0u;
-        a[3] = t == 0 ? pack_bf16(p1[o8], 0) : 0u;
+        a[0] = pack_u16(p0[o0], p0[o1]);
+        a[1] = pack_u16(p1[o0], p1[o1]);
+        a[2] = t == 0 ? (uint32_t)p0[o8] : 0u;
+        a[3] = t == 0 ? (uint32_t)p1[o8] : 0u;
         float d[4][4];
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
-          d[n][0] = d[n][1] = d[n][2] = d[n][3] = 0.f;
+          d[n][0] = d[n][2] = bs[n].x;
+          d[n][1] = d[n][3] = bs[n].y;
           mma16816(d[n], a, bf[n]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // pixels g (h = 0) and g + 8
-          const int x = x0 + sx + g + 8 * h;
-          if (x >= W) continue;
-          const long long pix = (long long)y * W + x;
+          const int px = 16 * sg + 8 * h;
+          if (px + g >= nx) continue;
 #pragma unroll
           for (int n = 0; n < 4; ++n) {
-            float v0 = d[n][2 * h], v1 = d[n][2 * h + 1];
-            const long long idx = (((long long)img * 4 + n) * HWp + pix) * 4 + t;
+            uint32_t r;
             if (MODE == kHidden) {
-              v0 = fmaxf(v0 + bs[n].x, 0.f);
-              v1 = fmaxf(v1 + bs[n].y, 0.f);
+              r = cvt_bf16x2<true>(d[n][2 * h], d[n][2 * h + 1]);
             } else {
-              const uint32_t mk = m32[idx];
-              const float2 mf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&mk));
-              if (!(mf.x > 0.f)) v0 = 0.f;
-              if (!(mf.y > 0.f)) v1 = 0.f;
+              __nv_bfloat162 m2;
+              *reinterpret_cast<uint32_t *>(&m2) = sm[(n * kM1C + px + g) * 4 + t];
+              r = cvt_bf16x2<false>(d[n][2 * h], d[n][2 * h + 1]) & __hgt2_mask(m2, __float2bfloat162_rn(0.f));
             }
-            const __nv_bfloat162 pk = __floats2bfloat162_rn(v0, v1);
-            o32[idx] = *reinterpret_cast<const uint32_t *>(&pk);
+            orow[n][px * 4] = r;
           }
         }
       }
     }
-    if (tn < ntiles) park(v, b ^ 1);  // read two tiles on, after the next barrier
+    if (tn < ntiles) {  // read two tiles on, after the next barrier
+      park(v, b ^ 1);
+      img = img_n;
+      y0 = y0_n;
+      x0 = x0_n;
+    }
   }
 }
 
@@ -393,9 +444,6 @@ constexpr uint32_t tc_idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool ok) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t ta, float *v) {
   uint32_t r[32];
@@ -958,7 +1006,9 @@ int grid_1to32_mma(int nimg, int H, int W) {
   if (!slots) {
     int sms = 152, per = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32_mma<MODE>, 256, 0);
+    if (smem_1to32_mma<MODE>() > 48 * 1024)
+      cudaFuncSetAttribute(k_conv_1to32_mma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_1to32_mma<MODE>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32_mma<MODE>, 256, smem_1to32_mma<MODE>());
     slots = sms * (per > 0 ? per : 1);
   }
   const long long tiles = (long long)((W + kM1C - 1) / kM1C) * ((H + kM1R - 1) / kM1R) * nimg;
@@ -1089,7 +1139,7 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
   if (conv1_mma())
-    k_conv_1to32_mma<kHidden><<<grid_1to32_mma<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1,
+    k_conv_1to32_mma<kHidden><<<grid_1to32_mma<kHidden>(nimg, H, W), 256, smem_1to32_mma<kHidden>(), s>>>(w.x0, w.wf + kW1, params_dev + kB1,
                                                                                   nullptr, w.act[0], nimg, H, W);
   else
     k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr,
@@ -1126,7 +1176,7 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
   if (conv1_mma())
-    k_conv_1to32_mma<kBackData><<<grid_1to32_mma<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr,
+    k_conv_1to32_mma<kBackData><<<grid_1to32_mma<kBackData>(nimg, H, W), 256, smem_1to32_mma<kBackData>(), s>>>(w.dy1, w.wb + kW5, nullptr,
                                                                                       w.act[3], w.dz[0], nimg, H, W);
   else
     k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3],
