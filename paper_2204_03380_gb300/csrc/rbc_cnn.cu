@@ -15,7 +15,8 @@
 // swapped, its epilogue applying the ReLU mask of the layer below) and the
 // 32 -> 1 last layer run as implicit GEMMs on the 5th-generation tensor cores
 // (tcgen05.mma, operands in shared memory, fp32 accumulators in tensor
-// memory).  The one-channel first layer runs on the CUDA cores.  Weight gradients are per-tap
+// memory).  The one-channel first layer runs on the warp-level tensor cores
+// (mma.sync m16n8k16, the 9 taps padded to K = 16).  Weight gradients are per-tap
 // GEMMs over the pixels on the warp-level tensor cores (mma.sync m16n8k16),
 // reduced by persistent blocks and added to the fp32 gradient once per block.
 #include <cuda.h>
@@ -51,145 +52,10 @@ __device__ __forceinline__ void mma16816(float *c, const uint32_t *a, const uint
 
 enum { kHidden = 0, kLast = 1, kBackData = 2 };
 
-// The first layer (and the last layer's backward-data pass) has one input
-// channel, below the K = 16 of a tensor-core MMA, and is bound by its
-// 64-byte-per-pixel output, so it runs on the CUDA cores: a block of 256
-// threads covers (8 x PPT) x 32 pixels, PPT pixels per thread (rows ty,
-// ty + 8, ...), the halo and the fp32 weights in shared memory; each weight
-// float4 is read once for the thread's pixels and applied with packed fp32x2
-// FMAs (each lane correctly rounded, the same sequence per channel as scalar
-// FMAs).
-// 1 -> 32 channels (first layer forward; last layer's backward-data pass):
+// The one-channel first layer (1 -> 32 channels, and the last layer's
+// backward-data pass) on the warp-level tensor cores:
 //   wt [tap][32] (bf16);  MODE kHidden: relu(conv + bias);  kBackData: conv * (mask > 0)
-// PPT pixels per thread (rows ty, ty + 8, ...): 2 for the forward layer, 1
-// for the backward-data pass, whose mask loads want the occupancy.
-template <int MODE> constexpr int ppt_1to32() { return MODE == kHidden ? 2 : 1; }
-// Persistent blocks walk the tiles (x fastest, then rows, then images); the
-// weights are converted once per block, and the next tile's input halo is
-// loaded into registers while the current tile is computed and stored, then
-// parked in the other half of a double-buffered shared-memory halo.
-constexpr int kHalo1 = 3;  // halo values per thread: ceil(18 x 34 / 256) for P = 2
-template <int MODE>
-__global__ void __launch_bounds__(256) k_conv_1to32(const __nv_bfloat16 *__restrict__ in,
-                                                    const __nv_bfloat16 *__restrict__ wt,
-                                                    const float *__restrict__ bias,
-                                                    const __nv_bfloat16 *__restrict__ mask,
-                                                    __nv_bfloat16 *__restrict__ out, int nimg, int H, int W) {
-  constexpr int P = ppt_1to32<MODE>(), TH1 = 8 * P, HP = (TH1 + 2) * (TW + 2);
-  static_assert(HP <= kHalo1 * 256, "the halo must fit in kHalo1 values per thread");
-  __shared__ __align__(16) float s_w[9 * 32];
-  __shared__ __align__(16) float s_b[32];
-  __shared__ float s_in[2][HP];
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int ntx = (W + TW - 1) / TW, nty = (H + TH1 - 1) / TH1;
-  const long long ntiles = (long long)ntx * nty * nimg, HWp = (long long)H * W;
-  for (int i = tid; i < 9 * 32; i += 256) s_w[i] = __bfloat162float(wt[i]);
-  if (MODE == kHidden && tid < 32) s_b[tid] = bias[tid];
-  auto origin = [&](long long t, int &img, int &y0, int &x0) {
-    img = (int)(t / ((long long)ntx * nty));
-    const int rem = (int)(t % ((long long)ntx * nty));
-    y0 = (rem / ntx) * TH1;
-    x0 = (rem % ntx) * TW;
-  };
-  // this thread's share of a tile's halo (zero outside the image)
-  auto fetch = [&](long long t, float *v) {
-    int img, y0, x0;
-    origin(t, img, y0, x0);
-#pragma unroll
-    for (int k = 0; k < kHalo1; ++k) {
-      const int i = tid + 256 * k;
-      const int yy = y0 + i / (TW + 2) - 1, xx = x0 + i % (TW + 2) - 1;
-      v[k] = (i < HP && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                 ? __bfloat162float(in[(long long)img * HWp + (long long)yy * W + xx])
-                 : 0.f;
-    }
-  };
-  auto park = [&](const float *v, int b) {
-#pragma unroll
-    for (int k = 0; k < kHalo1; ++k)
-      if (tid + 256 * k < HP) s_in[b][tid + 256 * k] = v[k];
-  };
-  float v[kHalo1];
-  if ((long long)blockIdx.x < ntiles) {
-    fetch(blockIdx.x, v);
-    park(v, 0);
-  }
-  int b = 0;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, b ^= 1) {
-    const long long tn = t + gridDim.x;
-    if (tn < ntiles) fetch(tn, v);  // in flight during this tile
-    __syncthreads();                // s_in[b] holds tile t
-    int img, y0, x0;
-    origin(t, img, y0, x0);
-    const int xx = x0 + tx;
-    const float *sb = s_in[b];
-    float2 acc[P][16];  // [pixel][channel pair]
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-#pragma unroll
-      for (int c = 0; c < 16; ++c) acc[p][c] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int tp = 0; tp < 9; ++tp) {
-      float2 a[P];
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float x = sb[(ty + 8 * p + tp / 3) * (TW + 2) + tx + tp % 3];
-        a[p] = make_float2(x, x);
-      }
-      const float4 *w4 = reinterpret_cast<const float4 *>(s_w + tp * 32);
-#pragma unroll
-      for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 w = w4[c4];
-        const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          acc[p][2 * c4] = __ffma2_rn(a[p], wl, acc[p][2 * c4]);
-          acc[p][2 * c4 + 1] = __ffma2_rn(a[p], wh, acc[p][2 * c4 + 1]);
-        }
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const int yy = y0 + ty + 8 * p;
-      if (yy >= H || xx >= W) continue;
-      const long long pix = (long long)yy * W + xx;
-      float o[32];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        o[2 * c] = acc[p][c].x;
-        o[2 * c + 1] = acc[p][c].y;
-      }
-      if (MODE == kHidden) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) o[c] = fmaxf(o[c] + s_b[c], 0.f);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 m4 = reinterpret_cast<const uint4 *>(mask)[((long long)img * 4 + q) * HWp + pix];
-          const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&m4);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 mf = __bfloat1622float2(m2[e]);
-            if (!(mf.x > 0.f)) o[q * 8 + 2 * e] = 0.f;
-            if (!(mf.y > 0.f)) o[q * 8 + 2 * e + 1] = 0.f;
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint4 pk;
-        __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(o[q * 8 + 2 * e], o[q * 8 + 2 * e + 1]);
-        reinterpret_cast<uint4 *>(out)[((long long)img * 4 + q) * HWp + pix] = pk;
-      }
-    }
-    if (tn < ntiles) park(v, b ^ 1);  // read two tiles on, after the next barrier
-  }
-}
-
-// The same 1 -> 32 layer on the warp-level tensor cores: per 16 pixels of a
-// row, one m16n8k16 MMA per group of 8 output channels with K = the 9 taps
+// Per 16 pixels of a row, one m16n8k16 MMA per group of 8 output channels with K = the 9 taps
 // (padded to 16, zero weights): the im2col operand A[pixel][tap] is gathered
 // from the staged halo straight into the A fragments, the weights are the B
 // fragments, held in registers for the whole kernel (the bias is the
@@ -216,7 +82,7 @@ constexpr int kM1HW = kM1C + 2, kM1HP = (kM1R + 2) * kM1HW;  // halo columns, ha
 constexpr int kM1P = 144;
 constexpr int kM1Pre = (kM1HP + 255) / 256;       // halo values per thread
 constexpr int kM1MaskWords = 4 * kM1C * 4;        // a warp's staged mask row: [group][pixel][4 words]
-template <int MODE> constexpr int smem_1to32_mma() { return MODE == kBackData ? 8 * kM1MaskWords * 4 : 0; }
+template <int MODE> constexpr int smem_1to32() { return MODE == kBackData ? 8 * kM1MaskWords * 4 : 0; }
 __device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 // {lo, hi} rounded to bf16 (and clamped at zero for kRelu) in one 4-byte word
 template <bool kRelu>
@@ -228,7 +94,7 @@ __device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 3) k_conv_1to32_mma(const __nv_bfloat16 *__restrict__ in,
+__global__ void __launch_bounds__(256, 3) k_conv_1to32(const __nv_bfloat16 *__restrict__ in,
                                                         const __nv_bfloat16 *__restrict__ wt,
                                                         const float *__restrict__ bias,
                                                         const __nv_bfloat16 *__restrict__ mask,
@@ -999,31 +865,6 @@ void set_attrs() {
   done = true;
 }
 
-// Persistent grid of the mma one-channel kernel: its resident blocks, at most one per tile.
-template <int MODE>
-int grid_1to32_mma(int nimg, int H, int W) {
-  static int slots = 0;
-  if (!slots) {
-    int sms = 152, per = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-    if (smem_1to32_mma<MODE>() > 48 * 1024)
-      cudaFuncSetAttribute(k_conv_1to32_mma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_1to32_mma<MODE>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32_mma<MODE>, 256, smem_1to32_mma<MODE>());
-    slots = sms * (per > 0 ? per : 1);
-  }
-  const long long tiles = (long long)((W + kM1C - 1) / kM1C) * ((H + kM1R - 1) / kM1R) * nimg;
-  return (int)(tiles < slots ? tiles : slots);
-}
-
-// RBC_CONV1=0 selects the CUDA-core first layer (a sweep knob, read once).
-bool conv1_mma() {
-  static const bool on = [] {
-    const char *e = getenv("RBC_CONV1");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
-
 // Persistent grid of the one-channel kernel: its resident blocks, at most one per tile.
 template <int MODE>
 int grid_1to32(int nimg, int H, int W) {
@@ -1031,13 +872,15 @@ int grid_1to32(int nimg, int H, int W) {
   if (!slots) {
     int sms = 152, per = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32<MODE>, 256, 0);
+    if (smem_1to32<MODE>() > 48 * 1024)
+      cudaFuncSetAttribute(k_conv_1to32<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_1to32<MODE>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_1to32<MODE>, 256, smem_1to32<MODE>());
     slots = sms * (per > 0 ? per : 1);
   }
-  const int th1 = 8 * ppt_1to32<MODE>();
-  const long long tiles = (long long)((W + TW - 1) / TW) * ((H + th1 - 1) / th1) * nimg;
+  const long long tiles = (long long)((W + kM1C - 1) / kM1C) * ((H + kM1R - 1) / kM1R) * nimg;
   return (int)(tiles < slots ? tiles : slots);
 }
+
 
 int grid_of(long long n) {
   long long b = (n + 255) / 256;
@@ -1138,12 +981,8 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float
   k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
-  if (conv1_mma())
-    k_conv_1to32_mma<kHidden><<<grid_1to32_mma<kHidden>(nimg, H, W), 256, smem_1to32_mma<kHidden>(), s>>>(w.x0, w.wf + kW1, params_dev + kB1,
-                                                                                  nullptr, w.act[0], nimg, H, W);
-  else
-    k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, 0, s>>>(w.x0, w.wf + kW1, params_dev + kB1, nullptr,
-                                                                          w.act[0], nimg, H, W);
+  k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, smem_1to32<kHidden>(), s>>>(
+      w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], nimg, H, W);
   bool ok_tc = true;
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
@@ -1175,12 +1014,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   k_conv_wgrad32<C, 1><<<pg, 288, kWgSmem, s>>>(w.act[3], w.dz[1], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
-  if (conv1_mma())
-    k_conv_1to32_mma<kBackData><<<grid_1to32_mma<kBackData>(nimg, H, W), 256, smem_1to32_mma<kBackData>(), s>>>(w.dy1, w.wb + kW5, nullptr,
-                                                                                      w.act[3], w.dz[0], nimg, H, W);
-  else
-    k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, 0, s>>>(w.dy1, w.wb + kW5, nullptr, w.act[3],
-                                                                              w.dz[0], nimg, H, W);
+  k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, smem_1to32<kBackData>(), s>>>(
+      w.dy1, w.wb + kW5, nullptr, w.act[3], w.dz[0], nimg, H, W);
   // layers 4, 3, 2: dW from dz; dz below = conv^T(dz) masked
   int cur = 0;
   bool ok_tc = true;
