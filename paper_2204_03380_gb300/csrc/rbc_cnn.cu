@@ -637,9 +637,8 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
 
 // Weight and bias gradients of a convolution layer:
 //   dW[tap][co][ci] = sum_p dz[co][p] x[ci][p + tap],  db[co] = sum_p dz[co][p],
-// with x and dz 32-channel planar; the one-channel ends of the network pass
-// their single channel as channel 0 of a 32-channel operand (k_expand_c0) and
-// keep the CI x CO corner of the result.
+// with x and dz 32-channel planar (the 32 -> 32 layers; the one-channel end
+// layers have their own kernel, k_conv_wgrad1).
 // Per tap a GEMM with M = 32 output channels, N = 32 input channels and K =
 // the pixels, on mma.sync m16n8k16 (bf16 in, fp32 accumulate).  Persistent
 // blocks of nine warps (one per tap) walk 8 x 32-pixel tiles; a tile's input
@@ -780,19 +779,174 @@ __global__ void __launch_bounds__(288) k_conv_wgrad32(const __nv_bfloat16 *__res
   }
 }
 
-// One channel [img][pixel] -> 32-channel planar bf16 with the value in
-// channel 0 and zeros elsewhere (the operand form of k_conv_wgrad32).
-template <typename T>
-__global__ void k_expand_c0(const T *__restrict__ in, __nv_bfloat16 *__restrict__ out, long long HWp, int nimg) {
-  uint4 *o = reinterpret_cast<uint4 *>(out);
-  const long long n = HWp * nimg;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long img = i / HWp, p = i % HWp;
-    const __nv_bfloat16 v = __float2bfloat16((float)in[i]);
-    o[(img * 4 + 0) * HWp + p] = make_uint4((uint32_t)__bfloat16_as_ushort(v), 0u, 0u, 0u);
-    o[(img * 4 + 1) * HWp + p] = make_uint4(0u, 0u, 0u, 0u);
-    o[(img * 4 + 2) * HWp + p] = make_uint4(0u, 0u, 0u, 0u);
-    o[(img * 4 + 3) * HWp + p] = make_uint4(0u, 0u, 0u, 0u);
+// Weight and bias gradients of the two one-channel end layers, without
+// widening the one channel to 32:
+//   first layer:  dW1[tap][co] = sum_p dz1[co][p] x0[p + off(tap)],   db1[co] = sum_p dz1[co][p]
+//   last layer:   dW5[tap][ci] = sum_q dy[q - off(tap)] x4[ci][q],    db5 = sum_q dy[q]
+// (the last layer's sum re-indexed by q = p + off(tap); the zero padding
+// makes both sums run over the image).  Each is a GEMM over the pixels,
+// D[tap][c] = sum_p A[tap][p] B[p][c], on mma.sync m16n8k16: M = the 9 taps
+// (row 9 all ones for db1, rows 10-15 zero), N = the 32 channels, K = 16
+// pixels of a row.  A is the im2col of the one-channel image u (x0, or dy
+// rounded to bf16), gathered from its staged halo straight into the A
+// fragments; B is the 32-channel operand v (dz1, or x4), staged as it lies
+// in global memory (channel-group planar) by 16-byte cp.async copies and read
+// with ldmatrix.trans.  db5 is the centre tap's row times a column of ones.
+// Persistent blocks of 4 warps walk tiles of 4 rows x 128 pixels (one warp
+// per row), double-buffered: tile k + 1's copies and halo loads are in flight
+// while tile k is multiplied.  A block sums its warps' partial results in
+// shared memory and adds them to the fp32 gradient once.
+constexpr int kW1R = 4, kW1C = 128;                       // tile rows, columns
+constexpr int kW1HW = kW1C + 2, kW1HP = (kW1R + 2) * kW1HW;  // halo columns, halo values
+constexpr int kW1P = 144;                                 // halo row pitch (conflict-free gathers)
+constexpr int kW1Pre = (kW1HP + 127) / 128;               // halo values per thread
+constexpr int kW1V = 4 * kW1R * kW1C * 8;                 // bf16 of a staged v tile: [group][row][px][8]
+constexpr int kW1Red = 9 * 32 + 32;                       // dW [tap][32], then db
+constexpr size_t kW1Smem = sizeof(__nv_bfloat16) * 2 * kW1V + sizeof(uint16_t) * 2 * (kW1R + 2) * kW1P +
+                           sizeof(float) * kW1Red;
+
+__device__ __forceinline__ uint16_t to_bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16(v)); }
+__device__ __forceinline__ uint16_t to_bf16_bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+
+template <bool kFirst, typename TU>
+__global__ void __launch_bounds__(128) k_conv_wgrad1(const TU *__restrict__ u, const __nv_bfloat16 *__restrict__ v,
+                                                     float *__restrict__ dw, float *__restrict__ db, int nimg, int H,
+                                                     int W) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  __nv_bfloat16 *s_v = reinterpret_cast<__nv_bfloat16 *>(s_raw);                  // [2][kW1V]
+  uint16_t *s_u = reinterpret_cast<uint16_t *>(s_v + 2 * kW1V);                     // [2][(kW1R + 2) * kW1P]
+  float *s_red = reinterpret_cast<float *>(s_u + 2 * (kW1R + 2) * kW1P);            // [kW1Red]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+  const int lj = lane >> 3, lr = lane & 7;  // ldmatrix: matrix and row of this lane's address
+  const int ntx = (W + kW1C - 1) / kW1C, tpi = ntx * ((H + kW1R - 1) / kW1R), ntiles = tpi * nimg;
+  const long long HWp = (long long)H * W;
+  for (int i = tid; i < kW1Red; i += 128) s_red[i] = 0.f;
+  // halo offsets of this lane's A rows: tap g, and tap 8 (g = 0); the last
+  // layer reads u at q - off(tap), the mirrored tap
+  const int tg = kFirst ? g : 8 - g;
+  const int oT = (tg / 3) * kW1P + tg % 3, o8 = kFirst ? 2 * kW1P + 2 : 0;
+  const uint32_t ones = 0x3F803F80u;  // bf16 1.0 pair
+  auto origin = [&](int tt, int &img, int &y0, int &x0) {
+    img = tt / tpi;
+    const int rem = tt - img * tpi, ty = rem / ntx;
+    y0 = ty * kW1R;
+    x0 = (rem - ty * ntx) * kW1C;
+  };
+  auto stage_v = [&](int img, int y0, int x0, int b) {
+    __nv_bfloat16 *dst = s_v + b * kW1V;
+#pragma unroll 4
+    for (int i = tid; i < 4 * kW1R * kW1C; i += 128) {
+      const int n = i / (kW1R * kW1C), r = (i / kW1C) % kW1R, px = i % kW1C;
+      const bool ok = y0 + r < H && x0 + px < W;
+      const __nv_bfloat16 *src = ok ? v + (((long long)img * 4 + n) * HWp + (long long)(y0 + r) * W + x0 + px) * 8 : v;
+      cp_async16((uint32_t)__cvta_generic_to_shared(dst + (size_t)i * 8), src, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto fetch_u = [&](int img, int y0, int x0, uint16_t *h) {
+    const TU *src = u + (long long)img * HWp;
+#pragma unroll
+    for (int k = 0; k < kW1Pre; ++k) {
+      const int i = tid + 128 * k, r = i / kW1HW;
+      const int yy = y0 + r - 1, xx = x0 + (i - r * kW1HW) - 1;
+      h[k] = (i < kW1HP && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W)
+                 ? to_bf16_bits(src[(long long)yy * W + xx])
+                 : (uint16_t)0;
+    }
+  };
+  auto park_u = [&](const uint16_t *h, int b) {
+#pragma unroll
+    for (int k = 0; k < kW1Pre; ++k) {
+      const int i = tid + 128 * k, r = i / kW1HW;
+      if (i < kW1HP) s_u[b * (kW1R + 2) * kW1P + r * kW1P + (i - r * kW1HW)] = h[k];
+    }
+  };
+  float acc[4][4], accb[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    accb[n] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[n][r] = 0.f;
+  }
+  uint16_t h[kW1Pre];
+  int img = 0, y0 = 0, x0 = 0;
+  if ((int)blockIdx.x < ntiles) {
+    origin(blockIdx.x, img, y0, x0);
+    stage_v(img, y0, x0, 0);
+    fetch_u(img, y0, x0, h);
+    park_u(h, 0);
+  }
+  int b = 0;
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x, b ^= 1) {
+    const int tn = tt + gridDim.x;
+    int img_n = 0, y0_n = 0, x0_n = 0;
+    if (tn < ntiles) {
+      origin(tn, img_n, y0_n, x0_n);
+      stage_v(img_n, y0_n, x0_n, b ^ 1);
+      fetch_u(img_n, y0_n, x0_n, h);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();  // tile tt's v and u are staged
+    if (y0 + warp < H) {
+      const uint16_t *ur = s_u + b * (kW1R + 2) * kW1P + warp * kW1P + 2 * t;
+      const __nv_bfloat16 *vr = s_v + b * kW1V + warp * kW1C * 8;
+      const int nx = min(kW1C, W - x0);
+#pragma unroll 2
+      for (int c0 = 0; c0 < nx; c0 += 16) {
+        uint32_t a[4];
+        a[0] = pack_u16(ur[c0 + oT], ur[c0 + oT + 1]);
+        a[2] = pack_u16(ur[c0 + oT + 8], ur[c0 + oT + 9]);
+        const uint32_t r8a = pack_u16(ur[c0 + o8], ur[c0 + o8 + 1]), r8b = pack_u16(ur[c0 + o8 + 8], ur[c0 + o8 + 9]);
+        const uint32_t rone = kFirst && g == 1 ? ones : 0u;
+        a[1] = g == 0 ? r8a : rone;
+        a[3] = g == 0 ? r8b : rone;
+        uint32_t bf[4][2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // channel groups 2q, 2q + 1; pixels 0-7 | 8-15
+          uint32_t r4[4];
+          ldsm_x4_t(r4, vr + ((2 * q + (lj >> 1)) * kW1R * kW1C + c0 + (lj & 1) * 8 + lr) * 8);
+          bf[2 * q][0] = r4[0];
+          bf[2 * q][1] = r4[1];
+          bf[2 * q + 1][0] = r4[2];
+          bf[2 * q + 1][1] = r4[3];
+        }
+#pragma unroll
+        for (int n = 0; n < 4; ++n) mma16816(acc[n], a, bf[n]);
+        if (!kFirst) {
+          const uint32_t bo[2] = {ones, ones};
+          mma16816(accb, a, bo);
+        }
+      }
+    }
+    if (tn < ntiles) {
+      park_u(h, b ^ 1);
+      img = img_n;
+      y0 = y0_n;
+      x0 = x0_n;
+    }
+    __syncthreads();  // buffer b is refilled by the copies two tiles on
+  }
+  // D rows: tap g (acc[n][0..1]) and row g + 8 (acc[n][2..3]): tap 8 for
+  // g = 0, the ones row (db1) for g = 1; columns 8n + 2t, 8n + 2t + 1
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int c = 8 * n + 2 * t;
+    atomicAdd(&s_red[g * 32 + c], acc[n][0]);
+    atomicAdd(&s_red[g * 32 + c + 1], acc[n][1]);
+    if (g == 0 || (kFirst && g == 1)) {
+      atomicAdd(&s_red[(8 + g) * 32 + c], acc[n][2]);
+      atomicAdd(&s_red[(8 + g) * 32 + c + 1], acc[n][3]);
+    }
+  }
+  if (!kFirst && g == 4 && t == 0) atomicAdd(&s_red[9 * 32], accb[0]);  // centre tap x ones: db5
+  __syncthreads();
+  for (int i = tid; i < 9 * 32; i += 128) atomicAdd(dw + i, s_red[i]);
+  if (kFirst) {
+    if (tid < 32) atomicAdd(db + tid, s_red[9 * 32 + tid]);
+  } else if (tid == 0) {
+    atomicAdd(db, s_red[9 * 32]);
   }
 }
 
@@ -860,9 +1014,23 @@ void set_attrs() {
   cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
-  cudaFuncSetAttribute(k_conv_wgrad32<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
-  cudaFuncSetAttribute(k_conv_wgrad32<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+  cudaFuncSetAttribute(k_conv_wgrad1<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
+  cudaFuncSetAttribute(k_conv_wgrad1<true, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   done = true;
+}
+
+// Persistent grid of the one-channel weight-gradient kernel (attributes set by set_attrs).
+template <bool kFirst, typename TU>
+int grid_wgrad1(int nimg, int H, int W) {
+  static int slots = 0;
+  if (!slots) {
+    int sms = 152, per = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_wgrad1<kFirst, TU>, 128, kW1Smem);
+    slots = sms * (per > 0 ? per : 1);
+  }
+  const long long tiles = (long long)((W + kW1C - 1) / kW1C) * ((H + kW1R - 1) / kW1R) * nimg;
+  return (int)(tiles < slots ? tiles : slots);
 }
 
 // Persistent grid of the one-channel kernel: its resident blocks, at most one per tile.
@@ -1010,8 +1178,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const int pg = 2 * sms;
   // layer 5: dW5, db5 from dy; dz4 = conv^T(dy) masked by act4 > 0
-  k_expand_c0<float><<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dz[1], (long long)H * W, nimg);
-  k_conv_wgrad32<C, 1><<<pg, 288, kWgSmem, s>>>(w.act[3], w.dz[1], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
+  k_conv_wgrad1<false, float><<<grid_wgrad1<false, float>(nimg, H, W), 128, kW1Smem, s>>>(
+      dy_dev, w.act[3], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
   k_to_bf16<<<grid_of(npx), 256, 0, s>>>(dy_dev, w.dy1, npx);
   set_attrs();
   k_conv_1to32<kBackData><<<grid_1to32<kBackData>(nimg, H, W), 256, smem_1to32<kBackData>(), s>>>(
@@ -1028,10 +1196,10 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
     cur = 1 - cur;
   }
   // layer 1
-  k_expand_c0<__nv_bfloat16><<<grid_of(npx), 256, 0, s>>>(w.x0, w.dz[1 - cur], (long long)H * W, nimg);
-  k_conv_wgrad32<1, C><<<pg, 288, kWgSmem, s>>>(w.dz[1 - cur], w.dz[cur], grad_dev + kW1, grad_dev + kB1, nimg, H, W);
+  k_conv_wgrad1<true, __nv_bfloat16><<<grid_wgrad1<true, __nv_bfloat16>(nimg, H, W), 128, kW1Smem, s>>>(
+      w.x0, w.dz[cur], grad_dev + kW1, grad_dev + kB1, nimg, H, W);
   if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_backward: launch failed");
-  rbc::add_launches(12);
+  rbc::add_launches(10);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
   return RBC_OK;

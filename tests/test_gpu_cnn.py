@@ -44,6 +44,16 @@ def test_cnn_forward_and_gradient_match_oracle(shape):
     assert rel(Y.cpu().numpy(), y_o) <= 1e-2
     assert float(loss) == pytest.approx(cnn.mse(y_o, t), rel=2e-2)
     assert rel(G.cpu().numpy(), g_o) <= 3e-2, rel(G.cpu().numpy(), g_o)
+    # every layer's block on its own (the one-channel end layers have their
+    # own weight-gradient kernel, and their blocks are small in the whole)
+    for l, ((Wg, bg), (Wo, bo)) in enumerate(zip(cnn.split(G.cpu().numpy()), cnn.split(g_o))):
+        assert rel(Wg, Wo) <= 3e-2, (l + 1, "W", rel(Wg, Wo))
+        if bo.size > 1:
+            assert rel(bg, bo) <= 3e-2, (l + 1, "b", rel(bg, bo))
+    # db5 is the sum of dL/dy over the batch: the GPU sums the values rounded
+    # to bf16 (relative error <= 2^-8 each)
+    d = dY.double().cpu()
+    assert abs(float(G[-1]) - float(d.sum())) <= 2.0 ** -8 * float(d.abs().sum())
 
 
 def test_cnn_adam_steps_reduce_the_loss():
