@@ -779,6 +779,193 @@ __global__ void __launch_bounds__(288) k_conv_wgrad32(const __nv_bfloat16 *__res
   }
 }
 
+// Weight and bias gradients of the 32 -> 32 layers on the 5th-generation
+// tensor cores:
+//   dW[dy][dx][co][ci] = sum_p dz[co][p] x[ci][p + (dy - 1, dx - 1)],   db[co] = sum_p dz[co][p].
+// Re-indexed by q = p + (dy - 1) rows, the taps split between the operands:
+//   dW[dy][dx][co][ci] = sum_q x[ci][q + (0, dx - 1)] dz[co][q - (dy - 1, 0)],
+// so that one MMA per 16 pixels q of a row (K = 16) computes all nine taps,
+// D[32 dx + ci][32 (2 - dy) + co] (M = 128, N = 96; fp32 in tensor memory).
+// Both operands are MN-major (channels contiguous) in a pixel-major layout
+// with the 64-byte swizzle: a pixel's 32 channels form one 64-byte row, and
+// the swizzle is a function of the shared-memory address, so a descriptor
+// may start at any pixel.  A = x: its 32-row M blocks start one pixel apart
+// (leading byte offset 64), block j holding the tap dx = j (block 3 is read
+// but not used); B = dz: its 32-column N blocks start one staged row apart,
+// block i holding the tap dy = 2 - i; a K step of 8 pixels is 512 bytes.
+// Tiles of 4 rows x 128 pixels: x is staged over the tile's rows and pixels
+// x0 - 1 .. x0 + 130, dz over rows y0 - 1 .. y0 + 4 and pixels x0 .. x0 + 127,
+// by 16-byte cp.async copies into their swizzled places (zero outside the
+// image), in two stages: tile k + 1's copies are in flight while tile k is
+// multiplied.  One thread issues a tile's 32 MMAs into the accumulator the
+// block keeps over all its tiles; meanwhile the block's threads sum dz over
+// the tile's own rows for db.  At the end warps 0-2 read the accumulator
+// (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
+// gives up flags the error word.
+constexpr int kWtR = 4, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
+constexpr int kWtXB = kWtR * kWtXP * 64;                    // staged x bytes
+constexpr int kWtZB = (kWtR + 2) * kWtC * 64;               // staged dz bytes
+constexpr int kWtStage = kWtXB + kWtZB;
+constexpr size_t kWtSmem = 2 * (size_t)kWtStage + 1024;
+static_assert(kWtXB % 1024 == 0 && kWtStage % 1024 == 0, "staged regions start on the swizzle period");
+static_assert(kWtSmem <= 227 * 1024, "two stages must fit in shared memory");
+// kind::f16, fp32 accumulator, bf16 A and B, both MN-major, N = 96, M = 128
+constexpr uint32_t kWtIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
+
+// 64-byte swizzle of a byte offset from a 1024-byte-aligned base: the 16-byte
+// chunk index (bits 4-5) XOR bits 7-8.
+__device__ __forceinline__ uint32_t swz64(uint32_t off) { return off ^ (((off >> 7) & 3u) << 4); }
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // start, leading (MN block) and stride (K block) byte offsets in 16-byte
+  // units, descriptor version 1, layout type 4 (64-byte swizzle), base offset 0
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+__global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
+                                                          const __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
+                                                          float *__restrict__ db, int nimg, int H, int W, int *err) {
+  extern __shared__ unsigned char s_raw[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ float s_db[32];
+  const uint32_t raw = (uint32_t)__cvta_generic_to_shared(s_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const unsigned char *gbase = s_raw + (base - raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntx = (W + kWtC - 1) / kWtC, tpi = ntx * ((H + kWtR - 1) / kWtR), ntiles = tpi * nimg;
+  const long long HWp = (long long)H * W;
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[0]);
+  if (tid == 0) {
+    s_abort = 0;
+    tc_mbar_init(bar0, 1);
+    tc_mbar_init(bar0 + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < 32) s_db[tid] = 0.f;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        (uint32_t)__cvta_generic_to_shared(&s_tmem)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  auto origin = [&](int tt, int &img, int &y0, int &x0) {
+    img = tt / tpi;
+    const int rem = tt - img * tpi, ty = rem / ntx;
+    y0 = ty * kWtR;
+    x0 = (rem - ty * ntx) * kWtC;
+  };
+  auto stage = [&](int tt, int sb) {
+    int img, y0, x0;
+    origin(tt, img, y0, x0);
+    const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
+#pragma unroll 4
+    for (int e = tid; e < 4 * kWtR * kWtXP; e += 128) {  // x: [group][row][pixel] order, pixels fastest
+      const int i = e % kWtXP, r = (e / kWtXP) % kWtR, n = e / (kWtXP * kWtR);
+      const int yy = y0 + r, xx = x0 - 1 + i;
+      const bool ok = yy < H && xx >= 0 && xx < W;
+      const __nv_bfloat16 *src = ok ? x + (((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 8 : x;
+      cp_async16(X + swz64((uint32_t)((r * kWtXP + i) * 64 + n * 16)), src, ok);
+    }
+#pragma unroll 4
+    for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += 128) {
+      const int i = e % kWtC, r = (e / kWtC) % (kWtR + 2), n = e / (kWtC * (kWtR + 2));
+      const int yy = y0 - 1 + r, xx = x0 + i;
+      const bool ok = yy >= 0 && yy < H && xx < W;
+      const __nv_bfloat16 *src = ok ? dz + (((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 8 : dz;
+      cp_async16(Z + swz64((uint32_t)((r * kWtC + i) * 64 + n * 16)), src, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  float bsum[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) bsum[c] = 0.f;
+  int k = 0;
+  if ((int)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x, ++k) {
+    const int sb = k & 1, tn = tt + gridDim.x;
+    if (tn < ntiles) {
+      // stage sb ^ 1 is free once tile k - 1's MMAs (and sums) are done
+      if (k >= 1 && tid == 0) tc_wait(bar0 + 8 * (sb ^ 1), ((k - 1) >> 1) & 1, &s_abort);
+      __syncthreads();
+      if (s_abort) break;
+      stage(tn, sb ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();  // tile k is staged
+    const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t a0 = umma_desc_sw64(X, 64, 512), b0 = umma_desc_sw64(Z, kWtC * 64, 512);
+#pragma unroll
+      for (int r = 0; r < kWtR; ++r)
+#pragma unroll
+        for (int c = 0; c < kWtC / 16; ++c) {
+          const uint64_t ad = a0 + (uint64_t)(((r * kWtXP + 16 * c) * 64) >> 4);
+          const uint64_t bd = b0 + (uint64_t)(((r * kWtC + 16 * c) * 64) >> 4);
+          const uint32_t acc = (k > 0 || r > 0 || c > 0) ? 1u : 0u;
+          asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem), "l"(ad), "l"(bd),
+                       "r"(kWtIdesc), "r"(acc));
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * sb)
+                   : "memory");
+    }
+    // db: dz of the tile's own rows (staged rows 1 .. 4), pixel tid
+    const unsigned char *zg = gbase + sb * kWtStage + kWtXB;
+#pragma unroll
+    for (int r = 1; r <= kWtR; ++r)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((r * kWtC + tid) * 64 + n * 16)));
+        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h2[e]);
+          bsum[8 * n + 2 * e] += f.x;
+          bsum[8 * n + 2 * e + 1] += f.y;
+        }
+      }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (k > 0 && tid == 0 && !s_abort) tc_wait(bar0 + 8 * ((k - 1) & 1), ((k - 1) >> 1) & 1, &s_abort);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool ok = !s_abort;
+  if (ok && k > 0 && warp < 3) {  // lanes 32 dx + ci; column 32 (2 - dy) + co
+#pragma unroll 1
+    for (int c0 = 0; c0 < 96; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      const int dyy = 2 - c0 / 32;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) atomicAdd(dw + ((3 * dyy + warp) * 32 + c) * 32 + lane, v[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    float v = bsum[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(&s_db[c], v);
+  }
+  __syncthreads();
+  if (ok && tid < 32) atomicAdd(db + tid, s_db[tid]);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
 // Weight and bias gradients of the two one-channel end layers, without
 // widening the one channel to 32:
 //   first layer:  dW1[tap][co] = sum_p dz1[co][p] x0[p + off(tap)],   db1[co] = sum_p dz1[co][p]
@@ -1014,9 +1201,25 @@ void set_attrs() {
   cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+  cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
   cudaFuncSetAttribute(k_conv_wgrad1<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   cudaFuncSetAttribute(k_conv_wgrad1<true, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   done = true;
+}
+
+// RBC_WGRAD=0 selects the mma.sync weight gradient of the 32 -> 32 layers (a sweep knob, read once).
+bool wgrad_tc() {
+  static const bool on = [] {
+    const char *e = getenv("RBC_WGRAD");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+int grid_wgrad_tc(int nimg, int H, int W) {
+  static int sms = 0;
+  if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const long long tiles = (long long)((W + kWtC - 1) / kWtC) * ((H + kWtR - 1) / kWtR) * nimg;
+  return (int)(tiles < sms ? tiles : sms);
 }
 
 // Persistent grid of the one-channel weight-gradient kernel (attributes set by set_attrs).
@@ -1190,8 +1393,12 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   const int woff[3] = {kW4, kW3, kW2}, boff[3] = {kB4, kB3, kB2};
   for (int l = 0; l < 3; ++l) {
     const int layer_in = 2 - l;  // act index of this layer's input: act3 (l=0) ... act1
-    k_conv_wgrad32<C, C><<<pg, 288, kWgSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l], grad_dev + boff[l],
-                                                   nimg, H, W);
+    if (wgrad_tc())
+      k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), 128, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
+                                                                       grad_dev + boff[l], nimg, H, W, tc_err_dev);
+    else
+      k_conv_wgrad32<C, C><<<pg, 288, kWgSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l], grad_dev + boff[l],
+                                                     nimg, H, W);
     ok_tc = ok_tc && launch_conv_tc<kBackData>(w.dz[cur], w.wb + woff[l], nullptr, w.act[layer_in], w.dz[1 - cur], nimg, H, W, s);
     cur = 1 - cur;
   }
