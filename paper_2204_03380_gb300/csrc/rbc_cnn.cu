@@ -797,9 +797,12 @@ __global__ void __launch_bounds__(288) k_conv_wgrad32(const __nv_bfloat16 *__res
 // x0 - 1 .. x0 + 130, dz over rows y0 - 1 .. y0 + 4 and pixels x0 .. x0 + 127,
 // by 16-byte cp.async copies into their swizzled places (zero outside the
 // image), in two stages: tile k + 1's copies are in flight while tile k is
-// multiplied.  One thread issues a tile's 32 MMAs into the accumulator the
-// block keeps over all its tiles; meanwhile the block's threads sum dz over
-// the tile's own rows for db.  At the end warps 0-2 read the accumulator
+// multiplied.  (A tensor copy cannot write this layout from the
+// channel-group-planar activations: with the 64-byte swizzle it pads a box
+// whose rows are 16 bytes.)  16 warps share the copies, so that their address
+// arithmetic and latency overlap.  One thread issues a tile's 32 MMAs into
+// the accumulator the block keeps over all its tiles; meanwhile the block's
+// threads sum dz over the tile's own rows for db (one pixel each).  At the end warps 0-2 read the accumulator
 // (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
 // gives up flags the error word.
 constexpr int kWtR = 4, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
@@ -807,6 +810,7 @@ constexpr int kWtXB = kWtR * kWtXP * 64;                    // staged x bytes
 constexpr int kWtZB = (kWtR + 2) * kWtC * 64;               // staged dz bytes
 constexpr int kWtStage = kWtXB + kWtZB;
 constexpr size_t kWtSmem = 2 * (size_t)kWtStage + 1024;
+constexpr int kWtThreads = 512;
 static_assert(kWtXB % 1024 == 0 && kWtStage % 1024 == 0, "staged regions start on the swizzle period");
 static_assert(kWtSmem <= 227 * 1024, "two stages must fit in shared memory");
 // kind::f16, fp32 accumulator, bf16 A and B, both MN-major, N = 96, M = 128
@@ -823,7 +827,7 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t addr, uint32_t lbo, 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-__global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
+__global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
                                                           const __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
                                                           float *__restrict__ db, int nimg, int H, int W, int *err) {
   extern __shared__ unsigned char s_raw[];
@@ -865,7 +869,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
     origin(tt, img, y0, x0);
     const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
 #pragma unroll 4
-    for (int e = tid; e < 4 * kWtR * kWtXP; e += 128) {  // x: [group][row][pixel] order, pixels fastest
+    for (int e = tid; e < 4 * kWtR * kWtXP; e += kWtThreads) {  // x: [group][row][pixel] order, pixels fastest
       const int i = e % kWtXP, r = (e / kWtXP) % kWtR, n = e / (kWtXP * kWtR);
       const int yy = y0 + r, xx = x0 - 1 + i;
       const bool ok = yy < H && xx >= 0 && xx < W;
@@ -873,7 +877,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
       cp_async16(X + swz64((uint32_t)((r * kWtXP + i) * 64 + n * 16)), src, ok);
     }
 #pragma unroll 4
-    for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += 128) {
+    for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += kWtThreads) {
       const int i = e % kWtC, r = (e / kWtC) % (kWtR + 2), n = e / (kWtC * (kWtR + 2));
       const int yy = y0 - 1 + r, xx = x0 + i;
       const bool ok = yy >= 0 && yy < H && xx < W;
@@ -919,21 +923,20 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * sb)
                    : "memory");
     }
-    // db: dz of the tile's own rows (staged rows 1 .. 4), pixel tid
+    // db: dz of the tile's own rows (staged rows 1 .. 4), one pixel per thread
+    static_assert(kWtThreads == kWtR * kWtC, "one pixel of the tile per thread");
     const unsigned char *zg = gbase + sb * kWtStage + kWtXB;
 #pragma unroll
-    for (int r = 1; r <= kWtR; ++r)
+    for (int n = 0; n < 4; ++n) {
+      const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((kWtC + tid) * 64 + n * 16)));
+      const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
 #pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((r * kWtC + tid) * 64 + n * 16)));
-        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(h2[e]);
-          bsum[8 * n + 2 * e] += f.x;
-          bsum[8 * n + 2 * e + 1] += f.y;
-        }
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(h2[e]);
+        bsum[8 * n + 2 * e] += f.x;
+        bsum[8 * n + 2 * e + 1] += f.y;
       }
+    }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (k > 0 && tid == 0 && !s_abort) tc_wait(bar0 + 8 * ((k - 1) & 1), ((k - 1) >> 1) & 1, &s_abort);
@@ -1394,7 +1397,7 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   for (int l = 0; l < 3; ++l) {
     const int layer_in = 2 - l;  // act index of this layer's input: act3 (l=0) ... act1
     if (wgrad_tc())
-      k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), 128, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
+      k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), kWtThreads, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
                                                                        grad_dev + boff[l], nimg, H, W, tc_err_dev);
     else
       k_conv_wgrad32<C, C><<<pg, 288, kWgSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l], grad_dev + boff[l],
