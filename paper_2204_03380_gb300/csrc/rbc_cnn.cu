@@ -16,9 +16,10 @@
 // 32 -> 1 last layer run as implicit GEMMs on the 5th-generation tensor cores
 // (tcgen05.mma, operands in shared memory, fp32 accumulators in tensor
 // memory).  The one-channel first layer runs on the warp-level tensor cores
-// (mma.sync m16n8k16, the 9 taps padded to K = 16).  Weight gradients are per-tap
-// GEMMs over the pixels on the warp-level tensor cores (mma.sync m16n8k16),
-// reduced by persistent blocks and added to the fp32 gradient once per block.
+// (mma.sync m16n8k16, the 9 taps padded to K = 16).  The weight gradients of
+// the 32 -> 32 layers run on tcgen05 too (one MMA per 16 pixels covers all
+// nine taps); those of the one-channel end layers on mma.sync with the taps
+// on M.  Persistent blocks add their sums to the fp32 gradient once each.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -35,7 +36,6 @@ void add_launches(long long n);
 
 namespace {
 
-constexpr int TH = 8, TW = 32;  // output tile: 8 rows x 32 columns, one warp per row
 constexpr int C = 32;           // hidden channels
 // parameter offsets (fp32 master copy): W1 b1 W2 b2 W3 b3 W4 b4 W5 b5
 constexpr int kW1 = 0, kB1 = kW1 + 9 * C, kW2 = kB1 + C, kB2 = kW2 + 9 * C * C, kW3 = kB2 + C,
@@ -635,148 +635,12 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
   if (warp == kTcEpi + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
-// Weight and bias gradients of a convolution layer:
-//   dW[tap][co][ci] = sum_p dz[co][p] x[ci][p + tap],  db[co] = sum_p dz[co][p],
-// with x and dz 32-channel planar (the 32 -> 32 layers; the one-channel end
-// layers have their own kernel, k_conv_wgrad1).
-// Per tap a GEMM with M = 32 output channels, N = 32 input channels and K =
-// the pixels, on mma.sync m16n8k16 (bf16 in, fp32 accumulate).  Persistent
-// blocks of nine warps (one per tap) walk 8 x 32-pixel tiles; a tile's input
-// halo (10 x 34 pixels) and its 256 output gradients are copied into shared
-// memory as they lie in global memory (channel-group planar: 16 bytes = 8
-// channels of one pixel), by 16-byte cp.async copies that zero-fill outside
-// the image, double-buffered so that tile k + 1 arrives while tile k is
-// multiplied.  Both operands come out of that layout with ldmatrix.trans: a
-// pixel's 16-byte chunk is one row of an 8 x 8 matrix whatever the tap's
-// shift, so every tap reads the same halo at a different start pixel.  The
-// centre-tap warp also multiplies by a column of ones: the bias gradient.
-constexpr int kWgHP = (TH + 2) * (TW + 2);  // halo pixels of a tile
-constexpr int kWgNP = TH * TW;              // output pixels of a tile
-constexpr int kWgBuf = 4 * (kWgHP + kWgNP) * 8;  // bf16 per buffer: x halo, then dz
-constexpr size_t kWgSmem = 2 * sizeof(__nv_bfloat16) * kWgBuf;
-
-__device__ __forceinline__ void cp16_zfill(void *smem, const void *gmem, bool valid) {
-  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
-               : "memory");
-}
-
+// ldmatrix of four 8 x 8 bf16 matrices, transposed (rows given by lanes 8j .. 8j + 7).
 __device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *smem_row) {
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem_row);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(sa));
-}
-
-template <int CI, int CO>
-__global__ void __launch_bounds__(288) k_conv_wgrad32(const __nv_bfloat16 *__restrict__ x,
-                                                      const __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
-                                                      float *__restrict__ db, int nimg, int H, int W) {
-  extern __shared__ __align__(16) __nv_bfloat16 s_wg[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, tq = lane & 3;
-  const int dy = warp / 3, dx = warp % 3;  // this warp's tap
-  const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
-  const long long ntiles = (long long)tx * ty * nimg, HWp = (long long)H * W;
-  // stage tile `tile` into buffer b (one cp.async group)
-  auto stage = [&](long long tile, int b) {
-    const int img = (int)(tile / ((long long)tx * ty));
-    const int rem = (int)(tile % ((long long)tx * ty));
-    const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
-    __nv_bfloat16 *sx = s_wg + b * kWgBuf, *sd = sx + 4 * kWgHP * 8;
-    for (int i = threadIdx.x; i < 4 * kWgHP; i += blockDim.x) {
-      const int cg = i / kWgHP, hp = i % kWgHP;
-      const int yy = y0 + hp / (TW + 2) - 1, xx = x0 + hp % (TW + 2) - 1;
-      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-      const __nv_bfloat16 *src = ok ? x + (((long long)img * 4 + cg) * HWp + (long long)yy * W + xx) * 8 : x;
-      cp16_zfill(sx + (cg * kWgHP + hp) * 8, src, ok);
-    }
-    for (int i = threadIdx.x; i < 4 * kWgNP; i += blockDim.x) {
-      const int cg = i / kWgNP, q = i % kWgNP;
-      const int yy = y0 + q / TW, xx = x0 + q % TW;
-      const bool ok = yy < H && xx < W;
-      const __nv_bfloat16 *src = ok ? dz + (((long long)img * 4 + cg) * HWp + (long long)yy * W + xx) * 8 : dz;
-      cp16_zfill(sd + (cg * kWgNP + q) * 8, src, ok);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  float acc[2][4][4], accb[2][4];
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-#pragma unroll
-    for (int n = 0; n < 4; ++n)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[m][n][r] = 0.f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) accb[m][r] = 0.f;
-  }
-  const uint32_t ones[2] = {0x3F803F80u, 0x3F803F80u};  // bf16 1.0 pairs
-  // ldmatrix row of this lane: matrix j = lane / 8, row r = lane % 8
-  const int lj = lane >> 3, lr = lane & 7;
-  int b = 0;
-  if ((long long)blockIdx.x < ntiles) stage(blockIdx.x, 0);
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long next = tile + gridDim.x;
-    if (next < ntiles) {
-      stage(next, b ^ 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    __syncthreads();
-    if (warp < 9) {
-      const __nv_bfloat16 *sx = s_wg + b * kWgBuf, *sd = sx + 4 * kWgHP * 8;
-#pragma unroll 1
-      for (int k0 = 0; k0 < kWgNP; k0 += 16) {
-        const int row = k0 / TW, c0 = k0 % TW;
-        // A (dz): matrices (co 0-7 | 8-15) x (pixels 0-7 | 8-15) of each 16-channel half
-        uint32_t a[2][4];
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-          ldsm_x4_t(a[m], sd + ((2 * m + (lj & 1)) * kWgNP + k0 + (lj >> 1) * 8 + lr) * 8);
-        // B (x shifted by the tap): channel groups 2h, 2h + 1, pixels 0-7 | 8-15
-        const int hq = (row + dy) * (TW + 2) + c0 + dx;
-        uint32_t bf[4][2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t r4[4];
-          ldsm_x4_t(r4, sx + ((2 * h + (lj >> 1)) * kWgHP + hq + (lj & 1) * 8 + lr) * 8);
-          bf[2 * h][0] = r4[0];
-          bf[2 * h][1] = r4[1];
-          bf[2 * h + 1][0] = r4[2];
-          bf[2 * h + 1][1] = r4[3];
-        }
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-          for (int n = 0; n < 4; ++n) mma16816(acc[m][n], a[m], bf[n]);
-        if (warp == 4) {
-#pragma unroll
-          for (int m = 0; m < 2; ++m) mma16816(accb[m], a[m], ones);
-        }
-      }
-    }
-    __syncthreads();  // buffer b is refilled by the stage two tiles on
-    b ^= 1;
-  }
-  if (warp < 9) {
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-      for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int co = m * 16 + g + (r >> 1) * 8, ci = n * 8 + tq * 2 + (r & 1);
-          if (co < CO && ci < CI) atomicAdd(dw + (warp * CO + co) * CI + ci, acc[m][n][r]);
-        }
-    if (warp == 4 && tq == 0) {
-#pragma unroll
-      for (int m = 0; m < 2; ++m) {
-        if (m * 16 + g < CO) atomicAdd(db + m * 16 + g, accb[m][0]);
-        if (m * 16 + g + 8 < CO) atomicAdd(db + m * 16 + g + 8, accb[m][2]);
-      }
-    }
-  }
 }
 
 // Weight and bias gradients of the 32 -> 32 layers on the 5th-generation
@@ -797,12 +661,9 @@ __global__ void __launch_bounds__(288) k_conv_wgrad32(const __nv_bfloat16 *__res
 // x0 - 1 .. x0 + 130, dz over rows y0 - 1 .. y0 + 4 and pixels x0 .. x0 + 127,
 // by 16-byte cp.async copies into their swizzled places (zero outside the
 // image), in two stages: tile k + 1's copies are in flight while tile k is
-// multiplied.  (A tensor copy cannot write this layout from the
-// channel-group-planar activations: with the 64-byte swizzle it pads a box
-// whose rows are 16 bytes.)  16 warps share the copies, so that their address
-// arithmetic and latency overlap.  One thread issues a tile's 32 MMAs into
-// the accumulator the block keeps over all its tiles; meanwhile the block's
-// threads sum dz over the tile's own rows for db (one pixel each).  At the end warps 0-2 read the accumulator
+// multiplied.  One thread issues a tile's 32 MMAs into the accumulator the
+// block keeps over all its tiles; meanwhile the block's threads sum dz over
+// the tile's own rows for db.  At the end warps 0-2 read the accumulator
 // (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
 // gives up flags the error word.
 constexpr int kWtR = 4, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
@@ -810,7 +671,6 @@ constexpr int kWtXB = kWtR * kWtXP * 64;                    // staged x bytes
 constexpr int kWtZB = (kWtR + 2) * kWtC * 64;               // staged dz bytes
 constexpr int kWtStage = kWtXB + kWtZB;
 constexpr size_t kWtSmem = 2 * (size_t)kWtStage + 1024;
-constexpr int kWtThreads = 512;
 static_assert(kWtXB % 1024 == 0 && kWtStage % 1024 == 0, "staged regions start on the swizzle period");
 static_assert(kWtSmem <= 227 * 1024, "two stages must fit in shared memory");
 // kind::f16, fp32 accumulator, bf16 A and B, both MN-major, N = 96, M = 128
@@ -827,7 +687,7 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t addr, uint32_t lbo, 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-__global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
+__global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
                                                           const __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
                                                           float *__restrict__ db, int nimg, int H, int W, int *err) {
   extern __shared__ unsigned char s_raw[];
@@ -869,7 +729,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
     origin(tt, img, y0, x0);
     const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
 #pragma unroll 4
-    for (int e = tid; e < 4 * kWtR * kWtXP; e += kWtThreads) {  // x: [group][row][pixel] order, pixels fastest
+    for (int e = tid; e < 4 * kWtR * kWtXP; e += 128) {  // x: [group][row][pixel] order, pixels fastest
       const int i = e % kWtXP, r = (e / kWtXP) % kWtR, n = e / (kWtXP * kWtR);
       const int yy = y0 + r, xx = x0 - 1 + i;
       const bool ok = yy < H && xx >= 0 && xx < W;
@@ -877,7 +737,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
       cp_async16(X + swz64((uint32_t)((r * kWtXP + i) * 64 + n * 16)), src, ok);
     }
 #pragma unroll 4
-    for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += kWtThreads) {
+    for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += 128) {
       const int i = e % kWtC, r = (e / kWtC) % (kWtR + 2), n = e / (kWtC * (kWtR + 2));
       const int yy = y0 - 1 + r, xx = x0 + i;
       const bool ok = yy >= 0 && yy < H && xx < W;
@@ -923,20 +783,21 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * sb)
                    : "memory");
     }
-    // db: dz of the tile's own rows (staged rows 1 .. 4), one pixel per thread
-    static_assert(kWtThreads == kWtR * kWtC, "one pixel of the tile per thread");
+    // db: dz of the tile's own rows (staged rows 1 .. 4), pixel tid
     const unsigned char *zg = gbase + sb * kWtStage + kWtXB;
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-      const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((kWtC + tid) * 64 + n * 16)));
-      const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
+    for (int r = 1; r <= kWtR; ++r)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(h2[e]);
-        bsum[8 * n + 2 * e] += f.x;
-        bsum[8 * n + 2 * e + 1] += f.y;
+      for (int n = 0; n < 4; ++n) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((r * kWtC + tid) * 64 + n * 16)));
+        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h2[e]);
+          bsum[8 * n + 2 * e] += f.x;
+          bsum[8 * n + 2 * e + 1] += f.y;
+        }
       }
-    }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (k > 0 && tid == 0 && !s_abort) tc_wait(bar0 + 8 * ((k - 1) & 1), ((k - 1) >> 1) & 1, &s_abort);
@@ -1203,21 +1064,13 @@ void set_attrs() {
   cudaFuncSetAttribute(k_conv_tc<kHidden, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
-  cudaFuncSetAttribute(k_conv_wgrad32<C, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
   cudaFuncSetAttribute(k_conv_wgrad1<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   cudaFuncSetAttribute(k_conv_wgrad1<true, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   done = true;
 }
 
-// RBC_WGRAD=0 selects the mma.sync weight gradient of the 32 -> 32 layers (a sweep knob, read once).
-bool wgrad_tc() {
-  static const bool on = [] {
-    const char *e = getenv("RBC_WGRAD");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
+// Persistent grid of the tcgen05 weight-gradient kernel: one block per SM (its shared memory).
 int grid_wgrad_tc(int nimg, int H, int W) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
@@ -1380,9 +1233,6 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   const long long npx = (long long)nimg * H * W;
   Ws w = carve(ws_dev, npx);  // activations from the preceding rbc_cnn_forward
 
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const int pg = 2 * sms;
   // layer 5: dW5, db5 from dy; dz4 = conv^T(dy) masked by act4 > 0
   k_conv_wgrad1<false, float><<<grid_wgrad1<false, float>(nimg, H, W), 128, kW1Smem, s>>>(
       dy_dev, w.act[3], grad_dev + kW5, grad_dev + kB5, nimg, H, W);
@@ -1396,12 +1246,8 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   const int woff[3] = {kW4, kW3, kW2}, boff[3] = {kB4, kB3, kB2};
   for (int l = 0; l < 3; ++l) {
     const int layer_in = 2 - l;  // act index of this layer's input: act3 (l=0) ... act1
-    if (wgrad_tc())
-      k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), kWtThreads, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
-                                                                       grad_dev + boff[l], nimg, H, W, tc_err_dev);
-    else
-      k_conv_wgrad32<C, C><<<pg, 288, kWgSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l], grad_dev + boff[l],
-                                                     nimg, H, W);
+    k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), 128, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
+                                                                     grad_dev + boff[l], nimg, H, W, tc_err_dev);
     ok_tc = ok_tc && launch_conv_tc<kBackData>(w.dz[cur], w.wb + woff[l], nullptr, w.act[layer_in], w.dz[1 - cur], nimg, H, W, s);
     cur = 1 - cur;
   }
