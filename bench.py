@@ -554,7 +554,7 @@ def run_denoise(args, rank, world):
                                                      "8_stack": e_half, "target": 5e-2},
                       "train_data_s": t_data, "train_s": t_train, "rtm_3d_s": t_rtm, "stack16_s": 16 * t_rtm,
                       "inference_s": t_inf},
-           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05: hidden layers and the 32 -> 1 last layer) + k_conv_1to32 (mma.sync first layer)", "achieved": achieved,
+           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05: layers 1-2 fused, layers 3-4, and the 32 -> 1 layer 5)", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
            "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": None}
@@ -611,7 +611,7 @@ def run_cnn(args, rank, world):
            "data": "synthetic", "config": {"workload": f"cnn: batch of {n} images of {H}x{Wd}",
                                            "train_step_ms": t_train * 1e3, "inference_ms": t_inf * 1e3,
                                            "training_tflops": 3 * 56448.0 * px / t_train / 1e12},
-           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05: hidden layers and the 32 -> 1 last layer) + k_conv_1to32 (mma.sync first layer)", "achieved": achieved,
+           "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05: layers 1-2 fused, layers 3-4, and the 32 -> 1 layer 5)", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops)", "traffic": None},
            "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": None}

@@ -340,6 +340,15 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W,
                     const float *x_dev, float *y_dev, void *ws_dev,
                     void *stream);
 
+/* y = CNN(x) for inference: the same result as rbc_cnn_forward, without
+ * keeping what rbc_cnn_backward needs (the first layer's output is built
+ * inside the second layer's kernel and never written to global memory).
+ * ws_dev: workspace of rbc_cnn_workspace_bytes, used for the hidden
+ * activations.  Errors: RBC_EINVAL, RBC_ECUDA. */
+int rbc_cnn_infer(const float *params_dev, int nimg, int H, int W,
+                  const float *x_dev, float *y_dev, void *ws_dev,
+                  void *stream);
+
 /* grad_dev (param_count fp32) += dL/dparams for the dL/dy in dy_dev, using
  * the activations the preceding rbc_cnn_forward left in ws_dev (same batch,
  * same parameters).  Errors: RBC_EINVAL, RBC_ECUDA. */

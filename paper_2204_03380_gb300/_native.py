@@ -101,10 +101,11 @@ def _load():
     lib.rbc_cnn_workspace_bytes.restype = C.c_longlong
     lib.rbc_cnn_workspace_bytes.argtypes = [I, I, I]
     lib.rbc_cnn_forward.argtypes = [P, I, I, I, P, P, P, P]
+    lib.rbc_cnn_infer.argtypes = [P, I, I, I, P, P, P, P]
     lib.rbc_cnn_backward.argtypes = [P, I, I, I, P, P, P, P]
     lib.rbc_cnn_mse.argtypes = [P, P, C.c_longlong, P, P, P]
     lib.rbc_cnn_adam.argtypes = [P, P, P, P, F, F, F, F, I, P]
-    for name in ("rbc_cnn_forward", "rbc_cnn_backward", "rbc_cnn_mse", "rbc_cnn_adam"):
+    for name in ("rbc_cnn_forward", "rbc_cnn_infer", "rbc_cnn_backward", "rbc_cnn_mse", "rbc_cnn_adam"):
         getattr(lib, name).restype = I
     lib.rbc_model_static.argtypes = [G, P, P, P, I, P, P, P]
     lib.rbc_model_static.restype = I
@@ -122,7 +123,7 @@ EXPORTED = ("rbc_build_velocity", "rbc_create", "rbc_destroy", "rbc_model", "rbc
             "rbc_image_stack", "rbc_set_snapshots", "rbc_get_panels", "rbc_phase_timing",
             "rbc_model_static", "rbc_fwi_forward", "rbc_fwi_backward", "rbc_batch_create",
             "rbc_batch_destroy", "rbc_batch_rtm", "rbc_batch_info", "rbc_batch_timing",
-            "rbc_cnn_param_count", "rbc_cnn_workspace_bytes", "rbc_cnn_forward", "rbc_cnn_backward",
+            "rbc_cnn_param_count", "rbc_cnn_workspace_bytes", "rbc_cnn_forward", "rbc_cnn_infer", "rbc_cnn_backward",
             "rbc_cnn_mse", "rbc_cnn_adam", "rbc_inject_fault", "rbc_last_error",
             "rbc_launch_count", "rbc_nyquist_stride", "rbc_storage_bytes", "rbc_rtm_storage",
             "rbc_set_coef")
@@ -363,6 +364,13 @@ def rbc_cnn_forward(params, x, y, ws, stream=None):
     n, H, W = x.shape
     _check(_lib.rbc_cnn_forward(_dev(params, None, "params"), n, H, W, _dev(x, None, "x"), _dev(y, None, "y"),
                                 _u8(ws, "ws"), _stream(stream)))
+
+
+def rbc_cnn_infer(params, x, y, ws, stream=None):
+    """Inference forward (keeps nothing for a backward pass); arguments as rbc_cnn_forward."""
+    n, H, W = x.shape
+    _check(_lib.rbc_cnn_infer(_dev(params, None, "params"), n, H, W, _dev(x, None, "x"), _dev(y, None, "y"),
+                              _u8(ws, "ws"), _stream(stream)))
 
 
 def rbc_cnn_backward(params, dy, grad, ws, stream=None):

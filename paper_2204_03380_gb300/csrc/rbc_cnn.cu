@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <cstdlib>
+#include <cstring>
 
 #include "../../include/rbc.h"
 #include "rbc_internal.cuh"
@@ -50,7 +51,7 @@ __device__ __forceinline__ void mma16816(float *c, const uint32_t *a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-enum { kHidden = 0, kLast = 1, kBackData = 2 };
+enum { kHidden = 0, kLast = 1, kBackData = 2, kFused = 3 };
 
 // The one-channel first layer (1 -> 32 channels, and the last layer's
 // backward-data pass) on the warp-level tensor cores:
@@ -387,21 +388,53 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 //   MODE kHidden:   out = relu(conv(in) + bias)                        (32 -> 32)
 //   MODE kBackData: out = conv(in) * (mask > 0)   (weights mirrored and transposed)
 //   MODE kLast:     out_f = resid + conv(in) + bias                    (32 -> 1)
+//   MODE kFused:    out = relu(conv(a1) + bias) with a1 = relu(conv1(x1) + b1)
+//                   computed in the block (the first two layers; a1 stored
+//                   to out0 when out0 is not null)
 // The last layer's single output channel is padded to N = 16 per output row
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
 // kTcEpi epilogue warps: warp e drains TMEM lane quarter e % 4 (pixels
 // 32 (e % 4) .. +31) for the output rows of its share (R * 4 / kTcEpi rows,
-// starting at row (e / 4) * R * 4 / kTcEpi); warp kTcEpi is the producer,
-// warp kTcEpi + 1 the MMA issuer.
+// starting at row (e / 4) * R * 4 / kTcEpi); warps kTcEpi .. kTcEpi +
+// tc_nprod(MODE) - 1 are the producers, the next warp the MMA issuer.
+//
+// kFused: instead of the tensor copy of a stored first-layer output, four
+// builder warps compute it over the tile's halo (R + 2 rows x 128 pixels)
+// into the ring stage, in the layout the copy would have produced: the fp32
+// one-channel input's halo (R + 4 rows x 130 pixels, prefetched a tile
+// ahead into registers, rounded to bf16) is parked in shared memory, and
+// each 16 pixels of a halo row are one m16n8k16 MMA per 8 channels as in
+// k_conv_1to32 (taps padded to K = 16, bias as the accumulator's start,
+// relu and rounding in one conversion), stored as 4-byte pieces of the
+// pixels' 16-byte channel groups; outside the image the stage holds zeros
+// (the second layer's padding).  The builders then make their writes visible
+// to the tensor cores and arrive on the stage's "full" barrier.  The first
+// layer's output never passes through global memory unless out0 asks for it
+// (the training pass keeps it for the backward pass).
+constexpr int tc_nprod(int mode) { return mode == kFused ? 4 : 1; }
+constexpr int tc_threads(int mode) { return 32 * (kTcEpi + tc_nprod(mode) + 1); }
+constexpr int kFxR = 4;                  // x halo rows beyond the tile's R (two on each side)
+constexpr int kFxC = kTcHW + 2;          // x halo columns (x0 - 2 .. x0 + 127)
+constexpr int kFxP = 144;                // x halo row pitch (2-byte values; conflict-free gathers)
+constexpr int tc_fx_bytes(int R) { return (R + kFxR) * kFxP * 2; }
+constexpr int tc_fx_pre(int R) { return ((R + kFxR) * kFxC + 127) / 128; }  // x values per builder thread
+constexpr int tc_smem_mode(int mode, int R) { return tc_smem(R) + (mode == kFused ? tc_fx_bytes(R) : 0); }
+static_assert(tc_smem(kTcR) + tc_fx_bytes(kTcR) <= 227 * 1024, "the fused ring must fit in shared memory");
+
 template <int MODE, int R>
-__global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
+__global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
                                                     const __nv_bfloat16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
                                                     const __nv_bfloat16 *__restrict__ mask,
                                                     __nv_bfloat16 *__restrict__ out, float *__restrict__ out_f,
                                                     const float *__restrict__ resid, int nimg, int H, int W,
-                                                    int *err) {
+                                                    int *err, const float *__restrict__ x1 = nullptr,
+                                                    const __nv_bfloat16 *__restrict__ w1 = nullptr,
+                                                    const float *__restrict__ b1 = nullptr,
+                                                    __nv_bfloat16 *__restrict__ out0 = nullptr) {
+  constexpr bool kHid = MODE == kHidden || MODE == kFused;  // relu(conv + bias) epilogue
+  constexpr int kMma = kTcEpi + tc_nprod(MODE);             // the MMA issuer warp
   constexpr int NCO = MODE == kLast ? 16 : 32;  // output channels per row accumulator
   constexpr int WCG = 3 * NCO * 16;              // weight bytes per (dx, channel group)
   constexpr int WDX = 4 * WCG;                   // weight bytes per dx
@@ -440,12 +473,12 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
       cp_async16(s_w + dx * WDX + j * WCG + dy * NCO * 16 + co * 16, wt + (t * 32 + co) * 32 + j * 8, true);
     }
   }
-  if (MODE == kHidden && tid < 32) s_bias[tid] = bias[tid];
+  if (kHid && tid < 32) s_bias[tid] = bias[tid];
   if (MODE == kLast && tid == 0) s_bias[0] = bias[0];
   if (tid == 0) {
     *abort_blk = 0;
     for (int i = 0; i < STAGES; ++i) {
-      tc_mbar_init(full(i), 1);
+      tc_mbar_init(full(i), MODE == kFused ? 32 * tc_nprod(MODE) : 1);
       tc_mbar_init(empty(i), 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -454,7 +487,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kTcEpi + 1) {
+  if (warp == kMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
         (uint32_t)__cvta_generic_to_shared(tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -488,7 +521,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
     y0 = (rem / ntx) * R;
     x0 = (rem % ntx) * kTcOut;
   };
-  if (warp == kTcEpi) {
+  if (MODE != kFused && warp == kTcEpi) {
     // ---- producer: one TMA copy of the halo per tile ----
     // (one bulk copy per channel group and halo row instead lost by 2.1x)
     if (lane == 0) {
@@ -509,7 +542,113 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
         }
       }
     }
-  } else if (warp == kTcEpi + 1) {
+  } else if (MODE == kFused && warp >= kTcEpi && warp < kMma) {
+    // ---- builders (kFused): the first layer's output over the tile's halo ----
+    const int bt = tid - 32 * kTcEpi, g = lane >> 2, tq = lane & 3;
+    const int bw = warp - kTcEpi;  // 0 .. 3
+    constexpr int NPRE = tc_fx_pre(R), XROWS = R + kFxR, XVALS = XROWS * kFxC;
+    uint16_t *xs = reinterpret_cast<uint16_t *>(smem + tc_smem(R));
+    unsigned char *hs = smem + kTcWBytes;  // generic address of the ring
+    const uint16_t *w1u = reinterpret_cast<const uint16_t *>(w1);
+    uint32_t bf[4][2];  // B fragments: B[k][co] = w1[tap k][co] for k < 9, zero above
+    float2 bs[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int co = 8 * n + g;
+      bf[n][0] = pack_u16(w1u[(2 * tq) * 32 + co], w1u[(2 * tq + 1) * 32 + co]);
+      bf[n][1] = tq == 0 ? pack_u16(w1u[8 * 32 + co], 0) : 0u;
+      bs[n] = make_float2(b1[8 * n + 2 * tq], b1[8 * n + 2 * tq + 1]);
+    }
+    const int o0 = ((2 * tq) / 3) * kFxP + (2 * tq) % 3, o1 = ((2 * tq + 1) / 3) * kFxP + (2 * tq + 1) % 3;
+    constexpr int o8 = 2 * kFxP + 2;
+    const long long HWp = (long long)H * W;
+    auto bar_b = [] { asm volatile("bar.sync 1, %0;" ::"n"(32 * tc_nprod(MODE)) : "memory"); };
+    // barrier of the builders that returns whether any of them saw the abort
+    // flag (one decision for all four warps)
+    auto bar_b_abort = [&]() -> bool {
+      uint32_t any;
+      asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+                   : "=r"(any)
+                   : "r"((uint32_t)*abort_blk), "n"(32 * tc_nprod(MODE))
+                   : "memory");
+      return any != 0;
+    };
+    // this thread's share of tile t's x halo (rows y0 - 2 .., columns x0 - 2 ..), bf16 bits
+    auto fetch = [&](long long t, uint16_t *v) {
+      int img, y0, x0;
+      tile_xy(t, img, y0, x0);
+      const float *src = x1 + (long long)img * HWp;
+#pragma unroll
+      for (int k = 0; k < NPRE; ++k) {
+        const int i = bt + 128 * k, r = i / kFxC;
+        const int yy = y0 - 2 + r, xx = x0 - 2 + (i - r * kFxC);
+        v[k] = (i < XVALS && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W)
+                   ? __bfloat16_as_ushort(__float2bfloat16(src[(long long)yy * W + xx]))
+                   : (uint16_t)0;
+      }
+    };
+    auto park = [&](const uint16_t *v) {
+#pragma unroll
+      for (int k = 0; k < NPRE; ++k) {
+        const int i = bt + 128 * k, r = i / kFxC;
+        if (i < XVALS) xs[r * kFxP + (i - r * kFxC)] = v[k];
+      }
+    };
+    uint16_t v[NPRE];
+    if ((long long)blockIdx.x < ntiles) {
+      fetch(blockIdx.x, v);
+      park(v);
+    }
+    bar_b();
+    int issued = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
+      const int s = issued % STAGES, u = issued / STAGES;
+      const long long tn = t + gridDim.x;
+      if (tn < ntiles) fetch(tn, v);  // in flight while this tile is built
+      if (u > 0) tc_wait(empty(s), (u - 1) & 1, abort_blk);
+      if (bar_b_abort()) break;
+      int img, y0, x0;
+      tile_xy(t, img, y0, x0);
+      unsigned char *st = hs + s * STAGE;
+      uint32_t *o32 = reinterpret_cast<uint32_t *>(out0);
+#pragma unroll 1
+      for (int sg = bw; sg < (R + 2) * (kTcHW / 16); sg += tc_nprod(MODE)) {
+        const int h = sg / (kTcHW / 16), i0 = (sg % (kTcHW / 16)) * 16;  // halo row, first pixel
+        const uint16_t *p0 = xs + h * kFxP + i0 + g, *p1 = p0 + 8;
+        uint32_t a[4];
+        a[0] = pack_u16(p0[o0], p0[o1]);
+        a[1] = pack_u16(p1[o0], p1[o1]);
+        a[2] = tq == 0 ? (uint32_t)p0[o8] : 0u;
+        a[3] = tq == 0 ? (uint32_t)p1[o8] : 0u;
+        float d[4][4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          d[n][0] = d[n][2] = bs[n].x;
+          d[n][1] = d[n][3] = bs[n].y;
+          mma16816(d[n], a, bf[n]);
+        }
+        const int yy = y0 - 1 + h;
+        const bool yin = (unsigned)yy < (unsigned)H, yown = h >= 1 && h <= R && yin;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {  // pixels g (hh = 0) and g + 8
+          const int i = i0 + g + 8 * hh, xx = x0 - 1 + i;
+          const bool in = yin && (unsigned)xx < (unsigned)W;
+          const bool own = o32 && yown && i >= 1 && i <= kTcOut && xx < W;
+#pragma unroll
+          for (int n = 0; n < 4; ++n) {
+            const uint32_t r = in ? cvt_bf16x2<true>(d[n][2 * hh], d[n][2 * hh + 1]) : 0u;
+            *reinterpret_cast<uint32_t *>(st + n * PLANE + (h * kTcHW + i) * 16 + 4 * tq) = r;
+            if (own) o32[(((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 4 + tq] = r;
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_arrive(full(s));
+      bar_b();  // every builder is done with the parked halo
+      if (tn < ntiles) park(v);
+      bar_b();
+    }
+  } else if (warp == kMma) {
     // ---- MMA issuer ----
     if (lane == 0) {
       int k = 0;
@@ -597,7 +736,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
         const int yy = y0 + rr;
         if (yy < H && xx < W) {
           const long long pix = (long long)yy * W + xx;
-          if (MODE == kHidden) {
+          if (kHid) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + s_bias[c], 0.f);
           } else {
@@ -632,7 +771,7 @@ __global__ void __launch_bounds__(32 * (kTcEpi + 2), 1) k_conv_tc(const __grid_c
   __syncthreads();
   if (tid == 0 && *abort_blk) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == kTcEpi + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  if (warp == kMma) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // ldmatrix of four 8 x 8 bf16 matrices, transposed (rows given by lanes 8j .. 8j + 7).
@@ -1064,6 +1203,8 @@ void set_attrs() {
   cudaFuncSetAttribute(k_conv_tc<kHidden, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
+  cudaFuncSetAttribute(k_conv_tc<kFused, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tc_smem_mode(kFused, kTcR));
   cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
   cudaFuncSetAttribute(k_conv_wgrad1<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   cudaFuncSetAttribute(k_conv_wgrad1<true, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
@@ -1184,9 +1325,51 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
   if (!act_map(&tin, in, nimg, H, W, kTcR + 2)) return false;
-  k_conv_tc<MODE, kTcR><<<grid, 32 * (kTcEpi + 2), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
-                                                                       H, W, tc_err_dev);
+  k_conv_tc<MODE, kTcR><<<grid, tc_threads(MODE), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
+                                                                      H, W, tc_err_dev);
   return true;
+}
+
+// The first two layers in one launch (kFused): x (fp32) -> act1; act0 is
+// stored to out0 when it is not null.
+void launch_conv_fused(const float *x, const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2,
+                       const float *b2, __nv_bfloat16 *out0, __nv_bfloat16 *out, int nimg, int H, int W,
+                       cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + kTcR - 1) / kTcR) * nimg;
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  CUtensorMap unused;  // the fused mode builds its operand instead of copying it
+  memset(&unused, 0, sizeof unused);
+  k_conv_tc<kFused, kTcR><<<grid, tc_threads(kFused), tc_smem_mode(kFused, kTcR), s>>>(
+      unused, w2, b2, nullptr, out, nullptr, nullptr, nimg, H, W, tc_err_dev, x, w1, b1, out0);
+}
+
+// The network's forward pass; `keep` stores what the backward pass reads
+// (the bf16 input and the first layer's output).
+int cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_dev, float *y_dev, void *ws_dev,
+                void *stream, bool keep, const char *who) {
+  if (!params_dev || !x_dev || !y_dev || !ws_dev || nimg < 1 || H < 1 || W < 1)
+    return rbc::set_error(RBC_EINVAL, who);
+  if (int rc = tc_err()) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long npx = (long long)nimg * H * W;
+  Ws w = carve(ws_dev, npx);
+  k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
+  if (keep) k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
+  set_attrs();
+  launch_conv_fused(x_dev, w.wf + kW1, params_dev + kB1, w.wf + kW2, params_dev + kB2, keep ? w.act[0] : nullptr,
+                    w.act[1], nimg, H, W, s);
+  bool ok_tc = true;
+  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
+  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
+  ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
+                                         y_dev, x_dev);
+  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: launch failed");
+  rbc::add_launches(keep ? 6 : 5);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
+  return RBC_OK;
 }
 
 } // namespace
@@ -1199,28 +1382,12 @@ long long rbc_cnn_workspace_bytes(int nimg, int H, int W) { return (long long)ws
 
 int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_dev, float *y_dev, void *ws_dev,
                     void *stream) {
-  if (!params_dev || !x_dev || !y_dev || !ws_dev || nimg < 1 || H < 1 || W < 1)
-    return rbc::set_error(RBC_EINVAL, "rbc_cnn_forward: bad arguments");
-  if (int rc = tc_err()) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  const long long npx = (long long)nimg * H * W;
-  Ws w = carve(ws_dev, npx);
-  k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
-  k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
-  set_attrs();
-  k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, smem_1to32<kHidden>(), s>>>(
-      w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], nimg, H, W);
-  bool ok_tc = true;
-  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
-  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
-  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
-  ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
-                                         y_dev, x_dev);
-  if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: launch failed");
-  rbc::add_launches(7);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
-  return RBC_OK;
+  return cnn_forward(params_dev, nimg, H, W, x_dev, y_dev, ws_dev, stream, true, "rbc_cnn_forward: bad arguments");
+}
+
+int rbc_cnn_infer(const float *params_dev, int nimg, int H, int W, const float *x_dev, float *y_dev, void *ws_dev,
+                  void *stream) {
+  return cnn_forward(params_dev, nimg, H, W, x_dev, y_dev, ws_dev, stream, false, "rbc_cnn_infer: bad arguments");
 }
 
 int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const float *dy_dev, float *grad_dev, void *ws_dev,

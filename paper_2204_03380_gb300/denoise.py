@@ -54,7 +54,7 @@ class Denoiser:
         """x: (n, H, W) fp32 CUDA -> denoised images."""
         x = x.contiguous()
         y = torch.empty_like(x)
-        N.rbc_cnn_forward(self.params, x, y, self._workspace(*x.shape))
+        N.rbc_cnn_infer(self.params, x, y, self._workspace(*x.shape))
         return y
 
     def train_step(self, x, t, lr=1e-3) -> torch.Tensor:

@@ -90,6 +90,8 @@ def test_bad_arguments_are_rejected_on_the_host():
     p16 = C.c_void_p(16)
     assert lib.rbc_cnn_forward(None, 1, 8, 8, p16, p16, p16, None) == 1
     assert lib.rbc_cnn_forward(p16, 0, 8, 8, p16, p16, p16, None) == 1
+    assert lib.rbc_cnn_infer(p16, 1, 8, 8, None, p16, p16, None) == 1
+    assert lib.rbc_cnn_infer(p16, 1, 8, 0, p16, p16, p16, None) == 1
     assert lib.rbc_cnn_backward(p16, 1, 0, 8, p16, p16, p16, None) == 1
     assert lib.rbc_cnn_mse(p16, p16, C.c_longlong(0), None, p16, None) == 1
     assert lib.rbc_cnn_adam(p16, p16, p16, p16, C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999),

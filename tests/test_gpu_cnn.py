@@ -16,7 +16,7 @@ def bf16(a):
     return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 37, 70), (2, 45, 300)])
+@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 37, 70), (2, 45, 300), (1, 9, 253)])
 def test_cnn_forward_and_gradient_match_oracle(shape):
     import paper_2204_03380_gb300 as R
     rng = np.random.default_rng(sum(shape))
@@ -40,6 +40,13 @@ def test_cnn_forward_and_gradient_match_oracle(shape):
     G = torch.zeros_like(P)
     R.rbc_cnn_backward(P, dY, G, ws)
     torch.cuda.synchronize()
+    # inference: the first layer built inside the second layer's kernel, the
+    # same operations as the training forward, so the same bits
+    Yi = torch.full_like(X, float("nan"))
+    wsi = torch.empty_like(ws)
+    R.rbc_cnn_infer(P, X, Yi, wsi)
+    torch.cuda.synchronize()
+    assert torch.equal(Yi, Y)
     assert R.rbc_cnn_param_count() == p.size
     assert rel(Y.cpu().numpy(), y_o) <= 1e-2
     assert float(loss) == pytest.approx(cnn.mse(y_o, t), rel=2e-2)
