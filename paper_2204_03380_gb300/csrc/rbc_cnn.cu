@@ -573,8 +573,9 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
                    : "memory");
       return any != 0;
     };
-    // this thread's share of tile t's x halo (rows y0 - 2 .., columns x0 - 2 ..), bf16 bits
-    auto fetch = [&](long long t, uint16_t *v) {
+    // this thread's share of tile t's x halo (rows y0 - 2 .., columns x0 - 2
+    // ..), left in flight as fp32 until park() rounds and stores it
+    auto fetch = [&](long long t, float *v) {
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
       const float *src = x1 + (long long)img * HWp;
@@ -582,19 +583,18 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
       for (int k = 0; k < NPRE; ++k) {
         const int i = bt + 128 * k, r = i / kFxC;
         const int yy = y0 - 2 + r, xx = x0 - 2 + (i - r * kFxC);
-        v[k] = (i < XVALS && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W)
-                   ? __bfloat16_as_ushort(__float2bfloat16(src[(long long)yy * W + xx]))
-                   : (uint16_t)0;
+        v[k] = (i < XVALS && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W) ? src[(long long)yy * W + xx]
+                                                                                       : 0.f;
       }
     };
-    auto park = [&](const uint16_t *v) {
+    auto park = [&](const float *v) {
 #pragma unroll
       for (int k = 0; k < NPRE; ++k) {
         const int i = bt + 128 * k, r = i / kFxC;
-        if (i < XVALS) xs[r * kFxP + (i - r * kFxC)] = v[k];
+        if (i < XVALS) xs[r * kFxP + (i - r * kFxC)] = __bfloat16_as_ushort(__float2bfloat16(v[k]));
       }
     };
-    uint16_t v[NPRE];
+    float v[NPRE];
     if ((long long)blockIdx.x < ntiles) {
       fetch(blockIdx.x, v);
       park(v);
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
       tile_xy(t, img, y0, x0);
       unsigned char *st = hs + s * STAGE;
       uint32_t *o32 = reinterpret_cast<uint32_t *>(out0);
-#pragma unroll 1
+#pragma unroll 2
       for (int sg = bw; sg < (R + 2) * (kTcHW / 16); sg += tc_nprod(MODE)) {
         const int h = sg / (kTcHW / 16), i0 = (sg % (kTcHW / 16)) * 16;  // halo row, first pixel
         const uint16_t *p0 = xs + h * kFxP + i0 + g, *p1 = p0 + 8;
