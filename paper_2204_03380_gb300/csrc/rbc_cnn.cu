@@ -389,8 +389,7 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 //   MODE kBackData: out = conv(in) * (mask > 0)   (weights mirrored and transposed)
 //   MODE kLast:     out_f = resid + conv(in) + bias                    (32 -> 1)
 //   MODE kFused:    out = relu(conv(a1) + bias) with a1 = relu(conv1(x1) + b1)
-//                   computed in the block (the first two layers; a1 stored
-//                   to out0 when out0 is not null)
+//                   computed in the block (the first two layers, for inference)
 // The last layer's single output channel is padded to N = 16 per output row
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
@@ -399,26 +398,26 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // starting at row (e / 4) * R * 4 / kTcEpi); warps kTcEpi .. kTcEpi +
 // tc_nprod(MODE) - 1 are the producers, the next warp the MMA issuer.
 //
-// kFused: instead of the tensor copy of a stored first-layer output, four
-// builder warps compute it over the tile's halo (R + 2 rows x 128 pixels)
-// into the ring stage, in the layout the copy would have produced: the fp32
-// one-channel input's halo (R + 4 rows x 130 pixels, prefetched a tile
-// ahead into registers, rounded to bf16) is parked in shared memory, and
-// each 16 pixels of a halo row are one m16n8k16 MMA per 8 channels as in
-// k_conv_1to32 (taps padded to K = 16, bias as the accumulator's start,
-// relu and rounding in one conversion), stored as 4-byte pieces of the
-// pixels' 16-byte channel groups; outside the image the stage holds zeros
-// (the second layer's padding).  The builders then make their writes visible
-// to the tensor cores and arrive on the stage's "full" barrier.  The first
-// layer's output never passes through global memory unless out0 asks for it
-// (the training pass keeps it for the backward pass).
-constexpr int tc_nprod(int mode) { return mode == kFused ? 4 : 1; }
+// kFused: instead of the tensor copy of a stored first-layer output, five
+// builder warps compute it over the tile's halo (R + 2 rows x 128 pixels,
+// two rows per warp) into the ring stage, in the layout the copy would have
+// produced: the fp32 one-channel input's halo (R + 4 rows x 130 pixels,
+// prefetched a tile ahead into registers, rounded to bf16) is parked in
+// shared memory, and each 16 pixels of a halo row are one m16n8k16 MMA per 8
+// channels as in k_conv_1to32 (taps padded to K = 16, bias as the
+// accumulator's start, relu and rounding in one conversion), stored as
+// 4-byte pieces of the pixels' 16-byte channel groups at constant offsets
+// from the row's base; outside the image the stage holds zeros (the second
+// layer's padding).  The builders then make their writes visible to the
+// tensor cores and arrive on the stage's "full" barrier.  The first layer's
+// output never passes through global memory.
+constexpr int tc_nprod(int mode) { return mode == kFused ? 5 : 1; }
 constexpr int tc_threads(int mode) { return 32 * (kTcEpi + tc_nprod(mode) + 1); }
 constexpr int kFxR = 4;                  // x halo rows beyond the tile's R (two on each side)
 constexpr int kFxC = kTcHW + 2;          // x halo columns (x0 - 2 .. x0 + 127)
 constexpr int kFxP = 144;                // x halo row pitch (2-byte values; conflict-free gathers)
 constexpr int tc_fx_bytes(int R) { return (R + kFxR) * kFxP * 2; }
-constexpr int tc_fx_pre(int R) { return ((R + kFxR) * kFxC + 127) / 128; }  // x values per builder thread
+#define XVALS_OF(R) (((R) + kFxR) * kFxC)  // x halo values of a tile
 constexpr int tc_smem_mode(int mode, int R) { return tc_smem(R) + (mode == kFused ? tc_fx_bytes(R) : 0); }
 static_assert(tc_smem(kTcR) + tc_fx_bytes(kTcR) <= 227 * 1024, "the fused ring must fit in shared memory");
 
@@ -431,8 +430,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
                                                     const float *__restrict__ resid, int nimg, int H, int W,
                                                     int *err, const float *__restrict__ x1 = nullptr,
                                                     const __nv_bfloat16 *__restrict__ w1 = nullptr,
-                                                    const float *__restrict__ b1 = nullptr,
-                                                    __nv_bfloat16 *__restrict__ out0 = nullptr) {
+                                                    const float *__restrict__ b1 = nullptr) {
   constexpr bool kHid = MODE == kHidden || MODE == kFused;  // relu(conv + bias) epilogue
   constexpr int kMma = kTcEpi + tc_nprod(MODE);             // the MMA issuer warp
   constexpr int NCO = MODE == kLast ? 16 : 32;  // output channels per row accumulator
@@ -544,9 +542,12 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
     }
   } else if (MODE == kFused && warp >= kTcEpi && warp < kMma) {
     // ---- builders (kFused): the first layer's output over the tile's halo ----
+    constexpr int NB = tc_nprod(MODE), NBT = 32 * NB;                    // builder warps, threads
+    constexpr int NPRE = (XVALS_OF(R) + NBT - 1) / NBT;                 // x values per builder thread
+    constexpr int XVALS = XVALS_OF(R);
+    static_assert((R + 2) % NB == 0, "each builder warp owns the same number of halo rows");
     const int bt = tid - 32 * kTcEpi, g = lane >> 2, tq = lane & 3;
-    const int bw = warp - kTcEpi;  // 0 .. 3
-    constexpr int NPRE = tc_fx_pre(R), XROWS = R + kFxR, XVALS = XROWS * kFxC;
+    const int bw = warp - kTcEpi;
     uint16_t *xs = reinterpret_cast<uint16_t *>(smem + tc_smem(R));
     unsigned char *hs = smem + kTcWBytes;  // generic address of the ring
     const uint16_t *w1u = reinterpret_cast<const uint16_t *>(w1);
@@ -562,14 +563,14 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
     const int o0 = ((2 * tq) / 3) * kFxP + (2 * tq) % 3, o1 = ((2 * tq + 1) / 3) * kFxP + (2 * tq + 1) % 3;
     constexpr int o8 = 2 * kFxP + 2;
     const long long HWp = (long long)H * W;
-    auto bar_b = [] { asm volatile("bar.sync 1, %0;" ::"n"(32 * tc_nprod(MODE)) : "memory"); };
+    auto bar_b = [] { asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory"); };
     // barrier of the builders that returns whether any of them saw the abort
-    // flag (one decision for all four warps)
+    // flag (one decision for all of them)
     auto bar_b_abort = [&]() -> bool {
       uint32_t any;
       asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
                    : "=r"(any)
-                   : "r"((uint32_t)*abort_blk), "n"(32 * tc_nprod(MODE))
+                   : "r"((uint32_t)*abort_blk), "n"(NBT)
                    : "memory");
       return any != 0;
     };
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
       const float *src = x1 + (long long)img * HWp;
 #pragma unroll
       for (int k = 0; k < NPRE; ++k) {
-        const int i = bt + 128 * k, r = i / kFxC;
+        const int i = bt + NBT * k, r = i / kFxC;
         const int yy = y0 - 2 + r, xx = x0 - 2 + (i - r * kFxC);
         v[k] = (i < XVALS && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W) ? src[(long long)yy * W + xx]
                                                                                        : 0.f;
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
     auto park = [&](const float *v) {
 #pragma unroll
       for (int k = 0; k < NPRE; ++k) {
-        const int i = bt + 128 * k, r = i / kFxC;
+        const int i = bt + NBT * k, r = i / kFxC;
         if (i < XVALS) xs[r * kFxP + (i - r * kFxC)] = __bfloat16_as_ushort(__float2bfloat16(v[k]));
       }
     };
@@ -609,36 +610,41 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
       if (bar_b_abort()) break;
       int img, y0, x0;
       tile_xy(t, img, y0, x0);
-      unsigned char *st = hs + s * STAGE;
-      uint32_t *o32 = reinterpret_cast<uint32_t *>(out0);
-#pragma unroll 2
-      for (int sg = bw; sg < (R + 2) * (kTcHW / 16); sg += tc_nprod(MODE)) {
-        const int h = sg / (kTcHW / 16), i0 = (sg % (kTcHW / 16)) * 16;  // halo row, first pixel
-        const uint16_t *p0 = xs + h * kFxP + i0 + g, *p1 = p0 + 8;
-        uint32_t a[4];
-        a[0] = pack_u16(p0[o0], p0[o1]);
-        a[1] = pack_u16(p1[o0], p1[o1]);
-        a[2] = tq == 0 ? (uint32_t)p0[o8] : 0u;
-        a[3] = tq == 0 ? (uint32_t)p1[o8] : 0u;
-        float d[4][4];
+#pragma unroll 1
+      for (int h = bw; h < R + 2; h += NB) {  // halo row h: image row y0 - 1 + h
+        // this lane's 4-byte piece of pixel (h, g) in channel group 0
+        unsigned char *row = hs + s * STAGE + (h * kTcHW + g) * 16 + 4 * tq;
+        if ((unsigned)(y0 - 1 + h) >= (unsigned)H) {  // outside the image: the second layer's zero padding
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          d[n][0] = d[n][2] = bs[n].x;
-          d[n][1] = d[n][3] = bs[n].y;
-          mma16816(d[n], a, bf[n]);
+          for (int i = 0; i < kTcHW; i += 8)
+#pragma unroll
+            for (int n = 0; n < 4; ++n) *reinterpret_cast<uint32_t *>(row + n * PLANE + i * 16) = 0u;
+          continue;
         }
-        const int yy = y0 - 1 + h;
-        const bool yin = (unsigned)yy < (unsigned)H, yown = h >= 1 && h <= R && yin;
+        const uint16_t *xr = xs + h * kFxP + g;
+        const int xg = x0 - 1 + g;  // image column of pixel (h, g)
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {  // pixels g (hh = 0) and g + 8
-          const int i = i0 + g + 8 * hh, xx = x0 - 1 + i;
-          const bool in = yin && (unsigned)xx < (unsigned)W;
-          const bool own = o32 && yown && i >= 1 && i <= kTcOut && xx < W;
+        for (int i0 = 0; i0 < kTcHW; i0 += 16) {
+          const uint16_t *p0 = xr + i0, *p1 = p0 + 8;
+          uint32_t a[4];
+          a[0] = pack_u16(p0[o0], p0[o1]);
+          a[1] = pack_u16(p1[o0], p1[o1]);
+          a[2] = tq == 0 ? (uint32_t)p0[o8] : 0u;
+          a[3] = tq == 0 ? (uint32_t)p1[o8] : 0u;
+          float d[4][4];
 #pragma unroll
           for (int n = 0; n < 4; ++n) {
-            const uint32_t r = in ? cvt_bf16x2<true>(d[n][2 * hh], d[n][2 * hh + 1]) : 0u;
-            *reinterpret_cast<uint32_t *>(st + n * PLANE + (h * kTcHW + i) * 16 + 4 * tq) = r;
-            if (own) o32[(((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 4 + tq] = r;
+            d[n][0] = d[n][2] = bs[n].x;
+            d[n][1] = d[n][3] = bs[n].y;
+            mma16816(d[n], a, bf[n]);
+          }
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {  // pixels g (hh = 0) and g + 8
+            const bool in = (unsigned)(xg + i0 + 8 * hh) < (unsigned)W;
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+              *reinterpret_cast<uint32_t *>(row + n * PLANE + (i0 + 8 * hh) * 16) =
+                  in ? cvt_bf16x2<true>(d[n][2 * hh], d[n][2 * hh + 1]) : 0u;
           }
         }
       }
@@ -1330,11 +1336,9 @@ bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const floa
   return true;
 }
 
-// The first two layers in one launch (kFused): x (fp32) -> act1; act0 is
-// stored to out0 when it is not null.
+// The first two layers in one launch (kFused): x (fp32) -> act1.
 void launch_conv_fused(const float *x, const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2,
-                       const float *b2, __nv_bfloat16 *out0, __nv_bfloat16 *out, int nimg, int H, int W,
-                       cudaStream_t s) {
+                       const float *b2, __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + kTcR - 1) / kTcR) * nimg;
@@ -1342,11 +1346,12 @@ void launch_conv_fused(const float *x, const __nv_bfloat16 *w1, const float *b1,
   CUtensorMap unused;  // the fused mode builds its operand instead of copying it
   memset(&unused, 0, sizeof unused);
   k_conv_tc<kFused, kTcR><<<grid, tc_threads(kFused), tc_smem_mode(kFused, kTcR), s>>>(
-      unused, w2, b2, nullptr, out, nullptr, nullptr, nimg, H, W, tc_err_dev, x, w1, b1, out0);
+      unused, w2, b2, nullptr, out, nullptr, nullptr, nimg, H, W, tc_err_dev, x, w1, b1);
 }
 
 // The network's forward pass; `keep` stores what the backward pass reads
-// (the bf16 input and the first layer's output).
+// (the bf16 input and the first layer's output: two launches for the first
+// two layers); without it the first two layers are one fused launch.
 int cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_dev, float *y_dev, void *ws_dev,
                 void *stream, bool keep, const char *who) {
   if (!params_dev || !x_dev || !y_dev || !ws_dev || nimg < 1 || H < 1 || W < 1)
@@ -1358,15 +1363,20 @@ int cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_
   k_prep_weights<<<36, 256, 0, s>>>(params_dev, w.wf, w.wb);
   if (keep) k_to_bf16<<<grid_of(npx), 256, 0, s>>>(x_dev, w.x0, npx);
   set_attrs();
-  launch_conv_fused(x_dev, w.wf + kW1, params_dev + kB1, w.wf + kW2, params_dev + kB2, keep ? w.act[0] : nullptr,
-                    w.act[1], nimg, H, W, s);
   bool ok_tc = true;
+  if (keep) {  // the backward pass reads the first layer's output
+    k_conv_1to32<kHidden><<<grid_1to32<kHidden>(nimg, H, W), 256, smem_1to32<kHidden>(), s>>>(
+        w.x0, w.wf + kW1, params_dev + kB1, nullptr, w.act[0], nimg, H, W);
+    ok_tc = launch_conv_tc<kHidden>(w.act[0], w.wf + kW2, params_dev + kB2, nullptr, w.act[1], nimg, H, W, s);
+  } else {
+    launch_conv_fused(x_dev, w.wf + kW1, params_dev + kB1, w.wf + kW2, params_dev + kB2, w.act[1], nimg, H, W, s);
+  }
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
                                          y_dev, x_dev);
   if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: launch failed");
-  rbc::add_launches(keep ? 6 : 5);
+  rbc::add_launches(keep ? 7 : 5);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
   return RBC_OK;
