@@ -398,9 +398,9 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // starting at row (e / 4) * R * 4 / kTcEpi); warps kTcEpi .. kTcEpi +
 // tc_nprod(MODE) - 1 are the producers, the next warp the MMA issuer.
 //
-// kFused: instead of the tensor copy of a stored first-layer output, five
+// kFused: instead of the tensor copy of a stored first-layer output, ten
 // builder warps compute it over the tile's halo (R + 2 rows x 128 pixels,
-// two rows per warp) into the ring stage, in the layout the copy would have
+// one row per warp) into the ring stage, in the layout the copy would have
 // produced: the fp32 one-channel input's halo (R + 4 rows x 130 pixels,
 // prefetched a tile ahead into registers, rounded to bf16) is parked in
 // shared memory, and each 16 pixels of a halo row are one m16n8k16 MMA per 8
@@ -411,7 +411,7 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // layer's padding).  The builders then make their writes visible to the
 // tensor cores and arrive on the stage's "full" barrier.  The first layer's
 // output never passes through global memory.
-constexpr int tc_nprod(int mode) { return mode == kFused ? 5 : 1; }
+constexpr int tc_nprod(int mode) { return mode == kFused ? 10 : 1; }
 constexpr int tc_threads(int mode) { return 32 * (kTcEpi + tc_nprod(mode) + 1); }
 constexpr int kFxR = 4;                  // x halo rows beyond the tile's R (two on each side)
 constexpr int kFxC = kTcHW + 2;          // x halo columns (x0 - 2 .. x0 + 127)
