@@ -138,25 +138,46 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
 }
 
 // Tiled form of the fused reverse step: one block of 4 warps per work item of
-// 128 columns x 8 rows (2 per warp), non-persistent (a grid of the group's
-// items), with the current levels of both fields over the item and its halo
-// and the item's imaging accumulators staged in shared memory by cp.async
-// before a single barrier, as in the single-shot k_rev2d_tile.
+// 128 columns x 8 rows (2 per warp), non-persistent (a grid of the items of
+// up to kBGMax consecutive shots), with the current levels of both fields
+// over the item and its halo and the item's imaging accumulators staged in
+// shared memory by cp.async before a single barrier, as in the single-shot
+// k_rev2d_tile.  What a block needs before it can stage (the shots' layouts,
+// field pointers, tile counts and image boxes, which stay fixed for the life
+// of the batch) is a kernel parameter: the item's shot is found from the
+// shots' first items, with no dependent loads from global memory; the
+// per-call part (source offset, receivers, records) is read from the shot
+// descriptors in global memory, the source offset before the wait for the
+// previous step.
 constexpr int kBTileW = 4, kBTileRZ = 2, kBTileT = kBTileW * kBTileRZ;
-__global__ void __launch_bounds__(32 * kBTileW, 7) k_rev2d_batch_tile(const BShot *__restrict__ shots,
-                                                                      const int *__restrict__ item_shot, int item0,
-                                                                      int n, int nt, const float *__restrict__ wav,
-                                                                      float src_scale, float rec_scale) {
+constexpr int kBGMax = 16;  // shots per launch of the tiled reverse
+struct BRevShot {
+  Lay L;
+  float *a, *p0, *p1, *q0, *q1, *num, *den;
+  int gx, ix0, ix1, iz0, iz1;
+};
+struct BRevGroup {
+  int nshot, shot0;           // shots shot0 .. shot0 + nshot - 1 of the batch
+  int tbase[kBGMax + 1];      // first item of each shot in this launch, then the item count
+  BRevShot s[kBGMax];
+};
+__global__ void __launch_bounds__(32 * kBTileW, 7) k_rev2d_batch_tile(const __grid_constant__ BRevGroup G,
+                                                                      const BShot *__restrict__ shots, int n, int nt,
+                                                                      const float *__restrict__ wav, float src_scale,
+                                                                      float rec_scale) {
   constexpr int T = kBTileT, RZ = kBTileRZ;
   __shared__ __align__(16) float s_r[(T + 8) * kStRow], s_b[(T + 8) * kStRow];
   __shared__ __align__(16) float s_num[T * kTileX], s_den[T * kTileX];
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
   const bool do_r = n < nt && n > 0, do_b = n > 0;
-  const int t = item0 + blockIdx.x;
-  griddep_wait();
-  const BShot &S = shots[__ldg(item_shot + t)];
+  const int t = blockIdx.x;
+  int si = 0;
+  while (si + 1 < G.nshot && t >= G.tbase[si + 1]) ++si;
+  const BRevShot &S = G.s[si];
+  const BShot &D = shots[G.shot0 + si];
+  const int src = D.src_off;  // in flight during the wait
   const Lay &L = S.L;
-  const int loc = t - S.tbase_r;
+  const int loc = t - G.tbase[si];
   const int X0 = (loc % S.gx) * kTileX, Z0 = (loc / S.gx) * T;
   const int x0 = X0 + lane * 4, zb = Z0 + w * RZ;
   const bool xok = x0 < L.NX4;
@@ -165,9 +186,10 @@ __global__ void __launch_bounds__(32 * kBTileW, 7) k_rev2d_batch_tile(const BSho
   float *rn = (n & 1) ? S.p0 : S.p1;
   const float *bc = (n & 1) ? S.q1 : S.q0;
   float *bn = (n & 1) ? S.q0 : S.q1;
+  const bool img_tile = Z0 < S.iz1 && Z0 + T > S.iz0 && X0 < S.ix1 && X0 + kTileX > S.ix0;
+  griddep_wait();
   stage_rows<T>(L, rc, s_r, X0, Z0, tid, 32 * kBTileW);
   stage_rows<T>(L, bc, s_b, X0, Z0, tid, 32 * kBTileW);
-  const bool img_tile = Z0 < S.iz1 && Z0 + T > S.iz0 && X0 < S.ix1 && X0 + kTileX > S.ix0;
   if (img_tile) {
     stage_own<T>(L, S.num, s_num, X0, Z0, tid, 32 * kBTileW);
     stage_own<T>(L, S.den, s_den, X0, Z0, tid, 32 * kBTileW);
@@ -184,7 +206,6 @@ __global__ void __launch_bounds__(32 * kBTileW, 7) k_rev2d_batch_tile(const BSho
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  const int src = S.src_off;
   const float fsrc = do_r ? wav[n] * src_scale : 0.f;  // f[nt] does not exist
   const bool img = xok && x0 + 3 >= S.ix0 && x0 < S.ix1;
 #pragma unroll
@@ -210,14 +231,14 @@ __global__ void __launch_bounds__(32 * kBTileW, 7) k_rev2d_batch_tile(const BSho
   }
   // Eq. 2 source term at this item's receivers, after the block's stores
   if (do_b) {
-    const int beg = S.tile_ptr[loc], end = S.tile_ptr[loc + 1];
+    const int beg = D.tile_ptr[loc], end = D.tile_ptr[loc + 1];
     if (end > beg) {
       __threadfence();
       __syncthreads();
       for (int k = beg + tid; k < end; k += 32 * kBTileW) {
-        const int r = S.tile_rec[k];
-        const int o = S.rec_off[r];
-        atomicAdd(bn + o, rec_scale * S.a[o] * S.seis_t[(long long)n * S.nrec + r]);
+        const int r = D.tile_rec[k];
+        const int o = D.rec_off[r];
+        atomicAdd(bn + o, rec_scale * S.a[o] * D.seis_t[(long long)n * D.nrec + r]);
       }
     }
   }
@@ -698,11 +719,26 @@ bool launch_rev_b(rbc_batch *b, int n, cudaStream_t s, int i0 = 0, int i1 = -1) 
     launch_pdl(k_rev2d_batch<1>, dim3(std::min(b->grid_r, items)), blk, 0, s, (const BShot *)b->ds,
                (const int *)b->d_item_r, i0, i1, n, nt, (const float *)b->d_wav, 1.f, 1.f);
     break;
-  case 3:
-    if (items > 0)
-      launch_pdl(k_rev2d_batch_tile, dim3(items), dim3(32, kBTileW), 0, s, (const BShot *)b->ds,
-                 (const int *)b->d_item_r, i0, n, nt, (const float *)b->d_wav, 1.f, 1.f);
+  case 3: {
+    // the shots of the items [i0, i1) (whole shots), kBGMax per launch
+    int sh = 0;
+    while (sh < b->nshots && b->hs[sh].tbase_r < i0) ++sh;
+    while (sh < b->nshots && b->hs[sh].tbase_r < i1) {
+      BRevGroup G = {};
+      G.shot0 = sh;
+      const int base = b->hs[sh].tbase_r;
+      for (; G.nshot < kBGMax && sh < b->nshots && b->hs[sh].tbase_r < i1; ++sh, ++G.nshot) {
+        const BShot &H = b->hs[sh];
+        G.tbase[G.nshot] = H.tbase_r - base;
+        G.s[G.nshot] = BRevShot{H.L, H.a, H.p0, H.p1, H.q0, H.q1, H.num, H.den, H.gx, H.ix0, H.ix1, H.iz0, H.iz1};
+      }
+      const BShot &last = b->hs[G.shot0 + G.nshot - 1];
+      G.tbase[G.nshot] = last.tbase_r + last.gx * last.gzr - base;
+      launch_pdl(k_rev2d_batch_tile, dim3(G.tbase[G.nshot]), dim3(32, kBTileW), 0, s, G, (const BShot *)b->ds, n,
+                 nt, (const float *)b->d_wav, 1.f, 1.f);
+    }
     break;
+  }
   default:
     launch_pdl(k_rev2d_batch<2>, dim3(std::min(b->grid_r, items)), blk, 0, s, (const BShot *)b->ds,
                (const int *)b->d_item_r, i0, i1, n, nt, (const float *)b->d_wav, 1.f, 1.f);
@@ -828,7 +864,9 @@ int enq_rev(rbc_batch *b, int g, cudaStream_t s) {
 
 // One phase (kind 0 forward, 1 reverse) of group g, as its cached graph.
 int run_b(rbc_batch *b, int kind, int g, cudaStream_t s, long long *launches) {
-  const long long per = kind == 0 ? b->g.nt : b->g.nt + 1;
+  // the tiled reverse launches once per kBGMax shots of the group and step
+  const long long chunks = b->rzr == 3 ? cdiv(b->grp[g + 1] - b->grp[g], kBGMax) : 1;
+  const long long per = kind == 0 ? b->g.nt : (b->g.nt + 1) * chunks;
   if (!b->use_graph) {
     *launches += per;
     return kind == 0 ? enq_fwd(b, g, s) : enq_rev(b, g, s);

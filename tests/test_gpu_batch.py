@@ -121,3 +121,52 @@ def test_batch_rejects_bad_windows():
                         R.RBC_REINJECT_SOURCE, 1e-6, img)
     assert e.value.code == 1
     R.rbc_batch_destroy(b)
+
+
+def test_tiled_reverse_over_more_shots_than_one_launch_holds(monkeypatch):
+    """18 shots in one group: the tiled reverse takes at most 16 shots' tile
+    descriptors per launch, so each step is two launches (16 + 2 shots); the
+    batched image equals the single-shot path's."""
+    import paper_2204_03380_gb300 as R
+    monkeypatch.setenv("RBC_BATCH_TILES", "2,3")
+    w = W.scaled(W.BATCH_2D, nx=300, nz=40, nb=10, nt=150, name="batch_many")
+    w = W.dataclasses.replace(w, nshots=18)
+    inp = W.batch_2d_inputs(w, wmin=30, wmax=60, rec_step=3)
+    dev = "cuda"
+    wav = torch.tensor(inp["wavelet"], dtype=torch.float32, device=dev)
+    a_mig, seis = [], []
+    for sh in inp["shots"]:
+        g = _shot_grid(R, w, sh["width"])
+        at = torch.empty(g.padded, dtype=torch.float32, device=dev)
+        R.rbc_build_velocity(g, torch.tensor(_window(inp["v_true"], sh["off_x"], sh["width"]), device=dev),
+                             w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, at)
+        am = torch.empty_like(at)
+        R.rbc_build_velocity(g, torch.tensor(_window(inp["v_mig"], sh["off_x"], sh["width"]), device=dev),
+                             w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, am)
+        ctx = R.rbc_create(g, at)
+        d = torch.empty((len(sh["rec"]), w.nt + 1), dtype=torch.float32, device=dev)
+        R.rbc_model(ctx, sh["src"], wav, sh["rec"], d)
+        R.rbc_destroy(ctx)
+        a_mig.append(am)
+        seis.append(d)
+    b = R.rbc_batch_create(_shot_grid(R, w, 1), [sh["width"] for sh in inp["shots"]], a_mig)
+    info = R.rbc_batch_info(b)
+    assert info["rows_rev"] == 3 and info["groups"] == 1
+    img_b = torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)
+    shots = [dict(src=sh["src"], rec=sh["rec"], seis=d, off_x=sh["off_x"]) for sh, d in zip(inp["shots"], seis)]
+    R.rbc_batch_rtm(b, shots, wav, R.RBC_REINJECT_SOURCE, 1e-6, img_b)
+    torch.cuda.synchronize()
+    R.rbc_batch_destroy(b)
+    survey = R.make_grid(2, w.nx, 1, w.nz, w.nb, w.h, w.dt, w.nt)
+    img_s = torch.zeros_like(img_b)
+    for sh, a, d in zip(inp["shots"], a_mig, seis):
+        g = _shot_grid(R, w, sh["width"])
+        ctx = R.rbc_create(g, a)
+        num = torch.zeros(g.interior, dtype=torch.float32, device=dev)
+        den = torch.zeros_like(num)
+        R.rbc_rtm_shot(ctx, sh["src"], wav, sh["rec"], d, R.RBC_REINJECT_SOURCE, num, den)
+        R.rbc_image_stack(g, num, den, 1e-6, sh["off_x"], 0, survey, img_s)
+        R.rbc_destroy(ctx)
+    torch.cuda.synchronize()
+    assert float(img_s.abs().max()) > 0
+    assert rel(img_b.cpu().numpy(), img_s.cpu().numpy()) <= 1e-5
