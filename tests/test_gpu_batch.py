@@ -138,10 +138,12 @@ def test_tiled_reverse_over_more_shots_than_one_launch_holds(monkeypatch):
     for sh in inp["shots"]:
         g = _shot_grid(R, w, sh["width"])
         at = torch.empty(g.padded, dtype=torch.float32, device=dev)
-        R.rbc_build_velocity(g, torch.tensor(_window(inp["v_true"], sh["off_x"], sh["width"]), device=dev),
+        R.rbc_build_velocity(g, torch.tensor(_window(inp["v_true"], sh["off_x"], sh["width"]), dtype=torch.float32,
+                                             device=dev),
                              w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, at)
         am = torch.empty_like(at)
-        R.rbc_build_velocity(g, torch.tensor(_window(inp["v_mig"], sh["off_x"], sh["width"]), device=dev),
+        R.rbc_build_velocity(g, torch.tensor(_window(inp["v_mig"], sh["off_x"], sh["width"]), dtype=torch.float32,
+                                             device=dev),
                              w.v_lo, w.v_hi, w.v_max, w.rbc_seed, 0, None, am)
         ctx = R.rbc_create(g, at)
         d = torch.empty((len(sh["rec"]), w.nt + 1), dtype=torch.float32, device=dev)
