@@ -55,44 +55,26 @@ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 constexpr int kBWarpsF = 4;
 
 // ---------------------------------------------------------------- kernels --
-// What the forward blocks need of a shot before they can load its fields
-// (layout, field pointers, tile counts: fixed for the life of the batch), for
-// up to kBGMax consecutive shots, passed as a kernel parameter: an item's
-// shot is found from the shots' first items, with no dependent loads from
-// global memory; the per-call source offset comes from the shot descriptors
-// in global memory.
-constexpr int kBGMax = 16;  // shots per launch of the forward and the tiled reverse
-struct BFwdShot {
-  Lay L;
-  const float *a;
-  float *p0, *p1;
-  int gx;
-};
-struct BFwdGroup {
-  int nshot, shot0;       // shots shot0 .. shot0 + nshot - 1 of the batch
-  int tbase[kBGMax + 1];  // first item of each shot in this launch, then the item count
-  BFwdShot s[kBGMax];
-};
-
 template <int RZ>
-__global__ void __launch_bounds__(32 * kBWarpsF) k_fwd2d_batch(const __grid_constant__ BFwdGroup G,
-                                                                const BShot *__restrict__ shots, int n,
-                                                                const float *__restrict__ wav, float src_scale) {
+__global__ void __launch_bounds__(32 * kBWarpsF) k_fwd2d_batch(const BShot *__restrict__ shots,
+                                                                const int *__restrict__ item_shot, int item0,
+                                                                int item1, int n, const float *__restrict__ wav,
+                                                                float src_scale) {
   const int lane = threadIdx.x, w = threadIdx.y;
   griddep_wait();
   const float f = wav[n] * src_scale;
-  const int items = G.tbase[G.nshot];
-  int si = 0;
-  for (int t = blockIdx.x; t < items; t += gridDim.x) {
-    while (si + 1 < G.nshot && t >= G.tbase[si + 1]) ++si;  // items ascend within a block
-    const BFwdShot &S = G.s[si];
-    const int loc = t - G.tbase[si];
+  // the next item's shot index is fetched one item ahead
+  int sh = item0 + (int)blockIdx.x < item1 ? __ldg(item_shot + item0 + blockIdx.x) : 0;
+  for (int t = item0 + blockIdx.x; t < item1; t += gridDim.x) {
+    const BShot &S = shots[sh];
+    sh = t + (int)gridDim.x < item1 ? __ldg(item_shot + t + gridDim.x) : 0;
+    const int loc = t - S.tbase_f;
     const int bx = loc % S.gx, bz = loc / S.gx;
     const int zb = (bz * kBWarpsF + w) * RZ;
     if (zb >= S.L.NZ) continue;  // warp-uniform
     const float *cur = (n & 1) ? S.p1 : S.p0;
     float *nxt = (n & 1) ? S.p0 : S.p1;
-    fwd2d_rows<RZ>(S.L, S.a, cur, nxt, lane, bx * kTileX + lane * 4, zb, shots[G.shot0 + si].src_off, f);
+    fwd2d_rows<RZ>(S.L, S.a, cur, nxt, lane, bx * kTileX + lane * 4, zb, S.src_off, f);
   }
   griddep_launch();
 }
@@ -168,6 +150,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
 // descriptors in global memory, the source offset before the wait for the
 // previous step.
 constexpr int kBTileW = 4, kBTileRZ = 2, kBTileT = kBTileW * kBTileRZ;
+constexpr int kBGMax = 16;  // shots per launch of the tiled reverse
 struct BRevShot {
   Lay L;
   float *a, *p0, *p1, *q0, *q1, *num, *den;
@@ -704,30 +687,18 @@ bool launch_fwd_b(rbc_batch *b, int n, cudaStream_t s, int i0 = 0, int i1 = -1) 
                n, (const float *)b->d_wav, sc, b->err_dev);
     break;
   }
-  default: {
-    // the shots of the items [i0, i1) (whole shots), kBGMax per launch
-    int sh = 0;
-    while (sh < b->nshots && b->hs[sh].tbase_f < i0) ++sh;
-    while (sh < b->nshots && b->hs[sh].tbase_f < i1) {
-      BFwdGroup G = {};
-      G.shot0 = sh;
-      const int base = b->hs[sh].tbase_f;
-      for (; G.nshot < kBGMax && sh < b->nshots && b->hs[sh].tbase_f < i1; ++sh, ++G.nshot) {
-        const BShot &H = b->hs[sh];
-        G.tbase[G.nshot] = H.tbase_f - base;
-        G.s[G.nshot] = BFwdShot{H.L, H.a, H.p0, H.p1, H.gx};
-      }
-      const BShot &last = b->hs[G.shot0 + G.nshot - 1];
-      G.tbase[G.nshot] = last.tbase_f + last.gx * last.gzf - base;
-      const dim3 grid(std::min(b->grid_f, G.tbase[G.nshot]));
-      const BShot *ds = b->ds;
-      const float *wv = b->d_wav;
-      if (b->rzf == 1) launch_pdl(k_fwd2d_batch<1>, grid, dim3(32, kBWarpsF), 0, s, G, ds, n, wv, sc);
-      else if (b->rzf == 2) launch_pdl(k_fwd2d_batch<2>, grid, dim3(32, kBWarpsF), 0, s, G, ds, n, wv, sc);
-      else launch_pdl(k_fwd2d_batch<4>, grid, dim3(32, kBWarpsF), 0, s, G, ds, n, wv, sc);
-    }
+  case 1:
+    launch_pdl(k_fwd2d_batch<1>, dim3(std::min(b->grid_f, items)), dim3(32, kBWarpsF), 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_f, i0, i1, n, (const float *)b->d_wav, sc);
     break;
-  }
+  case 2:
+    launch_pdl(k_fwd2d_batch<2>, dim3(std::min(b->grid_f, items)), dim3(32, kBWarpsF), 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_f, i0, i1, n, (const float *)b->d_wav, sc);
+    break;
+  default:
+    launch_pdl(k_fwd2d_batch<4>, dim3(std::min(b->grid_f, items)), dim3(32, kBWarpsF), 0, s, (const BShot *)b->ds,
+               (const int *)b->d_item_f, i0, i1, n, (const float *)b->d_wav, sc);
+    break;
   }
   return cudaPeekAtLastError() == cudaSuccess;
 }
@@ -893,10 +864,9 @@ int enq_rev(rbc_batch *b, int g, cudaStream_t s) {
 
 // One phase (kind 0 forward, 1 reverse) of group g, as its cached graph.
 int run_b(rbc_batch *b, int kind, int g, cudaStream_t s, long long *launches) {
-  // the tiled reverse and the register-queue forward launch once per
-  // kBGMax shots of the group and step
-  const long long chunks = cdiv(b->grp[g + 1] - b->grp[g], kBGMax);
-  const long long per = kind == 0 ? (long long)b->g.nt * (b->rzf ? chunks : 1) : (b->g.nt + 1) * (b->rzr == 3 ? chunks : 1);
+  // the tiled reverse launches once per kBGMax shots of the group and step
+  const long long chunks = b->rzr == 3 ? cdiv(b->grp[g + 1] - b->grp[g], kBGMax) : 1;
+  const long long per = kind == 0 ? b->g.nt : (b->g.nt + 1) * chunks;
   if (!b->use_graph) {
     *launches += per;
     return kind == 0 ? enq_fwd(b, g, s) : enq_rev(b, g, s);
