@@ -417,9 +417,7 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // kHidLast: the last layer (32 -> 1) is applied in the epilogue of the layer
 // before it.  Each epilogue thread holds one pixel p of that layer's output
 // (relu and bf16 rounding as when it is stored), computes its nine tap terms
-// c[dy][dx] = w5[dy][dx] . a(p) (on the warp-level tensor cores: the warp's 32
-// pixels x 32 channels staged in shared memory, read back as A fragments by
-// ldmatrix, the taps as N = 16 with w5 in B-fragment registers) and adds
+// c[dy][dx] = w5[dy][dx] . a(p) (fp32 FMAs over the 32 channels) and adds
 // c[dy][dx] to the output pixel q = p - (dy - 1, dx - 1) in a shared-memory
 // sum over the tile and its one-pixel ring (atomic adds in shared memory).
 // Once all epilogue warps are done with the tile, the sum is flushed: output
@@ -430,7 +428,7 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // bits of the two-pixel border of every tile, can differ from run to run.
 constexpr int tc_nprod(int mode) { return mode == kFused ? 10 : 1; }
 constexpr int tc_ys_bytes(int R) { return (R + 2) * kTcHW * 4; }  // kHidLast: the tile's output sums
-constexpr int kW5Bytes = kTcEpi * 32 * 64;                          // kHidLast: a warp's 32 pixels x 32 channels, bf16
+constexpr int kW5Bytes = 9 * 32 * 4;                                // kHidLast: w5 as fp32
 constexpr int tc_threads(int mode) { return 32 * (kTcEpi + tc_nprod(mode) + 1); }
 constexpr int kFxR = 4;                  // x halo rows beyond the tile's R (two on each side)
 constexpr int kFxC = kTcHW + 2;          // x halo columns (x0 - 2 .. x0 + 127)
@@ -496,7 +494,9 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
   if (kHid && tid < 32) s_bias[tid] = bias[tid];
   if (MODE == kHidLast) {
     float *ys0 = reinterpret_cast<float *>(smem + tc_smem(R));
+    float *w5s = ys0 + (R + 2) * kTcHW;
     for (int i = tid; i < (R + 2) * kTcHW; i += blockDim.x) ys0[i] = 0.f;
+    for (int i = tid; i < 9 * 32; i += blockDim.x) w5s[i] = __bfloat162float(w1[i]);
   }
   if (MODE == kLast && tid == 0) s_bias[0] = bias[0];
   if (tid == 0) {
@@ -721,20 +721,6 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
     // ---- epilogue: warps 0 .. kTcEpi-1, one accumulator row (pixel) per thread ----
     constexpr int RE = R * 4 / kTcEpi;  // output rows per epilogue warp
     const int lq = warp & 3, r0 = (warp >> 2) * RE;
-    // kHidLast: w5 as m16n8k16 B fragments, B[k = channel][n = tap], taps 9-15 zero
-    uint32_t w5f[2][2][2];
-    if constexpr (MODE == kHidLast) {
-      const uint16_t *w5u = reinterpret_cast<const uint16_t *>(w1);
-      const int g = lane >> 2, i2 = 2 * (lane & 3);
-#pragma unroll
-      for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int tp = 8 * j + g, c0 = 16 * kk + i2;
-          w5f[kk][j][0] = tp < 9 ? pack_u16(w5u[tp * 32 + c0], w5u[tp * 32 + c0 + 1]) : 0u;
-          w5f[kk][j][1] = tp < 9 ? pack_u16(w5u[tp * 32 + c0 + 8], w5u[tp * 32 + c0 + 9]) : 0u;
-        }
-    }
     const uint32_t lanes = (uint32_t)(lq * 32) << 16;
     const long long HWp = (long long)H * W;
     int k = 0;
@@ -790,57 +776,26 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
         tmem_ld32(ta, v);
         tmem_zero32(ta);  // the next tile in this buffer accumulates from zero
         const int yy = y0 + rr;
-        if constexpr (MODE == kHidLast) {
-          // this pixel's layer output, rounded as when stored; zero outside
-          // the image (the last layer's padding) and in MMA rows 126, 127
-          const bool in = yy < H && xx < W;
-          uint4 *sa = reinterpret_cast<uint4 *>(smem + tc_smem(R) + tc_ys_bytes(R)) + warp * 32 * 4;
+        if (MODE == kHidLast) {
+          if (yy < H && xx < W) {  // outside the image the layer's output is the last layer's zero padding
+            const float *w5s = reinterpret_cast<const float *>(smem + tc_smem(R)) + (R + 2) * kTcHW;
+            float *ys = reinterpret_cast<float *>(smem + tc_smem(R));
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            uint4 q;
-            q.x = in ? cvt_bf16x2<true>(v[8 * k] + s_bias[8 * k], v[8 * k + 1] + s_bias[8 * k + 1]) : 0u;
-            q.y = in ? cvt_bf16x2<true>(v[8 * k + 2] + s_bias[8 * k + 2], v[8 * k + 3] + s_bias[8 * k + 3]) : 0u;
-            q.z = in ? cvt_bf16x2<true>(v[8 * k + 4] + s_bias[8 * k + 4], v[8 * k + 5] + s_bias[8 * k + 5]) : 0u;
-            q.w = in ? cvt_bf16x2<true>(v[8 * k + 6] + s_bias[8 * k + 6], v[8 * k + 7] + s_bias[8 * k + 7]) : 0u;
-            sa[lane * 4 + (k ^ ((lane >> 1) & 3))] = q;  // [pixel][8-channel chunk], chunks XOR-swizzled
-          }
-          __syncwarp();
-          float d[2][2][4];  // [pixel half][tap group: 0-7, 8-15][fragment]
+            for (int c = 0; c < 32; ++c) v[c] = __bfloat162float(__float2bfloat16(fmaxf(v[c] + s_bias[c], 0.f)));
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+            for (int tp = 0; tp < 9; ++tp) {
+              const float4 *w4 = reinterpret_cast<const float4 *>(w5s + tp * 32);
+              float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) d[h][j][0] = d[h][j][1] = d[h][j][2] = d[h][j][3] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {  // channels 16 kk .. 16 kk + 15
-              // matrices (pixels 0-7 | 8-15 of the half) x (channels +0-7 | +8-15)
-              const int pr = 16 * h + (lane & 7) + 8 * ((lane >> 3) & 1), ch = 2 * kk + (lane >> 4);
-              uint32_t a[4];
-              const uint32_t addr = (uint32_t)__cvta_generic_to_shared(sa + pr * 4 + (ch ^ ((pr >> 1) & 3)));
-              asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                           : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
-                           : "r"(addr));
-#pragma unroll
-              for (int j = 0; j < 2; ++j) mma16816(d[h][j], a, w5f[kk][j]);
-            }
-          }
-          __syncwarp();  // the staging is rewritten by the next row
-          // D[pixel 16 h + g (+ 8)][tap 8 j + 2 i (+ 1)]: add to output pixel
-          // q = p - (dy - 1, dx - 1), sum row rr - dy + 2, column p - dx + 2
-          float *ys = reinterpret_cast<float *>(smem + tc_smem(R));
-          const int g = lane >> 2, i2 = 2 * (lane & 3);
-          const bool yin = yy < H;
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int pl = lq * 32 + 16 * h + g + 8 * (e >> 1);  // pixel of the tile's halo row
-              if (!yin || pl >= kTcOut || x0 + pl >= W) continue;
-#pragma unroll
-              for (int j = 0; j < 2; ++j) {
-                const int tp = 8 * j + i2 + (e & 1);
-                if (tp < 9) atomicAdd(&ys[(rr - tp / 3 + 2) * kTcHW + pl - tp % 3 + 2], d[h][j][e]);
+              for (int c4 = 0; c4 < 8; ++c4) {
+                const float4 wv = w4[c4];
+                acc = __ffma2_rn(make_float2(v[4 * c4], v[4 * c4 + 1]), make_float2(wv.x, wv.y), acc);
+                acc = __ffma2_rn(make_float2(v[4 * c4 + 2], v[4 * c4 + 3]), make_float2(wv.z, wv.w), acc);
               }
+              // q = p - (dy - 1, dx - 1): sum row rr - dy + 2, column px - dx + 2
+              atomicAdd(&ys[(rr - tp / 3 + 2) * kTcHW + px - tp % 3 + 2], acc.x + acc.y);
             }
+          }
           continue;
         }
         if (yy < H && xx < W) {
