@@ -340,14 +340,10 @@ int rbc_cnn_forward(const float *params_dev, int nimg, int H, int W,
                     const float *x_dev, float *y_dev, void *ws_dev,
                     void *stream);
 
-/* y = CNN(x) for inference, without keeping what rbc_cnn_backward needs:
- * the first layer's output is built inside the second layer's kernel and
- * the last layer is applied in the fourth layer's epilogue, so neither of
- * their inputs passes through global memory.  The result is
- * rbc_cnn_forward's up to fp32 summation order: the last layer's terms are
- * summed in another order, and at the two-pixel border of every 8 x 126
- * tile by atomic adds whose order (so the last bits) can differ from run to
- * run.  ws_dev: workspace of rbc_cnn_workspace_bytes, used for the hidden
+/* y = CNN(x) for inference: the same result as rbc_cnn_forward, without
+ * keeping what rbc_cnn_backward needs (the first layer's output is built
+ * inside the second layer's kernel and never written to global memory).
+ * ws_dev: workspace of rbc_cnn_workspace_bytes, used for the hidden
  * activations.  Errors: RBC_EINVAL, RBC_ECUDA. */
 int rbc_cnn_infer(const float *params_dev, int nimg, int H, int W,
                   const float *x_dev, float *y_dev, void *ws_dev,

@@ -51,7 +51,7 @@ __device__ __forceinline__ void mma16816(float *c, const uint32_t *a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-enum { kHidden = 0, kLast = 1, kBackData = 2, kFused = 3, kHidLast = 4 };
+enum { kHidden = 0, kLast = 1, kBackData = 2, kFused = 3 };
 
 // The one-channel first layer (1 -> 32 channels, and the last layer's
 // backward-data pass) on the warp-level tensor cores:
@@ -390,8 +390,6 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 //   MODE kLast:     out_f = resid + conv(in) + bias                    (32 -> 1)
 //   MODE kFused:    out = relu(conv(a1) + bias) with a1 = relu(conv1(x1) + b1)
 //                   computed in the block (the first two layers, for inference)
-//   MODE kHidLast:  out_f = resid + conv5(a) + b5 with a = relu(conv(in) + bias)
-//                   (the last two layers, for inference; w5, b5 in w1, b1)
 // The last layer's single output channel is padded to N = 16 per output row
 // (the smallest N of an M = 128 MMA); the 15 padding channels have zero
 // weights, so their accumulators stay zero and only channel 0 is read out.
@@ -413,33 +411,15 @@ __device__ __forceinline__ void tmem_zero1(uint32_t ta) {
 // layer's padding).  The builders then make their writes visible to the
 // tensor cores and arrive on the stage's "full" barrier.  The first layer's
 // output never passes through global memory.
-//
-// kHidLast: the last layer (32 -> 1) is applied in the epilogue of the layer
-// before it.  Each epilogue thread holds one pixel p of that layer's output
-// (relu and bf16 rounding as when it is stored), computes its nine tap terms
-// c[dy][dx] = w5[dy][dx] . a(p) (fp32 FMAs over the 32 channels) and adds
-// c[dy][dx] to the output pixel q = p - (dy - 1, dx - 1) in a shared-memory
-// sum over the tile and its one-pixel ring (atomic adds in shared memory).
-// Once all epilogue warps are done with the tile, the sum is flushed: output
-// pixels whose nine terms all come from this tile (two pixels or more inside
-// its edges) are stored with the residual and the bias; the others get atomic
-// adds in global memory, the residual and the bias from the tile that owns
-// them (the output starts at zero).  The order of those adds, and so the last
-// bits of the two-pixel border of every tile, can differ from run to run.
 constexpr int tc_nprod(int mode) { return mode == kFused ? 10 : 1; }
-constexpr int tc_ys_bytes(int R) { return (R + 2) * kTcHW * 4; }  // kHidLast: the tile's output sums
-constexpr int kW5Bytes = 9 * 32 * 4;                                // kHidLast: w5 as fp32
 constexpr int tc_threads(int mode) { return 32 * (kTcEpi + tc_nprod(mode) + 1); }
 constexpr int kFxR = 4;                  // x halo rows beyond the tile's R (two on each side)
 constexpr int kFxC = kTcHW + 2;          // x halo columns (x0 - 2 .. x0 + 127)
 constexpr int kFxP = 144;                // x halo row pitch (2-byte values; conflict-free gathers)
 constexpr int tc_fx_bytes(int R) { return (R + kFxR) * kFxP * 2; }
 #define XVALS_OF(R) (((R) + kFxR) * kFxC)  // x halo values of a tile
-constexpr int tc_smem_mode(int mode, int R) {
-  return tc_smem(R) + (mode == kFused ? tc_fx_bytes(R) : mode == kHidLast ? tc_ys_bytes(R) + kW5Bytes : 0);
-}
+constexpr int tc_smem_mode(int mode, int R) { return tc_smem(R) + (mode == kFused ? tc_fx_bytes(R) : 0); }
 static_assert(tc_smem(kTcR) + tc_fx_bytes(kTcR) <= 227 * 1024, "the fused ring must fit in shared memory");
-static_assert(tc_smem(kTcR) + tc_ys_bytes(kTcR) + kW5Bytes <= 227 * 1024, "the output sums must fit as well");
 
 template <int MODE, int R>
 __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_constant__ CUtensorMap tm_in,
@@ -451,7 +431,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
                                                     int *err, const float *__restrict__ x1 = nullptr,
                                                     const __nv_bfloat16 *__restrict__ w1 = nullptr,
                                                     const float *__restrict__ b1 = nullptr) {
-  constexpr bool kHid = MODE == kHidden || MODE == kFused || MODE == kHidLast;  // relu(conv + bias) epilogue
+  constexpr bool kHid = MODE == kHidden || MODE == kFused;  // relu(conv + bias) epilogue
   constexpr int kMma = kTcEpi + tc_nprod(MODE);             // the MMA issuer warp
   constexpr int NCO = MODE == kLast ? 16 : 32;  // output channels per row accumulator
   constexpr int WCG = 3 * NCO * 16;              // weight bytes per (dx, channel group)
@@ -492,12 +472,6 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
     }
   }
   if (kHid && tid < 32) s_bias[tid] = bias[tid];
-  if (MODE == kHidLast) {
-    float *ys0 = reinterpret_cast<float *>(smem + tc_smem(R));
-    float *w5s = ys0 + (R + 2) * kTcHW;
-    for (int i = tid; i < (R + 2) * kTcHW; i += blockDim.x) ys0[i] = 0.f;
-    for (int i = tid; i < 9 * 32; i += blockDim.x) w5s[i] = __bfloat162float(w1[i]);
-  }
   if (MODE == kLast && tid == 0) s_bias[0] = bias[0];
   if (tid == 0) {
     *abort_blk = 0;
@@ -747,17 +721,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
                            : make_uint4(0u, 0u, 0u, 0u);
       }
       const bool ok = tc_wait(tfull(b), ub & 1, abort_blk);
-      if constexpr (MODE == kHidLast) {
-        // the tile's flush is a barrier of all epilogue warps: decide together
-        uint32_t any;
-        asm volatile("{\n.reg .pred p, q;\nsetp.eq.u32 p, %1, 0;\nbar.red.or.pred q, 2, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
-                     : "=r"(any)
-                     : "r"((uint32_t)ok), "n"(32 * kTcEpi)
-                     : "memory");
-        if (any) break;
-      } else if (__any_sync(0xffffffffu, !ok)) {
-        break;
-      }
+      if (__any_sync(0xffffffffu, !ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if constexpr (MODE == kLast) {
 #pragma unroll
@@ -776,28 +740,6 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
         tmem_ld32(ta, v);
         tmem_zero32(ta);  // the next tile in this buffer accumulates from zero
         const int yy = y0 + rr;
-        if (MODE == kHidLast) {
-          if (yy < H && xx < W) {  // outside the image the layer's output is the last layer's zero padding
-            const float *w5s = reinterpret_cast<const float *>(smem + tc_smem(R)) + (R + 2) * kTcHW;
-            float *ys = reinterpret_cast<float *>(smem + tc_smem(R));
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = __bfloat162float(__float2bfloat16(fmaxf(v[c] + s_bias[c], 0.f)));
-#pragma unroll
-            for (int tp = 0; tp < 9; ++tp) {
-              const float4 *w4 = reinterpret_cast<const float4 *>(w5s + tp * 32);
-              float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-              for (int c4 = 0; c4 < 8; ++c4) {
-                const float4 wv = w4[c4];
-                acc = __ffma2_rn(make_float2(v[4 * c4], v[4 * c4 + 1]), make_float2(wv.x, wv.y), acc);
-                acc = __ffma2_rn(make_float2(v[4 * c4 + 2], v[4 * c4 + 3]), make_float2(wv.z, wv.w), acc);
-              }
-              // q = p - (dy - 1, dx - 1): sum row rr - dy + 2, column px - dx + 2
-              atomicAdd(&ys[(rr - tp / 3 + 2) * kTcHW + px - tp % 3 + 2], acc.x + acc.y);
-            }
-          }
-          continue;
-        }
         if (yy < H && xx < W) {
           const long long pix = (long long)yy * W + xx;
           if (kHid) {
@@ -830,26 +772,6 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       tc_arrive(tempty(b));
-      if constexpr (MODE == kHidLast) {
-        // flush the tile's output sums (rows y0 - 1 .. y0 + R, columns x0 - 1 .. x0 + 126)
-        asm volatile("bar.sync 2, %0;" ::"n"(32 * kTcEpi) : "memory");
-        float *ys = reinterpret_cast<float *>(smem + tc_smem(R));
-        const float b5 = b1[0];
-        for (int i = warp * 32 + lane; i < (R + 2) * kTcHW; i += 32 * kTcEpi) {
-          const int lr = i / kTcHW, lc = i - lr * kTcHW;
-          const int qy = y0 - 1 + lr, qx = x0 - 1 + lc;
-          float val = ys[i];
-          ys[i] = 0.f;
-          if ((unsigned)qy >= (unsigned)H || (unsigned)qx >= (unsigned)W) continue;
-          const long long q = (long long)img * HWp + (long long)qy * W + qx;
-          const bool own = lr >= 1 && lr <= R && lc >= 1 && lc <= kTcOut;
-          const bool inner = lr >= 2 && lr <= R - 1 && lc >= 2 && lc <= kTcOut - 1;
-          if (own) val += resid[q] + b5;
-          if (inner) out_f[q] = val;
-          else atomicAdd(out_f + q, val);
-        }
-        asm volatile("bar.sync 2, %0;" ::"n"(32 * kTcEpi) : "memory");
-      }
     }
   }
   __syncthreads();
@@ -1289,8 +1211,6 @@ void set_attrs() {
   cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kFused, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        tc_smem_mode(kFused, kTcR));
-  cudaFuncSetAttribute(k_conv_tc<kHidLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       tc_smem_mode(kHidLast, kTcR));
   cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
   cudaFuncSetAttribute(k_conv_wgrad1<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
   cudaFuncSetAttribute(k_conv_wgrad1<true, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW1Smem);
@@ -1404,16 +1324,15 @@ bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, i
 template <int MODE>
 bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, const __nv_bfloat16 *mask,
                     __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s, float *out_f = nullptr,
-                    const float *resid = nullptr, const __nv_bfloat16 *w_aux = nullptr,
-                    const float *b_aux = nullptr) {
+                    const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + kTcR - 1) / kTcR) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
   if (!act_map(&tin, in, nimg, H, W, kTcR + 2)) return false;
-  k_conv_tc<MODE, kTcR><<<grid, tc_threads(MODE), tc_smem_mode(MODE, kTcR), s>>>(
-      tin, wt, bias, mask, out, out_f, resid, nimg, H, W, tc_err_dev, nullptr, w_aux, b_aux);
+  k_conv_tc<MODE, kTcR><<<grid, tc_threads(MODE), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
+                                                                      H, W, tc_err_dev);
   return true;
 }
 
@@ -1431,9 +1350,8 @@ void launch_conv_fused(const float *x, const __nv_bfloat16 *w1, const float *b1,
 }
 
 // The network's forward pass; `keep` stores what the backward pass reads
-// (the bf16 input, the first and the fourth layer's outputs: two launches
-// each for layers 1-2 and 4-5); without it layers 1-2 and layers 4-5 are one
-// fused launch each.
+// (the bf16 input and the first layer's output: two launches for the first
+// two layers); without it the first two layers are one fused launch.
 int cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_dev, float *y_dev, void *ws_dev,
                 void *stream, bool keep, const char *who) {
   if (!params_dev || !x_dev || !y_dev || !ws_dev || nimg < 1 || H < 1 || W < 1)
@@ -1454,17 +1372,11 @@ int cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_
     launch_conv_fused(x_dev, w.wf + kW1, params_dev + kB1, w.wf + kW2, params_dev + kB2, w.act[1], nimg, H, W, s);
   }
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
-  if (keep) {  // the backward pass reads the fourth layer's output
-    ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
-    ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
-                                           y_dev, x_dev);
-  } else {  // layers 4 and 5 in one launch; its border pixels are atomic sums onto zero
-    if (cudaMemsetAsync(y_dev, 0, sizeof(float) * (size_t)npx, s) != cudaSuccess) ok_tc = false;
-    ok_tc = ok_tc && launch_conv_tc<kHidLast>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, nullptr, nimg, H, W, s,
-                                              y_dev, x_dev, w.wf + kW5, params_dev + kB5);
-  }
+  ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
+  ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
+                                         y_dev, x_dev);
   if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: launch failed");
-  rbc::add_launches(keep ? 7 : 4);
+  rbc::add_launches(keep ? 7 : 5);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rbc::set_error(RBC_ECUDA, cudaGetErrorString(e));
   return RBC_OK;
