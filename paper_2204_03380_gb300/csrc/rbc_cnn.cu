@@ -806,7 +806,10 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *smem_row) {
 // x0 - 1 .. x0 + 130, dz over rows y0 - 1 .. y0 + 4 and pixels x0 .. x0 + 127,
 // by 16-byte cp.async copies into their swizzled places (zero outside the
 // image), in two stages: tile k + 1's copies are in flight while tile k is
-// multiplied.  One thread issues a tile's 32 MMAs into the accumulator the
+// multiplied.  Eight consecutive lanes copy two pixels' four channel groups:
+// one 128-byte segment of shared memory, and 32 contiguous bytes of each
+// group plane (lanes copying one group of consecutive pixels would write
+// 16 bytes of every 64-byte pixel row, and the copies do not coalesce).  One thread issues a tile's 32 MMAs into the accumulator the
 // block keeps over all its tiles; meanwhile the block's threads sum dz over
 // the tile's own rows for db.  At the end warps 0-2 read the accumulator
 // (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
@@ -874,8 +877,8 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
     origin(tt, img, y0, x0);
     const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
 #pragma unroll 4
-    for (int e = tid; e < 4 * kWtR * kWtXP; e += 128) {  // x: [group][row][pixel] order, pixels fastest
-      const int i = e % kWtXP, r = (e / kWtXP) % kWtR, n = e / (kWtXP * kWtR);
+    for (int e = tid; e < 4 * kWtR * kWtXP; e += 128) {  // x: groups fastest, then pixels, then rows
+      const int n = e & 3, i = (e >> 2) % kWtXP, r = (e >> 2) / kWtXP;
       const int yy = y0 + r, xx = x0 - 1 + i;
       const bool ok = yy < H && xx >= 0 && xx < W;
       const __nv_bfloat16 *src = ok ? x + (((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 8 : x;
@@ -883,7 +886,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
     }
 #pragma unroll 4
     for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += 128) {
-      const int i = e % kWtC, r = (e / kWtC) % (kWtR + 2), n = e / (kWtC * (kWtR + 2));
+      const int n = e & 3, i = (e >> 2) % kWtC, r = (e >> 2) / kWtC;
       const int yy = y0 - 1 + r, xx = x0 + i;
       const bool ok = yy >= 0 && yy < H && xx < W;
       const __nv_bfloat16 *src = ok ? dz + (((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 8 : dz;
