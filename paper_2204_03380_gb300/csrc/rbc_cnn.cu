@@ -804,14 +804,17 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *smem_row) {
 // block i holding the tap dy = 2 - i; a K step of 8 pixels is 512 bytes.
 // Tiles of 4 rows x 128 pixels: x is staged over the tile's rows and pixels
 // x0 - 1 .. x0 + 130, dz over rows y0 - 1 .. y0 + 4 and pixels x0 .. x0 + 127,
-// by 16-byte cp.async copies into their swizzled places (zero outside the
-// image), in two stages: tile k + 1's copies are in flight while tile k is
-// multiplied.  Eight consecutive lanes copy two pixels' four channel groups:
-// one 128-byte segment of shared memory, and 32 contiguous bytes of each
-// group plane (lanes copying one group of consecutive pixels would write
-// 16 bytes of every 64-byte pixel row, and the copies do not coalesce).  One thread issues a tile's 32 MMAs into the accumulator the
-// block keeps over all its tiles; meanwhile the block's threads sum dz over
-// the tile's own rows for db.  At the end warps 0-2 read the accumulator
+// in two stages: the 512 threads load tile k + 1 into registers (16 bytes
+// per chunk, consecutive lanes on consecutive pixels of a channel-group plane,
+// so the loads coalesce; zero outside the image) while tile k is multiplied,
+// and store the chunks into their swizzled places once tile k - 1's MMAs have
+// released the stage.  (cp.async copies into the swizzled places do not
+// coalesce: about 30 L2 requests per warp instruction against 4 for linear
+// destinations, measured; and a tensor copy with the 64-byte swizzle pads a
+// box whose rows are the planar layout's 16 bytes.)  One thread issues a
+// tile's 32 MMAs into the accumulator the block keeps over all its tiles;
+// meanwhile the block's threads sum dz over the tile's own rows for db (one
+// pixel each).  At the end warps 0-2 read the accumulator
 // (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
 // gives up flags the error word.
 constexpr int kWtR = 4, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
@@ -835,9 +838,13 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t addr, uint32_t lbo, 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-__global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
-                                                          const __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
-                                                          float *__restrict__ db, int nimg, int H, int W, int *err) {
+constexpr int kWtThreads = 512;
+constexpr int kWtXC = 4 * kWtR * kWtXP, kWtZC = 4 * (kWtR + 2) * kWtC;  // 16-byte chunks of a tile's x and dz
+constexpr int kWtPre = (kWtXC + kWtZC + kWtThreads - 1) / kWtThreads;   // chunks per thread
+__global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
+                                                                 const __nv_bfloat16 *__restrict__ dz,
+                                                                 float *__restrict__ dw, float *__restrict__ db,
+                                                                 int nimg, int H, int W, int *err) {
   extern __shared__ unsigned char s_raw[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
@@ -845,7 +852,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
   __shared__ float s_db[32];
   const uint32_t raw = (uint32_t)__cvta_generic_to_shared(s_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const unsigned char *gbase = s_raw + (base - raw);
+  unsigned char *gbase = s_raw + (base - raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntx = (W + kWtC - 1) / kWtC, tpi = ntx * ((H + kWtR - 1) / kWtR), ntiles = tpi * nimg;
   const long long HWp = (long long)H * W;
@@ -872,47 +879,79 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
     y0 = ty * kWtR;
     x0 = (rem - ty * ntx) * kWtC;
   };
-  auto stage = [&](int tt, int sb) {
+  // chunk e of a tile: x chunks [group][row][pixel], then dz chunks [group][row][pixel]
+  // (consecutive lanes read consecutive pixels of one group plane); its
+  // global offset (in 16-byte units, -1 outside the image) and its shared-memory byte offset
+  auto chunk = [&](int e, int img, int y0, int x0, long long &g, uint32_t &o) {
+    int n, r, i, yy, xx;
+    bool ok;
+    if (e < kWtXC) {
+      n = e / (kWtR * kWtXP);
+      const int rem = e - n * (kWtR * kWtXP);
+      r = rem / kWtXP;
+      i = rem - r * kWtXP;
+      yy = y0 + r;
+      xx = x0 - 1 + i;
+      ok = yy < H && xx >= 0 && xx < W;
+      o = swz64((uint32_t)((r * kWtXP + i) * 64 + n * 16));
+    } else {
+      const int e2 = e - kWtXC;
+      n = e2 / ((kWtR + 2) * kWtC);
+      const int rem = e2 - n * ((kWtR + 2) * kWtC);
+      r = rem / kWtC;
+      i = rem - r * kWtC;
+      yy = y0 - 1 + r;
+      xx = x0 + i;
+      ok = yy >= 0 && yy < H && xx < W;
+      o = kWtXB + swz64((uint32_t)((r * kWtC + i) * 64 + n * 16));
+    }
+    g = ok ? ((long long)img * 4 + n) * HWp + (long long)yy * W + xx : -1;
+  };
+  // this thread's chunks of tile tt into registers (loads left in flight)
+  auto load = [&](int tt, uint4 *v) {
     int img, y0, x0;
     origin(tt, img, y0, x0);
-    const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
-#pragma unroll 4
-    for (int e = tid; e < 4 * kWtR * kWtXP; e += 128) {  // x: groups fastest, then pixels, then rows
-      const int n = e & 3, i = (e >> 2) % kWtXP, r = (e >> 2) / kWtXP;
-      const int yy = y0 + r, xx = x0 - 1 + i;
-      const bool ok = yy < H && xx >= 0 && xx < W;
-      const __nv_bfloat16 *src = ok ? x + (((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 8 : x;
-      cp_async16(X + swz64((uint32_t)((r * kWtXP + i) * 64 + n * 16)), src, ok);
+#pragma unroll
+    for (int j = 0; j < kWtPre; ++j) {
+      const int e = tid + kWtThreads * j;
+      v[j] = make_uint4(0u, 0u, 0u, 0u);
+      if (e < kWtXC + kWtZC) {
+        long long g;
+        uint32_t o;
+        chunk(e, img, y0, x0, g, o);
+        if (g >= 0) v[j] = __ldg(reinterpret_cast<const uint4 *>(e < kWtXC ? x : dz) + g);
+      }
     }
-#pragma unroll 4
-    for (int e = tid; e < 4 * (kWtR + 2) * kWtC; e += 128) {
-      const int n = e & 3, i = (e >> 2) % kWtC, r = (e >> 2) / kWtC;
-      const int yy = y0 - 1 + r, xx = x0 + i;
-      const bool ok = yy >= 0 && yy < H && xx < W;
-      const __nv_bfloat16 *src = ok ? dz + (((long long)img * 4 + n) * HWp + (long long)yy * W + xx) * 8 : dz;
-      cp_async16(Z + swz64((uint32_t)((r * kWtC + i) * 64 + n * 16)), src, ok);
+  };
+  auto store = [&](int tt, int sb, const uint4 *v) {
+    int img, y0, x0;
+    origin(tt, img, y0, x0);
+    unsigned char *st = gbase + sb * kWtStage;
+#pragma unroll
+    for (int j = 0; j < kWtPre; ++j) {
+      const int e = tid + kWtThreads * j;
+      if (e < kWtXC + kWtZC) {
+        long long g;
+        uint32_t o;
+        chunk(e, img, y0, x0, g, o);
+        *reinterpret_cast<uint4 *>(st + o) = v[j];
+      }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   float bsum[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) bsum[c] = 0.f;
+  uint4 v[kWtPre];
   int k = 0;
-  if ((int)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+  if ((int)blockIdx.x < ntiles) {
+    load(blockIdx.x, v);
+    store(blockIdx.x, 0, v);
+  }
   for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x, ++k) {
     const int sb = k & 1, tn = tt + gridDim.x;
-    if (tn < ntiles) {
-      // stage sb ^ 1 is free once tile k - 1's MMAs (and sums) are done
-      if (k >= 1 && tid == 0) tc_wait(bar0 + 8 * (sb ^ 1), ((k - 1) >> 1) & 1, &s_abort);
-      __syncthreads();
-      if (s_abort) break;
-      stage(tn, sb ^ 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();  // tile k is staged
+    if (tn < ntiles) load(tn, v);  // in flight while tile k is multiplied
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // this thread's stores, to the tensor cores
+    __syncthreads();                                               // tile k is staged
     const uint32_t X = base + sb * kWtStage, Z = X + kWtXB;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -931,23 +970,29 @@ __global__ void __launch_bounds__(128, 1) k_conv_wgrad_tc(const __nv_bfloat16 *_
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * sb)
                    : "memory");
     }
-    // db: dz of the tile's own rows (staged rows 1 .. 4), pixel tid
+    // db: dz of the tile's own rows (staged rows 1 .. 4), one pixel per thread
+    static_assert(kWtThreads == kWtR * kWtC, "one pixel of the tile per thread");
     const unsigned char *zg = gbase + sb * kWtStage + kWtXB;
 #pragma unroll
-    for (int r = 1; r <= kWtR; ++r)
+    for (int n = 0; n < 4; ++n) {
+      const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((kWtC + tid) * 64 + n * 16)));
+      const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
 #pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((r * kWtC + tid) * 64 + n * 16)));
-        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(h2[e]);
-          bsum[8 * n + 2 * e] += f.x;
-          bsum[8 * n + 2 * e + 1] += f.y;
-        }
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(h2[e]);
+        bsum[8 * n + 2 * e] += f.x;
+        bsum[8 * n + 2 * e + 1] += f.y;
       }
+    }
+    if (tn < ntiles) {
+      // stage sb ^ 1 is free once tile k - 1's MMAs are done (its sums were
+      // read before this iteration's barrier)
+      if (k >= 1 && tid == 0) tc_wait(bar0 + 8 * (sb ^ 1), ((k - 1) >> 1) & 1, &s_abort);
+      __syncthreads();
+      if (s_abort) break;
+      store(tn, sb ^ 1, v);
+    }
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (k > 0 && tid == 0 && !s_abort) tc_wait(bar0 + 8 * ((k - 1) & 1), ((k - 1) >> 1) & 1, &s_abort);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1426,7 +1471,7 @@ int rbc_cnn_backward(const float *params_dev, int nimg, int H, int W, const floa
   const int woff[3] = {kW4, kW3, kW2}, boff[3] = {kB4, kB3, kB2};
   for (int l = 0; l < 3; ++l) {
     const int layer_in = 2 - l;  // act index of this layer's input: act3 (l=0) ... act1
-    k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), 128, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
+    k_conv_wgrad_tc<<<grid_wgrad_tc(nimg, H, W), kWtThreads, kWtSmem, s>>>(w.act[layer_in], w.dz[cur], grad_dev + woff[l],
                                                                      grad_dev + boff[l], nimg, H, W, tc_err_dev);
     ok_tc = ok_tc && launch_conv_tc<kBackData>(w.dz[cur], w.wb + woff[l], nullptr, w.act[layer_in], w.dz[1 - cur], nimg, H, W, s);
     cur = 1 - cur;
