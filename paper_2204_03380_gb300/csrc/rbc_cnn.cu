@@ -291,9 +291,6 @@ constexpr int kTcEpi = 8;                                    // epilogue warps
 // 128-column tiles and the 16-byte-row halo copy: R = 6 1.14 / 5.51 ms, R = 4
 // 1.18 / 5.57 ms, R = 4 with 4 epilogue warps 1.23 / 5.88 ms.
 constexpr int kTcR = 8;
-// The last layer (light MMAs and epilogue, so its ring's copy latency shows)
-// runs 4-row tiles with a 4-stage ring.
-constexpr int kTcRLast = 4;
 constexpr int tc_plane(int R) { return (R + 2) * kTcHW * 16; }
 constexpr int tc_stages(int R) { return R <= 4 ? 4 : R <= 6 ? 3 : 2; }
 constexpr int tc_smem(int R) { return kTcWBytes + tc_stages(R) * 4 * tc_plane(R) + 256; }
@@ -1259,7 +1256,7 @@ void set_attrs() {
   if (done) return;
   cudaFuncSetAttribute(k_conv_tc<kHidden, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kBackData, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
-  cudaFuncSetAttribute(k_conv_tc<kLast, kTcRLast>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcRLast));
+  cudaFuncSetAttribute(k_conv_tc<kLast, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(kTcR));
   cudaFuncSetAttribute(k_conv_tc<kFused, kTcR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        tc_smem_mode(kFused, kTcR));
   cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
@@ -1372,18 +1369,18 @@ bool act_map(CUtensorMap *m, const __nv_bfloat16 *buf, int nimg, int H, int W, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE, int R = kTcR>
+template <int MODE>
 bool launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, const __nv_bfloat16 *mask,
                     __nv_bfloat16 *out, int nimg, int H, int W, cudaStream_t s, float *out_f = nullptr,
                     const float *resid = nullptr) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + R - 1) / R) * nimg;
+  const long long tiles = (long long)((W + kTcOut - 1) / kTcOut) * ((H + kTcR - 1) / kTcR) * nimg;
   const int grid = (int)(tiles < sms ? tiles : sms);
   CUtensorMap tin;
-  if (!act_map(&tin, in, nimg, H, W, R + 2)) return false;
-  k_conv_tc<MODE, R><<<grid, tc_threads(MODE), tc_smem(R), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg, H, W,
-                                                                tc_err_dev);
+  if (!act_map(&tin, in, nimg, H, W, kTcR + 2)) return false;
+  k_conv_tc<MODE, kTcR><<<grid, tc_threads(MODE), tc_smem(kTcR), s>>>(tin, wt, bias, mask, out, out_f, resid, nimg,
+                                                                      H, W, tc_err_dev);
   return true;
 }
 
@@ -1424,8 +1421,8 @@ int cnn_forward(const float *params_dev, int nimg, int H, int W, const float *x_
   }
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[1], w.wf + kW3, params_dev + kB3, nullptr, w.act[2], nimg, H, W, s);
   ok_tc = ok_tc && launch_conv_tc<kHidden>(w.act[2], w.wf + kW4, params_dev + kB4, nullptr, w.act[3], nimg, H, W, s);
-  ok_tc = ok_tc && launch_conv_tc<kLast, kTcRLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H,
-                                                   W, s, y_dev, x_dev);
+  ok_tc = ok_tc && launch_conv_tc<kLast>(w.act[3], w.wf + kW5, params_dev + kB5, nullptr, nullptr, nimg, H, W, s,
+                                         y_dev, x_dev);
   if (!ok_tc) return rbc::set_error(RBC_ECUDA, "rbc_cnn_forward: launch failed");
   rbc::add_launches(keep ? 7 : 5);
   cudaError_t e = cudaGetLastError();
