@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(256, 3) k_conv_1to32(const __nv_bfloat16 *__re
 //
 // Per block (one per SM, persistent over tiles), three roles: warp kTcEpi
 // streams each tile's halo (zero-filled outside the image) into a shared-
-// memory ring of tc_stages(R) stages; warp kTcEpi + 1 issues the 6 (R + 2)
+// memory ring of tc_stages(R) stages (in the fused first-layer mode, builder
+// warps compute it there instead); the next warp issues the 6 (R + 2)
 // MMAs of a tile into one of two tensor-memory accumulators and commits them
 // to the ring's "empty" and the accumulator's "full" barrier; warps 0 ..
 // kTcEpi - 1 (two per tensor-memory lane quarter, one pixel per thread, half
@@ -417,7 +418,7 @@ constexpr int kFxR = 4;                  // x halo rows beyond the tile's R (two
 constexpr int kFxC = kTcHW + 2;          // x halo columns (x0 - 2 .. x0 + 127)
 constexpr int kFxP = 144;                // x halo row pitch (2-byte values; conflict-free gathers)
 constexpr int tc_fx_bytes(int R) { return (R + kFxR) * kFxP * 2; }
-#define XVALS_OF(R) (((R) + kFxR) * kFxC)  // x halo values of a tile
+constexpr int tc_fx_vals(int R) { return (R + kFxR) * kFxC; }  // x halo values of a tile
 constexpr int tc_smem_mode(int mode, int R) { return tc_smem(R) + (mode == kFused ? tc_fx_bytes(R) : 0); }
 static_assert(tc_smem(kTcR) + tc_fx_bytes(kTcR) <= 227 * 1024, "the fused ring must fit in shared memory");
 
@@ -543,8 +544,7 @@ __global__ void __launch_bounds__(tc_threads(MODE), 1) k_conv_tc(const __grid_co
   } else if (MODE == kFused && warp >= kTcEpi && warp < kMma) {
     // ---- builders (kFused): the first layer's output over the tile's halo ----
     constexpr int NB = tc_nprod(MODE), NBT = 32 * NB;                    // builder warps, threads
-    constexpr int NPRE = (XVALS_OF(R) + NBT - 1) / NBT;                 // x values per builder thread
-    constexpr int XVALS = XVALS_OF(R);
+    constexpr int XVALS = tc_fx_vals(R), NPRE = (XVALS + NBT - 1) / NBT;  // x values, per builder thread
     static_assert((R + 2) % NB == 0, "each builder warp owns the same number of halo rows");
     const int bt = tid - 32 * kTcEpi, g = lane >> 2, tq = lane & 3;
     const int bw = warp - kTcEpi;
