@@ -812,21 +812,18 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *smem_row) {
 // coalesce: about 30 L2 requests per warp instruction against 4 for linear
 // destinations, measured; and a tensor copy with the 64-byte swizzle pads a
 // box whose rows are the planar layout's 16 bytes.)  One thread issues a
-// tile's 32 MMAs into the accumulator the block keeps over all its tiles,
-// each followed by one for db: A = 128 x 16 ones (K-major), B = the row's own
-// dz (the dy = 1 block, N = 32), into accumulator columns 96 .. 127.  At the end warps 0-2 read the accumulator
+// tile's 32 MMAs into the accumulator the block keeps over all its tiles;
+// meanwhile the block's threads sum dz over the tile's own rows for db (one
+// pixel each).  At the end warps 0-2 read the accumulator
 // (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
 // gives up flags the error word.
 constexpr int kWtR = 4, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
 constexpr int kWtXB = kWtR * kWtXP * 64;                    // staged x bytes
 constexpr int kWtZB = (kWtR + 2) * kWtC * 64;               // staged dz bytes
 constexpr int kWtStage = kWtXB + kWtZB;
-constexpr int kWtOnes = 128 * 16 * 2;  // the bias MMA's A operand: 128 x 16 bf16 ones, K-major
-constexpr size_t kWtSmem = 2 * (size_t)kWtStage + kWtOnes + 1024;
+constexpr size_t kWtSmem = 2 * (size_t)kWtStage + 1024;
 static_assert(kWtXB % 1024 == 0 && kWtStage % 1024 == 0, "staged regions start on the swizzle period");
 static_assert(kWtSmem <= 227 * 1024, "two stages must fit in shared memory");
-// the bias MMA: A K-major (the ones), B MN-major (dz), N = 32, M = 128
-constexpr uint32_t kWtIdescB = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 // kind::f16, fp32 accumulator, bf16 A and B, both MN-major, N = 96, M = 128
 constexpr uint32_t kWtIdesc =
     (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
@@ -852,10 +849,10 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
+  __shared__ float s_db[32];
   const uint32_t raw = (uint32_t)__cvta_generic_to_shared(s_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char *gbase = s_raw + (base - raw);
-  const uint32_t ones = base + 2 * kWtStage;  // [m / 8][k / 8][8 rows][16 B], all bf16 ones
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntx = (W + kWtC - 1) / kWtC, tpi = ntx * ((H + kWtR - 1) / kWtR), ntiles = tpi * nimg;
   const long long HWp = (long long)H * W;
@@ -866,8 +863,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
     tc_mbar_init(bar0 + 8, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < kWtOnes / 16; i += kWtThreads)
-    *reinterpret_cast<uint4 *>(gbase + 2 * kWtStage + 16 * i) = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+  if (tid < 32) s_db[tid] = 0.f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
         (uint32_t)__cvta_generic_to_shared(&s_tmem)));
@@ -942,6 +938,9 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
       }
     }
   };
+  float bsum[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) bsum[c] = 0.f;
   uint4 v[kWtPre];
   int k = 0;
   if ((int)blockIdx.x < ntiles) {
@@ -957,7 +956,6 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t a0 = umma_desc_sw64(X, 64, 512), b0 = umma_desc_sw64(Z, kWtC * 64, 512);
-      const uint64_t a1 = umma_desc(ones, 128, 256);  // K-major, no swizzle: K groups 128 B, row groups 256 B
 #pragma unroll
       for (int r = 0; r < kWtR; ++r)
 #pragma unroll
@@ -968,14 +966,23 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
           asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem), "l"(ad), "l"(bd),
                        "r"(kWtIdesc), "r"(acc));
-          // db: every row of ones x the row's own dz (N block 1, the tap dy = 1) into columns 96 .. 127
-          const uint64_t bc = bd + (uint64_t)((kWtC * 64) >> 4);
-          asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + 96), "l"(a1),
-                       "l"(bc), "r"(kWtIdescB), "r"(acc));
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * sb)
                    : "memory");
+    }
+    // db: dz of the tile's own rows (staged rows 1 .. 4), one pixel per thread
+    static_assert(kWtThreads == kWtR * kWtC, "one pixel of the tile per thread");
+    const unsigned char *zg = gbase + sb * kWtStage + kWtXB;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const uint4 q = *reinterpret_cast<const uint4 *>(zg + swz64((uint32_t)((kWtC + tid) * 64 + n * 16)));
+      const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(h2[e]);
+        bsum[8 * n + 2 * e] += f.x;
+        bsum[8 * n + 2 * e + 1] += f.y;
+      }
     }
     if (tn < ntiles) {
       // stage sb ^ 1 is free once tile k - 1's MMAs are done (its sums were
@@ -1000,13 +1007,15 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bflo
       for (int c = 0; c < 32; ++c) atomicAdd(dw + ((3 * dyy + warp) * 32 + c) * 32 + lane, v[c]);
     }
   }
-  if (ok && k > 0 && warp == 3) {  // db: columns 96 .. 127 of any lane (every A row is ones)
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(3 * 32) << 16) + 96, v);
-    if (lane == 0)
 #pragma unroll
-      for (int c = 0; c < 32; ++c) atomicAdd(db + c, v[c]);
+  for (int c = 0; c < 32; ++c) {
+    float v = bsum[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(&s_db[c], v);
   }
+  __syncthreads();
+  if (ok && tid < 32) atomicAdd(db + tid, s_db[tid]);
   if (!ok && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
