@@ -817,13 +817,13 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *smem_row) {
 // pixel each).  At the end warps 0-2 read the accumulator
 // (lane 32 dx + ci) and add it to dW.  Every wait is bounded; a block that
 // gives up flags the error word.
-constexpr int kWtR = 2, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
+constexpr int kWtR = 4, kWtC = 128, kWtXP = kWtC + 4;       // rows, pixels per row, staged x pixels per row
 constexpr int kWtXB = kWtR * kWtXP * 64;                    // staged x bytes
 constexpr int kWtZB = (kWtR + 2) * kWtC * 64;               // staged dz bytes
 constexpr int kWtStage = kWtXB + kWtZB;
 constexpr size_t kWtSmem = 2 * (size_t)kWtStage + 1024;
-static_assert(kWtXB % 512 == 0 && kWtStage % 512 == 0, "staged regions start on the swizzle period");
-static_assert(2 * kWtSmem + 2048 <= 228 * 1024, "two blocks of two stages each must fit on an SM");
+static_assert(kWtXB % 1024 == 0 && kWtStage % 1024 == 0, "staged regions start on the swizzle period");
+static_assert(kWtSmem <= 227 * 1024, "two stages must fit in shared memory");
 // kind::f16, fp32 accumulator, bf16 A and B, both MN-major, N = 96, M = 128
 constexpr uint32_t kWtIdesc =
     (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
@@ -838,10 +838,10 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t addr, uint32_t lbo, 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-constexpr int kWtThreads = 256;
+constexpr int kWtThreads = 512;
 constexpr int kWtXC = 4 * kWtR * kWtXP, kWtZC = 4 * (kWtR + 2) * kWtC;  // 16-byte chunks of a tile's x and dz
 constexpr int kWtPre = (kWtXC + kWtZC + kWtThreads - 1) / kWtThreads;   // chunks per thread
-__global__ void __launch_bounds__(kWtThreads, 2) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
+__global__ void __launch_bounds__(kWtThreads, 1) k_conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
                                                                  const __nv_bfloat16 *__restrict__ dz,
                                                                  float *__restrict__ dw, float *__restrict__ db,
                                                                  int nimg, int H, int W, int *err) {
@@ -1270,7 +1270,7 @@ int grid_wgrad_tc(int nimg, int H, int W) {
   static int sms = 0;
   if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const long long tiles = (long long)((W + kWtC - 1) / kWtC) * ((H + kWtR - 1) / kWtR) * nimg;
-  return (int)(tiles < 2 * sms ? tiles : 2 * sms);  // two blocks per SM
+  return (int)(tiles < sms ? tiles : sms);
 }
 
 // Persistent grid of the one-channel weight-gradient kernel (attributes set by set_attrs).
