@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
 }
 
 // Tiled form of the fused reverse step: one block of 4 warps per work item of
-// 128 columns x 16 rows (2 per warp), non-persistent (a grid of the items of
+// 128 columns x 16 rows (4 per warp), non-persistent (a grid of the items of
 // up to kBGMax consecutive shots), with the current levels of both fields
 // over the item and its halo and the item's imaging accumulators staged in
 // shared memory by cp.async before a single barrier, as in the single-shot
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(32 * k2dWarps) k_rev2d_batch(const BShot *__re
 // per-call part (source offset, receivers, records) is read from the shot
 // descriptors in global memory, the source offset before the wait for the
 // previous step.
-constexpr int kBTileW = 8, kBTileRZ = 2, kBTileT = kBTileW * kBTileRZ;
+constexpr int kBTileW = 4, kBTileRZ = 4, kBTileT = kBTileW * kBTileRZ;
 constexpr int kBGMax = 16;  // shots per launch of the tiled reverse
 struct BRevShot {
   Lay L;
@@ -161,7 +161,7 @@ struct BRevGroup {
   int tbase[kBGMax + 1];      // first item of each shot in this launch, then the item count
   BRevShot s[kBGMax];
 };
-__global__ void __launch_bounds__(32 * kBTileW, 4) k_rev2d_batch_tile(const __grid_constant__ BRevGroup G,
+__global__ void __launch_bounds__(32 * kBTileW, 5) k_rev2d_batch_tile(const __grid_constant__ BRevGroup G,
                                                                       const BShot *__restrict__ shots, int n, int nt,
                                                                       const float *__restrict__ wav, float src_scale,
                                                                       float rec_scale) {
