@@ -16,7 +16,9 @@
 // 32 -> 1 last layer run as implicit GEMMs on the 5th-generation tensor cores
 // (tcgen05.mma, operands in shared memory, fp32 accumulators in tensor
 // memory).  The one-channel first layer runs on the warp-level tensor cores
-// (mma.sync m16n8k16, the 9 taps padded to K = 16).  The weight gradients of
+// (mma.sync m16n8k16, the 9 taps padded to K = 16): as its own kernel in the
+// training forward (its output is kept for the backward pass), inside the
+// second layer's kernel for inference.  The weight gradients of
 // the 32 -> 32 layers run on tcgen05 too (one MMA per 16 pixels covers all
 // nine taps); those of the one-channel end layers on mma.sync with the taps
 // on M.  Persistent blocks add their sums to the fp32 gradient once each.
